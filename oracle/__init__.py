@@ -1,0 +1,308 @@
+"""CPU oracle for the tiled Householder QR -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow FP64 implementation of Algorithm 2 of Buttari, Langou, Kurzak and
+Dongarra (the four tile kernels of Sec. 3.2.1 with the inner blocking of
+Sec. 3.2.3), an independent unblocked Householder QR, Q^T application and the
+least-squares solve, all in ``tileqr_oracle.c`` and called here through ctypes.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA
+library and the CUDA library never calls it.
+
+Every pinned function is checked in ``tests/test_oracle_*.py`` against
+closed forms, LAPACK's own tile kernels (dgeqrt, dgemqrt, dtpqrt, dtpmqrt),
+invariants, and brute force; none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tileqr_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+TASK_GEQRT, TASK_TSQRT, TASK_LARFB, TASK_SSRFB = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no FMA contraction, no -march)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        i64, i32, dp = ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+        lib.oracle_tiled_qr.argtypes = [i64, i64, dp, i64, i32, i32, dp, i64]
+        lib.oracle_tiled_qr_ordered.argtypes = [i64, i64, dp, i64, i32, i32, dp, i64, i64,
+                                                ctypes.POINTER(ctypes.c_int32)]
+        lib.oracle_apply_qt.argtypes = [i64, i64, dp, i64, i32, i32, dp, i64, i64, dp, i64]
+        lib.oracle_solve_ls.argtypes = [i64, i64, dp, i64, i32, i32, dp, i64, i64, dp, i64]
+        lib.oracle_unblocked_qr.argtypes = [i64, i64, dp, i64]
+        lib.oracle_flops.restype = ctypes.c_double
+        lib.oracle_set_mutation.argtypes = [i32]
+        for f in (lib.oracle_tiled_qr, lib.oracle_tiled_qr_ordered, lib.oracle_apply_qt,
+                  lib.oracle_solve_ls, lib.oracle_unblocked_qr):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _fortran(a) -> np.ndarray:
+    return np.array(a, dtype=np.float64, order="F", copy=True)
+
+
+def geometry(m: int, n: int, nb: int):
+    """Tile grid p x q and the partial-tile extents (Sec. 3.2.1 with ragged edges)."""
+    p, q = -(-m // nb), -(-n // nb)
+    mr = [min(nb, m - i * nb) for i in range(p)]
+    nc = [min(nb, n - j * nb) for j in range(q)]
+    return p, q, mr, nc
+
+
+class Factored:
+    """Result of the tiled factorization: A overwritten by R and V, plus T.
+
+    ``A`` is m x n column-major; ``T`` is (p*ib) x n column-major, the strip of
+    tile (i, k) being rows i*ib..i*ib+ib-1 and columns k*nb..k*nb+nc(k)-1.
+    """
+
+    def __init__(self, A, T, m, n, nb, ib):
+        self.A, self.T, self.m, self.n, self.nb, self.ib = A, T, m, n, nb, ib
+
+    def R(self) -> np.ndarray:
+        """The min(m,n) x n upper-trapezoidal R factor."""
+        k = min(self.m, self.n)
+        return np.triu(self.A[:k, :])
+
+    def tile(self, i, j):
+        nb = self.nb
+        return self.A[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb]
+
+    def tstrip(self, i, k):
+        nb, ib = self.nb, self.ib
+        return self.T[i * ib:(i + 1) * ib, k * nb:(k + 1) * nb]
+
+
+def tiled_qr(A, nb: int, ib: int) -> Factored:
+    """Algorithm 2 on a copy of A, tasks in the printed loop order."""
+    lib = _load()
+    A = _fortran(A)
+    m, n = A.shape
+    p = -(-m // nb) if m else 0
+    T = np.zeros((max(p * ib, 1), max(n, 1)), dtype=np.float64, order="F")
+    rc = lib.oracle_tiled_qr(m, n, _dp(A), max(m, 1), nb, ib, _dp(T), T.shape[0])
+    if rc:
+        raise ValueError(f"oracle_tiled_qr: illegal argument {rc}")
+    return Factored(A, T, m, n, nb, ib)
+
+
+def tiled_qr_ordered(A, nb: int, ib: int, tasks) -> Factored:
+    """Algorithm 2 with its tasks run in the given order (rows {kind,i,j,k})."""
+    lib = _load()
+    A = _fortran(A)
+    m, n = A.shape
+    p = -(-m // nb)
+    T = np.zeros((max(p * ib, 1), max(n, 1)), dtype=np.float64, order="F")
+    tk = np.ascontiguousarray(np.asarray(tasks, dtype=np.int32).reshape(-1, 4))
+    rc = lib.oracle_tiled_qr_ordered(m, n, _dp(A), max(m, 1), nb, ib, _dp(T), T.shape[0],
+                                     tk.shape[0],
+                                     tk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc:
+        raise ValueError(f"oracle_tiled_qr_ordered: illegal argument {rc}")
+    return Factored(A, T, m, n, nb, ib)
+
+
+def apply_qt(f: Factored, B) -> np.ndarray:
+    """Q^T B for the Q held (as V and T) in a Factored result."""
+    lib = _load()
+    B = _fortran(B)
+    if B.ndim == 1:
+        B = B.reshape(-1, 1, order="F")
+    rc = lib.oracle_apply_qt(f.m, f.n, _dp(f.A), max(f.m, 1), f.nb, f.ib, _dp(f.T),
+                             f.T.shape[0], B.shape[1], _dp(B), max(f.m, 1))
+    if rc:
+        raise ValueError(f"oracle_apply_qt: illegal argument {rc}")
+    return B
+
+
+def solve_ls(f: Factored, B) -> np.ndarray:
+    """argmin_X ||A X - B||_F for m >= n: Q^T B then back substitution with R."""
+    lib = _load()
+    B = _fortran(B)
+    if B.ndim == 1:
+        B = B.reshape(-1, 1, order="F")
+    rc = lib.oracle_solve_ls(f.m, f.n, _dp(f.A), max(f.m, 1), f.nb, f.ib, _dp(f.T),
+                             f.T.shape[0], B.shape[1], _dp(B), max(f.m, 1))
+    if rc < 0:
+        raise ValueError(f"oracle_solve_ls: illegal argument {rc}")
+    if rc > 0:
+        raise np.linalg.LinAlgError(f"R({rc - 1},{rc - 1}) is exactly zero")
+    return B[:f.n, :].copy(order="F")
+
+
+def unblocked_qr(A) -> np.ndarray:
+    """R of the textbook unblocked Householder QR (independent of the tiled code)."""
+    lib = _load()
+    A = _fortran(A)
+    m, n = A.shape
+    rc = lib.oracle_unblocked_qr(m, n, _dp(A), max(m, 1))
+    if rc:
+        raise ValueError("oracle_unblocked_qr: illegal argument")
+    return np.triu(A[:min(m, n), :])
+
+
+def flops() -> float:
+    return _load().oracle_flops()
+
+
+def reset_flops() -> None:
+    _load().oracle_reset_flops()
+
+
+def set_mutation(code: int) -> None:
+    """Plant a deliberate mistake in the oracle's arithmetic (tests only)."""
+    _load().oracle_set_mutation(int(code))
+
+
+# ---------------------------------------------------------------------------
+# Task graph of Algorithm 2 (Sec. 4).
+def task_list(m: int, n: int, nb: int):
+    """Tasks {kind, i, j, k} in the printed loop order of Algorithm 2."""
+    p, q, _, _ = geometry(m, n, nb)
+    out = []
+    for k in range(min(p, q)):
+        out.append((TASK_GEQRT, k, k, k))
+        for j in range(k + 1, q):
+            out.append((TASK_LARFB, k, j, k))
+        for i in range(k + 1, p):
+            out.append((TASK_TSQRT, i, k, k))
+            for j in range(k + 1, q):
+                out.append((TASK_SSRFB, i, j, k))
+    return out
+
+
+def task_access(kind: int, i: int, j: int, k: int):
+    """(reads, writes) of one task as sets of data items, from the kernel
+    definitions of Sec. 3.2.1.  The diagonal tile is split into its R part
+    ('R', k, k) (upper triangle) and its V part ('V', k, k) (strict lower);
+    ('T', i, k) is the T strip."""
+    if kind == TASK_GEQRT:
+        # consumes the whole diagonal tile as last written by the previous step
+        return {("A", k, k)}, {("R", k, k), ("V", k, k), ("T", k, k)}
+    if kind == TASK_LARFB:
+        return {("V", k, k), ("T", k, k)}, {("A", k, j)}
+    if kind == TASK_TSQRT:
+        return set(), {("R", k, k), ("A", i, k), ("T", i, k)}
+    return {("A", i, k), ("T", i, k)}, {("A", k, j), ("A", i, j)}
+
+
+def dependencies(m: int, n: int, nb: int):
+    """Predecessor sets derived mechanically from the reads/writes of the
+    sequential order: a task depends on the last writer of everything it
+    touches, and a writer also waits for the readers since that write."""
+    tasks = task_list(m, n, nb)
+    last_w, readers = {}, {}
+    preds = {}
+    for t in tasks:
+        r, w = task_access(*t)
+        # the read-modify-write of tiles: a written tile is also read unless the
+        # task creates it outright (GEQRT/TSQRT start from the prior contents)
+        touched = r | w
+        ps = set()
+        for d in touched:
+            if d in last_w:
+                ps.add(last_w[d])
+        for d in w:
+            ps |= readers.get(d, set())
+        preds[t] = ps - {t}
+        for d in r:
+            readers.setdefault(d, set()).add(t)
+        for d in w:
+            last_w[d] = t
+            readers[d] = set()
+    return tasks, preds
+
+
+def random_topological_order(m: int, n: int, nb: int, rng: np.random.Generator):
+    tasks, preds = dependencies(m, n, nb)
+    succ = {t: [] for t in tasks}
+    indeg = {t: len(preds[t]) for t in tasks}
+    for t, ps in preds.items():
+        for s in ps:
+            succ[s].append(t)
+    ready = [t for t in tasks if indeg[t] == 0]
+    order = []
+    while ready:
+        t = ready.pop(int(rng.integers(len(ready))))
+        order.append(t)
+        for s in succ[t]:
+            indeg[s] -= 1
+            if indeg[s] == 0:
+                ready.append(s)
+    assert len(order) == len(tasks)
+    return order
+
+
+# ---------------------------------------------------------------------------
+# Checks used by the tests.
+def sign_normalize(R: np.ndarray) -> np.ndarray:
+    """D R with D = diag(sign(R_jj)), sign(0) = +1."""
+    k = min(R.shape)
+    d = np.where(np.diag(R[:k, :k]) < 0, -1.0, 1.0)
+    out = R.copy()
+    out[:k, :] *= d[:, None]
+    return out
+
+
+def explicit_qt(f: Factored) -> np.ndarray:
+    """The m x m matrix Q^T, by applying Q^T to the identity."""
+    return apply_qt(f, np.eye(f.m))
+
+
+def invariants(A0: np.ndarray, f: Factored):
+    """(||Q^T Q - I||_F, ||A - QR||_F / ||A||_F, max |strict lower of R|)."""
+    Qt = explicit_qt(f)
+    Q = Qt.T
+    m, n = A0.shape
+    k = min(m, n)
+    R = f.R()
+    orth = np.linalg.norm(Q.T @ Q - np.eye(m))
+    back = np.linalg.norm(A0 - Q[:, :k] @ R) / max(np.linalg.norm(A0), 1e-300)
+    return orth, back, float(np.max(np.abs(np.tril(R, -1)))) if R.size else 0.0
+
+
+def lapack_opcount(m: int, n: int) -> float:
+    """LAPACK's Householder QR operation count 2 n^2 (m - n/3) (Sec. 5)."""
+    return 2.0 * n * n * (m - n / 3.0)
+
+
+def tiled_flop_model(m: int, n: int, nb: int, ib: int) -> float:
+    """Sec. 3.2.3: 2 n^2 (m - n/3) (1 + s/(4b)) for the DSSRFB-dominated cost."""
+    return lapack_opcount(m, n) * (1.0 + ib / (4.0 * nb))
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))
