@@ -1,0 +1,339 @@
+"""Benchmark: plain FP64 tiled QR of a 16384 x 16384 N(0,1) matrix (nb 128,
+ib 32) on one GB300 through libtileqr's C ABI, reported as Gflop/s with the
+LAPACK operation count 2 n^2 (m - n/3) (the paper's rate convention, Sec. 5)
+and as a fraction of the FP64 peak.
+
+One step = one tileqr_factor call (layout conversion + the persistent task-
+graph kernel) on an input resident in HBM.  The input (2.1 GB) is larger than
+L2 (129 MB), so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank factors its own replica on its own GPU
+(the factorization does not shard; weak scaling) and rank 0 prints one JSON
+line with the max-over-ranks time.  --impl reference times the CPU oracle
+(Algorithm 2 in plain C, one thread) on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tile-QR Gflop/s & % FP64 peak; mixed/batched speedup at ≤1e-12 LS error"
+UNIT = "Gflop/s"
+NSM = 152
+FP64_FLOP_PER_CLK_PER_SM = 4   # 2 DFMA lanes per clock per SM (1.25 TFLOP/s nominal at 2.07 GHz)
+
+
+def lapack_opcount(m, n):
+    return 2.0 * n * n * (m - n / 3.0)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_0709_1272_gb300/csrc/tile_f64.cuh", "paper_0709_1272_gb300/csrc/factor.cu",
+                "paper_0709_1272_gb300/csrc/sched.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(workload_key):
+    """DRAM bytes per launch of the task-graph kernel from the committed ncu
+    summary, if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "k_factor_dag_fp64.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"traffic_bytes_per_launch\[{re.escape(workload_key)}\]:\s*([0-9.eE+]+)", txt)
+    return float(m.group(1)) if m else None
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(nb, ib, n_sample=3072):
+    """The oracle as it stands, one thread, on a bounded sample of the workload."""
+    import oracle
+    from paper_0709_1272_gb300 import inputs
+    A = inputs.normal_matrix(n_sample, n_sample, seed=20070709 + 2)
+    t0 = time.perf_counter()
+    oracle.tiled_qr(A, nb, ib)
+    dt = time.perf_counter() - t0
+    return {"value": lapack_opcount(n_sample, n_sample) / dt / 1e9, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"oracle tiled QR (Algorithm 2, plain C, -O2, one thread) of one "
+                      f"{n_sample}x{n_sample} N(0,1) matrix, nb={nb}, ib={ib}: {dt:.1f} s"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_0709_1272_gb300 import inputs
+    n = args.ref_n
+    A = inputs.normal_matrix(n, n, seed=20070709 + 2)
+    for _ in range(args.warmup):
+        oracle.tiled_qr(A, args.nb, args.ib)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.tiled_qr(A, args.nb, args.ib)
+    dt = time.perf_counter() - t0
+    value = args.steps * lapack_opcount(n, n) / dt / 1e9
+    sample = (f"oracle tiled QR (Algorithm 2, plain C, -O2, one thread) of a {n}x{n} N(0,1) "
+              f"matrix per step, nb={args.nb}, ib={args.ib} (bounded sample of the "
+              f"{args.n}x{args.n} workload)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"plain FP64 tile QR, {n}x{n} N(0,1), nb={args.nb}, ib={args.ib} "
+                                  f"(sample of {args.n}x{args.n})", "parallelism": "none (host)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=16384)
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--nb", type=int, default=128)
+    ap.add_argument("--ib", type=int, default=32)
+    ap.add_argument("--schedule", default="dag", choices=["dag", "bulk"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-n", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_0709_1272_gb300 import build, inputs, tileqr
+    build.build()
+    tileqr.load()
+    sched = tileqr.TILEQR_SCHED_DAG if args.schedule == "dag" else tileqr.TILEQR_SCHED_BULK
+    m, n, nb, ib = args.m, args.n, args.nb, args.ib
+
+    A_host = inputs.normal_matrix(m, n, seed=20070709 + 1 + 1000 * rank)
+    A = tileqr.to_device_colmajor(A_host, dev)
+    ws = torch.empty(tileqr.tileqr_workspace_size(m, n, nb, ib), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for w in range(max(args.warmup, 1)):
+        f = tileqr.tileqr_factor(A, nb, ib, schedule=sched, workspace=ws)
+        if w == 0:
+            f.check()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    clocks = ClockSampler(gpu_id)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    tileqr.tileqr_reset_launch_count()
+    t_start.record(stream)
+    for s in range(args.steps):
+        tileqr.tileqr_set_profile_events(ev_b[s], ev_a[s])
+        f = tileqr.tileqr_factor(A, nb, ib, schedule=sched, workspace=ws)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = tileqr.tileqr_launch_count()
+    tileqr.tileqr_set_profile_events(None, None)
+    clk = clocks.stop()
+    barrier()
+    status = f.status()
+    if status != 0:
+        raise SystemExit(f"factorization failed: {tileqr.strerror(status)}")
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    dag_times = [ev_b[s].elapsed_time(ev_a[s]) / 1e3 for s in range(args.steps)]
+    if dist is not None:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    ops = lapack_opcount(m, n)
+    value = world * args.steps * ops / elapsed / 1e9
+
+    # ---- end to end through the public API: pinned host A in, R out
+    e2e = None
+    if args.e2e_steps > 0:
+        A_pin = torch.from_numpy(np.ascontiguousarray(A_host.T)).pin_memory()   # (n, m) row-major == A col-major
+        k = min(m, n)
+        R_pin = torch.empty((n, k), dtype=torch.float64).pin_memory()
+        A_dev = torch.empty((n, m), dtype=torch.float64, device=dev)
+        R_dev = torch.empty((n, k), dtype=torch.float64, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            A_dev.copy_(A_pin, non_blocking=True)
+            g = tileqr.tileqr_factor(A_dev.t(), nb, ib, schedule=sched, workspace=ws)
+            rc = tileqr.load().tileqr_get_R(tileqr.ctypes.byref(g.desc),
+                                            tileqr.ctypes.c_void_p(R_dev.data_ptr()), max(k, 1),
+                                            tileqr.ctypes.c_void_p(stream.cuda_stream))
+            assert rc == 0
+            R_pin.copy_(R_dev, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        et = e0.elapsed_time(e1) / 1e3
+        if dist is not None:
+            t = torch.tensor([et], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        assert g.status() == 0
+        e2e = {"value": world * args.e2e_steps * ops / et / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": k * n * 8,
+               "steps": args.e2e_steps,
+               "path": "pinned host A -> cudaMemcpyAsync -> tileqr_factor -> tileqr_get_R -> pinned host R"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp64_peak = NSM * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e9   # GFLOP/s
+    alg_flops = ops * (1.0 + ib / (4.0 * nb))   # work the algorithm performs (Sec. 3.2.3)
+    dag_mean = statistics.mean(dag_times)
+    achieved = alg_flops / dag_mean / 1e9
+    wl_key = f"{m}x{n}/nb{nb}/ib{ib}"
+    traffic = profiled_traffic(wl_key)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"plain FP64 tile QR, {m}x{n} N(0,1), nb={nb}, ib={ib}, "
+                               f"{'persistent task-graph kernel' if sched == 0 else 'fork-join per-step launches'}",
+                   "m": m, "n": n, "nb": nb, "ib": ib, "schedule": args.schedule,
+                   "l2": "input (%.1f GB) and tiles larger than L2 (129 MB); no flush" % (m * n * 8 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "pct_fp64_peak": 100.0 * (value / world) / fp64_peak,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
+                     "frac": achieved / fp64_peak, "traffic": traffic,
+                     "kernel": f"k_factor_dag<{nb},{ib}>",
+                     "peak_source": f"FP64 DFMA: {NSM} SMs x {FP64_FLOP_PER_CLK_PER_SM} flop/clk x "
+                                    f"{sm_max:.0f} MHz (sm_max_mhz of measured peaks)",
+                     "achieved_flops": "2n^2(m-n/3)(1+ib/(4nb)) per launch / mean launch time (CUDA events)"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if e2e:
+        out["e2e"] = e2e
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(nb, ib)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

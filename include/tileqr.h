@@ -1,0 +1,171 @@
+/*
+ * tileqr.h -- C ABI of the GB300 tiled Householder QR library (libtileqr.so).
+ *
+ * The library factors A = QR with the tiled algorithm of Buttari, Langou,
+ * Kurzak and Dongarra, "A Class of Parallel Tiled Linear Algebra Algorithms
+ * for Multicore Architectures": A is stored as a p x q grid of nb x nb tiles
+ * (Sec. 3, Block Data Layout), each tile is processed by the DGEQRT, DLARFB,
+ * DTSQRT and DSSRFB tasks of Sec. 3.2.1 with inner block size ib (Sec. 3.2.3),
+ * in the order of Algorithm 2 as its dependencies clear (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are FP64, column-major, with a leading dimension >= rows.
+ *  - Pointers named A, B, R, X are DEVICE pointers owned by the caller.
+ *  - All device memory the library uses is the caller's `workspace`; the
+ *    library allocates no device memory.  The descriptor filled in by
+ *    tileqr_factor points into that workspace, so the workspace must stay
+ *    allocated and untouched while the descriptor is used.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) unless stated otherwise.  Device-side failures (watchdog, non-
+ *    finite input) are recorded in the workspace and returned by
+ *    tileqr_status(), which synchronises the stream.
+ *  - Return codes follow LAPACK: 0 = success, -i = argument i is illegal,
+ *    positive = one of the TILEQR_ERR_* codes below.
+ */
+#ifndef TILEQR_H
+#define TILEQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *tileqr_stream_t; /* identical to cudaStream_t */
+
+/* Arithmetic of the trailing updates (DLARFB/DSSRFB).  Panels (DGEQRT,
+ * DTSQRT: norms, tau, T factors) are always FP64. */
+enum {
+    TILEQR_FP64 = 0,       /* every task in FP64 */
+    TILEQR_TF32 = 1,       /* updates as TF32 products, FP32 accumulation (reserved) */
+    TILEQR_SPLIT_BF16 = 2  /* updates as split-BF16 products, FP32 accumulation (reserved) */
+};
+
+/* How the task graph is executed. */
+enum {
+    TILEQR_SCHED_DAG = 0,  /* one persistent kernel: per-task dependency counters and
+                              device ready queues in the priority order of Sec. 4 */
+    TILEQR_SCHED_BULK = 1  /* fork-join comparator: per step k, one launch per task
+                              kind (GEQRT; LARFB row; TSQRT chain; SSRFB columns) */
+};
+
+/* Flags for tileqr_factor. */
+enum {
+    TILEQR_FLAG_NONE = 0,
+    /* Fault injection for tests of the watchdog: the scheduler never releases
+     * the final task, so the persistent kernel must give up after the watchdog
+     * limit and report TILEQR_ERR_TIMEOUT.  No device fault is involved. */
+    TILEQR_FLAG_TEST_WITHHOLD_LAST_TASK = 1
+};
+
+/* Positive error codes. */
+enum {
+    TILEQR_ERR_CUDA = 1001,      /* a CUDA runtime call failed */
+    TILEQR_ERR_TIMEOUT = 1002,   /* the scheduler's watchdog saw no progress */
+    TILEQR_ERR_NONFINITE = 1003, /* A holds a NaN or an infinity; nothing was factored */
+    TILEQR_ERR_WORKSPACE = 1004, /* workspace too small or misaligned (256 B) */
+    TILEQR_ERR_SINGULAR = 1005,  /* R has an exact zero on its diagonal (solve) */
+    TILEQR_ERR_UNSUPPORTED = 1006 /* (nb, ib, precision) combination not built */
+};
+
+/* Factorization descriptor, filled in by tileqr_factor.  Plain data; the
+ * device pointers point into the caller's workspace.
+ *
+ * tiles: p*q tiles of nb*nb doubles, tile (i,j) at offset ((j*p)+i)*nb*nb,
+ *   column-major inside the tile; partial edge tiles are zero-padded.  After
+ *   the factorization tile (i,j) holds R_ij for i < j, R_kk on and above the
+ *   diagonal of diagonal tiles with V_kk (unit lower, implicit 1s) below it,
+ *   and the full reflector tile V_ik for i > k (Sec. 3.2.1: "no extra
+ *   storage is required for the V and R tiles").
+ * T: one strip of ib*nb doubles per tile, strip (i,k) at offset
+ *   ((k*p)+i)*ib*nb, column-major ib x nb: t = nb/ib upper-triangular ib x ib
+ *   blocks side by side (the s x s T_i of Sec. 3.2.3), lower parts zero. */
+typedef struct tileqr_desc {
+    int64_t m, n;
+    int32_t nb, ib;
+    int32_t p, q;
+    int32_t precision;
+    int32_t schedule;
+    double *tiles;
+    double *T;
+    void *sched;          /* scheduler state (device) */
+    size_t sched_bytes;
+    void *workspace;
+    size_t workspace_bytes;
+} tileqr_desc;
+
+/* Bytes of device workspace tileqr_factor needs for an m x n matrix (the
+ * tiles, the T strips of Sec. 3.2.1, and the scheduler state).  Returns 0 or
+ * -i for an illegal argument i.  Host only; no CUDA call. */
+int tileqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int precision, size_t *bytes);
+
+/* Tiled QR factorization, Algorithm 2 (Sec. 3.2.1) with inner blocking
+ * (Sec. 3.2.3), executed as a task graph (Sec. 4).
+ *   m, n      matrix shape (m, n >= 0; any aspect ratio, min(p,q) steps)
+ *   A, lda    device, column-major, lda >= max(1,m); read only
+ *   nb, ib    tile size b and inner block size s; ib must divide nb.  Built
+ *             combinations: nb in {64,128,256}, ib in {16,32}
+ *   precision TILEQR_FP64 (others: TILEQR_ERR_UNSUPPORTED in this build)
+ *   schedule  TILEQR_SCHED_DAG or TILEQR_SCHED_BULK
+ *   flags     TILEQR_FLAG_*
+ *   workspace device, 256-byte aligned, >= tileqr_workspace_size() bytes
+ *   out       host descriptor, filled in on success
+ * Asynchronous.  Returns 0, -i, TILEQR_ERR_WORKSPACE, TILEQR_ERR_UNSUPPORTED
+ * or TILEQR_ERR_CUDA (launch failure).  Device-side outcome: tileqr_status. */
+int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib,
+                  int precision, int schedule, int flags, void *workspace, size_t ws_bytes,
+                  tileqr_stream_t stream, tileqr_desc *out);
+
+/* Synchronises `stream` and returns the device-side status of the last
+ * factorization run on `d`: 0, TILEQR_ERR_TIMEOUT or TILEQR_ERR_NONFINITE
+ * (or TILEQR_ERR_CUDA if the stream reports an error). */
+int tileqr_status(const tileqr_desc *d, tileqr_stream_t stream);
+
+/* Copies the min(m,n) x n upper-trapezoidal R (zeros below the diagonal) to
+ * the device array R (column-major, ldr >= max(1,min(m,n))). */
+int tileqr_get_R(const tileqr_desc *d, double *R, int64_t ldr, tileqr_stream_t stream);
+
+/* Copies the factored matrix in LAPACK's in-place form: m x n column-major
+ * AV (ldav >= max(1,m)) with R on and above the diagonal of the tile rows and
+ * the reflectors below, exactly the tile contents without padding; and, if T
+ * is not NULL, the T strips as a (p*ib) x n column-major array (ldt >= p*ib),
+ * strip (i,k) at rows i*ib.., columns k*nb.. . Both device pointers. */
+int tileqr_get_factors(const tileqr_desc *d, double *AV, int64_t ldav, double *T, int64_t ldt,
+                       tileqr_stream_t stream);
+
+/* B <- Q^T B for the Q of a factorization (Sec. 3.2.1: the DLARFB and DSSRFB
+ * transformations replayed on the columns of B in the order of Algorithm 2).
+ *   B, ldb    device, column-major m x nrhs, ldb >= max(1,m), in place
+ *   workspace device scratch of tileqr_apply_workspace_size() bytes
+ * Asynchronous. */
+int tileqr_apply_workspace_size(const tileqr_desc *d, int64_t nrhs, size_t *bytes);
+int tileqr_apply_qt(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
+                    size_t ws_bytes, tileqr_stream_t stream);
+
+/* Least-squares solve min ||A X - B||_F for m >= n with the factorization d
+ * of A: B <- Q^T B, then R X = (Q^T B)(0:n-1, :) by tiled back substitution.
+ *   B, ldb    device m x nrhs, in place; on return X is in B(0:n-1, :)
+ *   workspace device scratch of tileqr_apply_workspace_size() bytes
+ * Synchronous (returns after the solve has finished).  Returns 0, -i,
+ * TILEQR_ERR_SINGULAR (exact zero on diag R), TILEQR_ERR_CUDA. */
+int tileqr_solve_ls(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
+                    size_t ws_bytes, tileqr_stream_t stream);
+
+/* Human-readable text for a return code (static storage). */
+const char *tileqr_strerror(int code);
+
+/* Instrumentation for benchmarks.  tileqr_launch_count: kernels the library
+ * launched since the last reset (host only).  tileqr_set_profile_events: if
+ * both are non-NULL (cudaEvent_t handles), every later tileqr_factor records
+ * `before` just before and `after` just after the launches of the task-graph
+ * execution proper (after the layout conversion), on the call's stream; NULL
+ * disables it. */
+uint64_t tileqr_launch_count(void);
+void tileqr_reset_launch_count(void);
+void tileqr_set_profile_events(void *before, void *after);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TILEQR_H */

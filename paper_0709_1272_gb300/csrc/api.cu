@@ -1,0 +1,314 @@
+// api.cu -- the C ABI of libtileqr (declared in include/tileqr.h): argument
+// checking, workspace layout, and the launch sequences of the factorization,
+// Q^T application and least-squares solve.  All device memory comes from the
+// caller's workspace.
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+
+#include "factor.h"
+
+namespace tqr {
+static std::atomic<unsigned long long> g_launches{0};
+static cudaEvent_t g_ev_before = nullptr, g_ev_after = nullptr;
+void count_launch(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static unsigned long long watchdog_ns_default()
+{
+    const char *e = std::getenv("TILEQR_WATCHDOG_MS");
+    long ms = e ? std::atol(e) : 0;
+    if (ms <= 0)
+        ms = 10000;
+    return (unsigned long long)ms * 1000000ull;
+}
+}  // namespace tqr
+
+using namespace tqr;
+
+static int check_geom(int64_t m, int64_t n, int nb, int ib)
+{
+    if (m < 0)
+        return -1;
+    if (n < 0)
+        return -2;
+    if (nb < 1)
+        return -5;
+    if (ib < 1 || ib > nb || nb % ib != 0)
+        return -6;
+    // task codes hold 21-bit tile indices
+    if ((m + nb - 1) / nb >= (1 << 21) || (n + nb - 1) / nb >= (1 << 21))
+        return -1;
+    return 0;
+}
+
+extern "C" int tileqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int precision, size_t *bytes)
+{
+    int rc = check_geom(m, n, nb, ib);
+    if (rc)
+        return rc;
+    if (precision != TILEQR_FP64 && precision != TILEQR_TF32 && precision != TILEQR_SPLIT_BF16)
+        return -5;
+    if (!bytes)
+        return -6;
+    *bytes = make_layout(m, n, nb, ib).end;
+    return 0;
+}
+
+extern "C" int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib,
+                             int precision, int schedule, int flags, void *workspace, size_t ws_bytes,
+                             tileqr_stream_t stream, tileqr_desc *out)
+{
+    if (m < 0)
+        return -1;
+    if (n < 0)
+        return -2;
+    if (A == nullptr && m > 0 && n > 0)
+        return -3;
+    if (lda < (m > 1 ? m : 1))
+        return -4;
+    int rc = check_geom(m, n, nb, ib);
+    if (rc == -5)
+        return -5;
+    if (rc == -6)
+        return -6;
+    if (rc)
+        return rc;
+    if (precision != TILEQR_FP64 && precision != TILEQR_TF32 && precision != TILEQR_SPLIT_BF16)
+        return -7;
+    if (schedule != TILEQR_SCHED_DAG && schedule != TILEQR_SCHED_BULK)
+        return -8;
+    if (out == nullptr)
+        return -13;
+    if (precision != TILEQR_FP64 || !factor_supported(nb, ib))
+        return TILEQR_ERR_UNSUPPORTED;
+    const WsLayout L = make_layout(m, n, nb, ib);
+    if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < L.end)
+        return TILEQR_ERR_WORKSPACE;
+    char *ws = (char *)workspace;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    std::memset(out, 0, sizeof(*out));
+    out->m = m;
+    out->n = n;
+    out->nb = nb;
+    out->ib = ib;
+    out->p = L.p;
+    out->q = L.q;
+    out->precision = precision;
+    out->schedule = schedule;
+    out->tiles = (double *)(ws + L.off_tiles);
+    out->T = (double *)(ws + L.off_T);
+    out->sched = ws + L.off_ctrl;
+    out->sched_bytes = L.end - L.off_ctrl;
+    out->workspace = workspace;
+    out->workspace_bytes = ws_bytes;
+
+    // reset the scheduler state (control block, counters, queues)
+    if (cudaMemsetAsync(ws + L.off_ctrl, 0, L.end - L.off_ctrl, st) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    if (m == 0 || n == 0)
+        return 0;
+    rc = launch_cm2tile(A, lda, m, n, out->tiles, nb, L.p, L.q, (SchedCtrl *)(ws + L.off_ctrl), st);
+    if (rc)
+        return rc;
+    unsigned long long wd = watchdog_ns_default();
+    if (flags & TILEQR_FLAG_TEST_WITHHOLD_LAST_TASK)
+        wd = 300ull * 1000000ull;
+    if (schedule == TILEQR_SCHED_BULK) {
+        // the fork-join comparator has no device scheduler; a non-finite input
+        // is still reported through the control block by tileqr_status
+    }
+    if (g_ev_before && g_ev_after && cudaEventRecord(g_ev_before, st) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    rc = launch_factor(L, ws, schedule, flags, st, wd, nullptr, 0);
+    if (rc == 0 && g_ev_before && g_ev_after && cudaEventRecord(g_ev_after, st) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    return rc;
+}
+
+extern "C" int tileqr_status(const tileqr_desc *d, tileqr_stream_t stream)
+{
+    if (d == nullptr)
+        return -1;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    if (d->m == 0 || d->n == 0)
+        return 0;
+    SchedCtrl c;
+    if (cudaMemcpy(&c, d->sched, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    if (c.nonfinite)
+        return TILEQR_ERR_NONFINITE;
+    return c.error;
+}
+
+extern "C" int tileqr_get_R(const tileqr_desc *d, double *R, int64_t ldr, tileqr_stream_t stream)
+{
+    if (d == nullptr)
+        return -1;
+    const int64_t k = d->m < d->n ? d->m : d->n;
+    if (R == nullptr && k > 0)
+        return -2;
+    if (ldr < (k > 1 ? k : 1))
+        return -3;
+    if (k == 0)
+        return 0;
+    return launch_tile2cm(d->tiles, d->nb, d->p, d->q, d->m, d->n, R, ldr, 1, k, (cudaStream_t)stream);
+}
+
+extern "C" int tileqr_get_factors(const tileqr_desc *d, double *AV, int64_t ldav, double *T, int64_t ldt,
+                                  tileqr_stream_t stream)
+{
+    if (d == nullptr)
+        return -1;
+    if (AV == nullptr && d->m > 0 && d->n > 0)
+        return -2;
+    if (ldav < (d->m > 1 ? d->m : 1))
+        return -3;
+    if (T != nullptr && ldt < (int64_t)d->p * d->ib)
+        return -5;
+    if (d->m == 0 || d->n == 0)
+        return 0;
+    int rc = launch_tile2cm(d->tiles, d->nb, d->p, d->q, d->m, d->n, AV, ldav, 0, d->m, (cudaStream_t)stream);
+    if (rc == 0 && T != nullptr)
+        rc = launch_strips2cm(d->T, d->nb, d->ib, d->p, d->q, d->n, T, ldt, (cudaStream_t)stream);
+    return rc;
+}
+
+static int64_t apply_ncp(int64_t nrhs) { return ((nrhs + APPLY_W - 1) / APPLY_W) * APPLY_W; }
+
+extern "C" int tileqr_apply_workspace_size(const tileqr_desc *d, int64_t nrhs, size_t *bytes)
+{
+    if (d == nullptr)
+        return -1;
+    if (nrhs < 0)
+        return -2;
+    if (bytes == nullptr)
+        return -3;
+    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib);
+    const int64_t ncp = apply_ncp(nrhs);
+    *bytes = align256((size_t)L.p * L.nb * ncp * sizeof(double)) + apply_sched_bytes(L, (int)(ncp / APPLY_W)) + 256;
+    return 0;
+}
+
+// Q^T applied to Bt (tile-row layout) inside the apply workspace.
+static int apply_core(const tileqr_desc *d, const WsLayout &L, double *B, int64_t ldb, int64_t nrhs,
+                      char *aws, cudaStream_t st, double **Bt_out, int64_t *ncp_out, int **flag_out)
+{
+    const int64_t ncp = apply_ncp(nrhs);
+    double *Bt = (double *)aws;
+    char *sched = aws + align256((size_t)L.p * L.nb * ncp * sizeof(double));
+    int *flag = (int *)(sched + apply_sched_bytes(L, (int)(ncp / APPLY_W)));
+    if (cudaMemsetAsync(flag, 0, 256, st) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    int rc = launch_cm2rows(B, ldb, d->m, nrhs, Bt, d->nb, d->p, ncp, st);
+    if (rc)
+        return rc;
+    rc = launch_apply(L, (const char *)d->workspace, Bt, ncp, sched, st, watchdog_ns_default());
+    *Bt_out = Bt;
+    *ncp_out = ncp;
+    *flag_out = flag;
+    return rc;
+}
+
+extern "C" int tileqr_apply_qt(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
+                               size_t ws_bytes, tileqr_stream_t stream)
+{
+    if (d == nullptr)
+        return -1;
+    if (B == nullptr && nrhs > 0 && d->m > 0)
+        return -2;
+    if (ldb < (d->m > 1 ? d->m : 1))
+        return -3;
+    if (nrhs < 0)
+        return -4;
+    size_t need = 0;
+    tileqr_apply_workspace_size(d, nrhs, &need);
+    if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < need)
+        return TILEQR_ERR_WORKSPACE;
+    if (nrhs == 0 || d->m == 0 || d->n == 0)
+        return 0;
+    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib);
+    cudaStream_t st = (cudaStream_t)stream;
+    double *Bt;
+    int64_t ncp;
+    int *flag;
+    int rc = apply_core(d, L, B, ldb, nrhs, (char *)workspace, st, &Bt, &ncp, &flag);
+    if (rc)
+        return rc;
+    return launch_rows2cm(Bt, d->nb, d->p, ncp, d->m, nrhs, B, ldb, st);
+}
+
+extern "C" int tileqr_solve_ls(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
+                               size_t ws_bytes, tileqr_stream_t stream)
+{
+    if (d == nullptr)
+        return -1;
+    if (d->m < d->n)
+        return -1;
+    if (B == nullptr && nrhs > 0 && d->m > 0)
+        return -2;
+    if (ldb < (d->m > 1 ? d->m : 1))
+        return -3;
+    if (nrhs < 0)
+        return -4;
+    size_t need = 0;
+    tileqr_apply_workspace_size(d, nrhs, &need);
+    if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < need)
+        return TILEQR_ERR_WORKSPACE;
+    if (nrhs == 0 || d->n == 0)
+        return 0;
+    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib);
+    cudaStream_t st = (cudaStream_t)stream;
+    double *Bt;
+    int64_t ncp;
+    int *flag;
+    int rc = apply_core(d, L, B, ldb, nrhs, (char *)workspace, st, &Bt, &ncp, &flag);
+    if (rc)
+        return rc;
+    rc = launch_trsm(L, (const char *)d->workspace, Bt, ncp, flag, st);
+    if (rc)
+        return rc;
+    rc = launch_rows2cm(Bt, d->nb, d->p, ncp, d->m, nrhs, B, ldb, st);
+    if (rc)
+        return rc;
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    int h_flag = 0;
+    SchedCtrl c;
+    if (cudaMemcpy(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    char *sched = (char *)workspace + align256((size_t)L.p * L.nb * ncp * sizeof(double));
+    if (cudaMemcpy(&c, sched, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    if (c.error)
+        return c.error;
+    if (h_flag)
+        return TILEQR_ERR_SINGULAR;
+    return 0;
+}
+
+extern "C" const char *tileqr_strerror(int code)
+{
+    if (code == 0)
+        return "success";
+    if (code < 0)
+        return "illegal argument";
+    switch (code) {
+    case TILEQR_ERR_CUDA: return "CUDA runtime error";
+    case TILEQR_ERR_TIMEOUT: return "scheduler watchdog: no progress";
+    case TILEQR_ERR_NONFINITE: return "input holds NaN or Inf";
+    case TILEQR_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case TILEQR_ERR_SINGULAR: return "R has an exact zero on its diagonal";
+    case TILEQR_ERR_UNSUPPORTED: return "unsupported (nb, ib, precision)";
+    default: return "unknown error";
+    }
+}
+
+extern "C" uint64_t tileqr_launch_count(void) { return g_launches.load(); }
+extern "C" void tileqr_reset_launch_count(void) { g_launches.store(0); }
+extern "C" void tileqr_set_profile_events(void *before, void *after)
+{
+    g_ev_before = (cudaEvent_t)before;
+    g_ev_after = (cudaEvent_t)after;
+}

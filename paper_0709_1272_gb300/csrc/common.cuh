@@ -1,0 +1,141 @@
+// common.cuh -- internal definitions shared by the CUDA translation units of
+// libtileqr (geometry, scheduler state layout, memory-access helpers).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tileqr.h"
+
+namespace tqr {
+
+constexpr int NT = 256;    // threads per task CTA (8 warps)
+constexpr int NWARP = NT / 32;
+
+// Task kinds in the priority order of Sec. 4 (highest first): the panel
+// tasks lie on the critical path, then the row update, then the bulk update.
+enum TaskKind { K_GEQRT = 0, K_TSQRT = 1, K_LARFB = 2, K_SSRFB = 3, K_NKIND = 4 };
+
+// A task of Algorithm 2 is identified by the tile (i, j) it writes and its
+// step k <= min(i, j); the kind follows from (i == k, j == k).
+__host__ __device__ inline int task_kind(int i, int j, int k)
+{
+    return (i == k) ? (j == k ? K_GEQRT : K_LARFB) : (j == k ? K_TSQRT : K_SSRFB);
+}
+__host__ __device__ inline unsigned long long encode_task(int k, int i, int j)
+{
+    return ((unsigned long long)k << 42) | ((unsigned long long)i << 21) | (unsigned long long)j;
+}
+__host__ __device__ inline void decode_task(unsigned long long c, int &k, int &i, int &j)
+{
+    k = (int)(c >> 42);
+    i = (int)((c >> 21) & 0x1FFFFF);
+    j = (int)(c & 0x1FFFFF);
+}
+
+// Number of predecessors of a task (Sec. 4; derived from the reads and writes
+// of the four kernels): the previous-step writer of its tile (k > 0) plus
+//   GEQRT: nothing else; LARFB: GEQRT(k); TSQRT: GEQRT(k) or TSQRT(i-1,k);
+//   SSRFB: TSQRT(i,k) and LARFB(k,j) or SSRFB(i-1,j,k).
+__host__ __device__ inline int task_ndeps(int i, int j, int k)
+{
+    int prev = k > 0 ? 1 : 0;
+    switch (task_kind(i, j, k)) {
+    case K_GEQRT: return prev;
+    case K_LARFB: return 1 + prev;
+    case K_TSQRT: return 1 + prev;
+    default: return 2 + prev;
+    }
+}
+
+// Scheduler control block, at the start of the scheduler state.
+struct SchedCtrl {
+    unsigned int head[K_NKIND];   // next slot to pop, per priority level
+    unsigned int tail[K_NKIND];   // next slot to fill, per priority level
+    unsigned int completed;       // tasks finished
+    int error;                    // TILEQR_ERR_* or 0
+    int nonfinite;                // set by the layout kernel
+    unsigned int trace_cursor;    // next free trace record
+    unsigned long long pad[11];
+};
+static_assert(sizeof(SchedCtrl) <= 256, "control block must fit its 256-byte slot");
+
+// Byte layout of the workspace (every piece 256-byte aligned).
+struct WsLayout {
+    int64_t m, n;
+    int nb, ib, p, q, steps;
+    size_t off_tiles, off_T, off_ctrl, off_cnt, off_q[K_NKIND], end;
+    unsigned int cap[K_NKIND];
+    unsigned int total;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+inline WsLayout make_layout(int64_t m, int64_t n, int nb, int ib)
+{
+    WsLayout L{};
+    L.m = m;
+    L.n = n;
+    L.nb = nb;
+    L.ib = ib;
+    L.p = (int)((m + nb - 1) / nb);
+    L.q = (int)((n + nb - 1) / nb);
+    L.steps = L.p < L.q ? L.p : L.q;
+    size_t tiles = (size_t)L.p * L.q * nb * nb * sizeof(double);
+    size_t tst = (size_t)L.p * L.q * ib * nb * sizeof(double);
+    L.off_tiles = 0;
+    L.off_T = align256(tiles);
+    L.off_ctrl = L.off_T + align256(tst);
+    L.off_cnt = L.off_ctrl + 256;
+    size_t cnt = (size_t)L.steps * L.p * L.q * sizeof(unsigned int);
+    size_t off = L.off_cnt + align256(cnt);
+    unsigned long long caps[K_NKIND] = {0, 0, 0, 0};
+    for (int k = 0; k < L.steps; k++) {
+        caps[K_GEQRT] += 1;
+        caps[K_LARFB] += (unsigned long long)(L.q - k - 1);
+        caps[K_TSQRT] += (unsigned long long)(L.p - k - 1);
+        caps[K_SSRFB] += (unsigned long long)(L.p - k - 1) * (L.q - k - 1);
+    }
+    unsigned long long tot = 0;
+    for (int t = 0; t < K_NKIND; t++) {
+        L.cap[t] = (unsigned int)caps[t];
+        tot += caps[t];
+        L.off_q[t] = off;
+        off += align256((size_t)(caps[t] ? caps[t] : 1) * sizeof(unsigned long long));
+    }
+    L.total = (unsigned int)tot;
+    L.end = off;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Global-memory access that bypasses L1: tiles are written by other SMs
+// between tasks, so every tile read goes to L2 (ld.global.cg).
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ void stcg(double *p, double v) { __stcg(p, v); }
+
+__device__ __forceinline__ double warp_allsum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_allmax(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Library-wide launch counter (host side), for the benchmark's launch count.
+void count_launch(unsigned long long n = 1);
+
+}  // namespace tqr

@@ -1,0 +1,39 @@
+// factor.h -- host-side interfaces between the translation units of libtileqr.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace tqr {
+
+bool factor_supported(int nb, int ib);
+
+// Launch the factorization of the tiles already in the workspace.
+int launch_factor(const WsLayout &L, char *ws, int schedule, int flags, cudaStream_t st,
+                  unsigned long long watchdog_ns, unsigned long long *trace, unsigned int trace_cap);
+
+// Column-major <-> tile layout (K1); cm2tile also flags non-finite input in ctrl.
+int launch_cm2tile(const double *A, int64_t lda, int64_t m, int64_t n, double *tiles, int nb, int p,
+                   int q, SchedCtrl *ctrl, cudaStream_t st);
+int launch_tile2cm(const double *tiles, int nb, int p, int q, int64_t m, int64_t n, double *A,
+                   int64_t lda, int upper_only, int64_t rows_out, cudaStream_t st);
+int launch_strips2cm(const double *T, int nb, int ib, int p, int q, int64_t n, double *Tout,
+                     int64_t ldt, cudaStream_t st);
+
+// Right-hand sides in tile-row layout: p blocks of nb x ncp (ld nb), block i
+// at Bt + i * nb * ncp; ncp = ncols rounded up to the apply chunk width.
+int launch_cm2rows(const double *B, int64_t ldb, int64_t m, int64_t ncols, double *Bt, int nb, int p,
+                   int64_t ncp, cudaStream_t st);
+int launch_rows2cm(const double *Bt, int nb, int p, int64_t ncp, int64_t m, int64_t ncols, double *B,
+                   int64_t ldb, cudaStream_t st);
+
+// Q^T applied to the tile-row right-hand sides, as a task graph.
+constexpr int APPLY_W = 32;
+size_t apply_sched_bytes(const WsLayout &L, int nchunk);
+int launch_apply(const WsLayout &L, const char *ws, double *Bt, int64_t ncp, char *sched,
+                 cudaStream_t st, unsigned long long watchdog_ns);
+// Back substitution R X = Y on the first q row blocks of Bt; sets *flag to
+// j+1 (device int) for an exact zero R(j,j).
+int launch_trsm(const WsLayout &L, const char *ws, double *Bt, int64_t ncp, int *flag, cudaStream_t st);
+
+}  // namespace tqr

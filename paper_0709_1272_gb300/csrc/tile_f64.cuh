@@ -1,0 +1,513 @@
+// tile_f64.cuh -- FP64 tile tasks of the tiled QR (Sec. 3.2.1) with inner
+// blocking (Sec. 3.2.3), each executed by one 256-thread CTA.
+//
+// On GB300 the FP64 rate is ~2 DFMA/clk/SM (DFMA ~1.2 TFLOP/s per GPU; the
+// FP64 mma.sync shapes run slower than DFMA), so these kernels are built to
+// keep the DFMA pipe busy: operands staged in shared memory (loads are nearly
+// free next to a 64-cycle-per-warp DFMA issue), register-tiled accumulators
+// for latency hiding, and few barriers per inner block.
+//
+// Tiles are nb x nb column-major and zero-padded; a strip of T is ib x nb
+// column-major holding nb/ib upper-triangular ib x ib blocks.
+#pragma once
+#include "common.cuh"
+
+namespace tqr {
+
+// Column-chunk width of the updates inside the factorization.
+template <int NB>
+struct FactorW {
+    static constexpr int value = NB >= 256 ? 64 : NB;
+};
+
+template <int NB, int S, int W_ = FactorW<NB>::value>
+struct F64Cfg {
+    static_assert(NB % S == 0, "ib must divide nb");
+    static_assert(S % NWARP == 0 && S >= NWARP && S <= 32, "ib in {8,16,32}");
+    static_assert(W_ % 32 == 0 && W_ <= NB, "chunk width: multiple of 32, at most nb");
+    static constexpr int W = W_;                   // column-chunk width of the updates
+    static constexpr int LDC = NB + 1;             // shared ld of a staged column chunk
+    static constexpr int LDV = S + 1;              // shared ld of V staged as [r][a]
+    static constexpr int AW = S / NWARP;           // inner-block rows per warp (phases A, B)
+    static constexpr int CU = W / 32;              // chunk columns per lane
+    static constexpr int RV = NB / NWARP;          // tile rows per warp (phase C)
+    static constexpr int OFF_C = 0;
+    static constexpr int OFF_V = OFF_C + W * LDC;
+    static constexpr int OFF_Y = OFF_V + NB * LDV;
+    static constexpr int OFF_T = OFF_Y + S * W;
+    static constexpr int OFF_RED = OFF_T + S * S;
+    static constexpr int OFF_TAU = OFF_RED + 2 * NWARP;
+    static constexpr int OFF_MISC = OFF_TAU + S;
+    static constexpr int TOTAL = OFF_MISC + 8;
+    static constexpr size_t SMEM = (size_t)TOTAL * sizeof(double);
+    // panel staging reuses the chunk area: tail columns ld LDC, head S x S
+    static constexpr int OFF_PT = OFF_C;
+    static constexpr int OFF_PH = OFF_C + S * LDC;
+    static constexpr bool PANEL_FITS = S * LDC + S * S <= W * LDC;
+    static_assert(SMEM <= 232448, "shared memory budget of one CTA");
+};
+
+// ---------------------------------------------------------------------------
+// Apply one inner block of reflectors, transposed (Sec. 3.2.3 / Fig. 4):
+//   Y = B_l + V_l^T C ;  W = T_l^T Y ;  B_l -= W ;  C -= V_l W
+// V_l (NB x S) is staged in shared memory as [r][a] (zero where the
+// reflectors are zero), T_l as S x S column-major, the column chunk of C as
+// [c][r].  Rows r < r0 of V_l are zero and skipped.  B_l (the S rows of the
+// top tile, DSSRFB / DTSQRT) is read and written in global memory at
+// Bg[c * NB + a]; Bg == nullptr for DLARFB (the unit block of V_l lies inside
+// C).  Only columns c < nc are meaningful; columns beyond stay untouched in
+// global memory.
+template <int NB, int S, int W_>
+__device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int nc)
+{
+    using C_ = F64Cfg<NB, S, W_>;
+    constexpr int W = C_::W, LDC = C_::LDC, LDV = C_::LDV, AW = C_::AW, CU = C_::CU, RV = C_::RV;
+    double *Cs = sm + C_::OFF_C;
+    const double *Vs = sm + C_::OFF_V;
+    double *Ys = sm + C_::OFF_Y;
+    const double *Ts = sm + C_::OFF_T;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int a0 = warp * AW;
+
+    // Phase A: Y = B + V^T C
+    double y[AW][CU];
+#pragma unroll
+    for (int ai = 0; ai < AW; ai++)
+#pragma unroll
+        for (int u = 0; u < CU; u++)
+            y[ai][u] = 0.0;
+    for (int r = r0; r < NB; r++) {
+        double v[AW], cc[CU];
+#pragma unroll
+        for (int ai = 0; ai < AW; ai++)
+            v[ai] = Vs[r * LDV + a0 + ai];
+#pragma unroll
+        for (int u = 0; u < CU; u++)
+            cc[u] = Cs[(lane + 32 * u) * LDC + r];
+#pragma unroll
+        for (int ai = 0; ai < AW; ai++)
+#pragma unroll
+            for (int u = 0; u < CU; u++)
+                y[ai][u] = fma(v[ai], cc[u], y[ai][u]);
+    }
+    double b[AW][CU];
+#pragma unroll
+    for (int ai = 0; ai < AW; ai++)
+#pragma unroll
+        for (int u = 0; u < CU; u++) {
+            const int c = lane + 32 * u;
+            b[ai][u] = (Bg != nullptr && c < nc) ? ldcg(Bg + (size_t)c * NB + a0 + ai) : 0.0;
+            Ys[(a0 + ai) * W + c] = y[ai][u] + b[ai][u];
+        }
+    __syncthreads();
+
+    // Phase B: W = T^T Y (T upper triangular: W(a) = sum_{b<=a} T(b,a) Y(b))
+    double w[AW][CU];
+#pragma unroll
+    for (int ai = 0; ai < AW; ai++) {
+        const int a = a0 + ai;
+#pragma unroll
+        for (int u = 0; u < CU; u++)
+            w[ai][u] = 0.0;
+        for (int bb = 0; bb <= a; bb++) {
+            const double t = Ts[bb + a * S];
+#pragma unroll
+            for (int u = 0; u < CU; u++)
+                w[ai][u] = fma(t, Ys[bb * W + lane + 32 * u], w[ai][u]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ai = 0; ai < AW; ai++)
+#pragma unroll
+        for (int u = 0; u < CU; u++) {
+            const int c = lane + 32 * u;
+            Ys[(a0 + ai) * W + c] = w[ai][u];
+            if (Bg != nullptr && c < nc)
+                stcg(Bg + (size_t)c * NB + a0 + ai, b[ai][u] - w[ai][u]);
+        }
+    __syncthreads();
+
+    // Phase C: C -= V W over rows r >= r0
+    const int rbase = warp * RV;
+    if (rbase + RV > r0) {
+        double acc[RV][CU];
+#pragma unroll
+        for (int v = 0; v < RV; v++)
+#pragma unroll
+            for (int u = 0; u < CU; u++)
+                acc[v][u] = Cs[(lane + 32 * u) * LDC + rbase + v];
+        for (int a = 0; a < S; a++) {
+            double wv[CU];
+#pragma unroll
+            for (int u = 0; u < CU; u++)
+                wv[u] = Ys[a * W + lane + 32 * u];
+#pragma unroll
+            for (int v = 0; v < RV; v++) {
+                const double vv = Vs[(rbase + v) * LDV + a];
+#pragma unroll
+                for (int u = 0; u < CU; u++)
+                    acc[v][u] = fma(-vv, wv[u], acc[v][u]);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < RV; v++)
+            if (rbase + v >= r0)
+#pragma unroll
+                for (int u = 0; u < CU; u++)
+                    Cs[(lane + 32 * u) * LDC + rbase + v] = acc[v][u];
+    }
+    __syncthreads();
+}
+
+// Stage columns [c0, c0+nc) of a tile into the chunk area ([c][r], ld LDC);
+// columns nc..W-1 are zero-filled.
+template <int NB, int S, int W_>
+__device__ __forceinline__ void stage_chunk(double *sm, const double *tile, int c0, int nc)
+{
+    using C_ = F64Cfg<NB, S, W_>;
+    double *Cs = sm + C_::OFF_C;
+    for (int idx = threadIdx.x; idx < C_::W * NB; idx += NT) {
+        const int c = idx / NB, r = idx - c * NB;
+        Cs[c * C_::LDC + r] = (c < nc) ? ldcg(tile + (size_t)(c0 + c) * NB + r) : 0.0;
+    }
+}
+template <int NB, int S, int W_>
+__device__ __forceinline__ void store_chunk(const double *sm, double *tile, int c0, int nc, int r0)
+{
+    using C_ = F64Cfg<NB, S, W_>;
+    const double *Cs = sm + C_::OFF_C;
+    for (int idx = threadIdx.x; idx < nc * NB; idx += NT) {
+        const int c = idx / NB, r = idx - c * NB;
+        if (r >= r0)
+            stcg(tile + (size_t)(c0 + c) * NB + r, Cs[c * C_::LDC + r]);
+    }
+}
+
+// Stage V block l of a full reflector tile (DTSQRT output) as [r][a].
+template <int NB, int S, int W_>
+__device__ __forceinline__ void stage_v_full(double *sm, const double *Vt, int l0)
+{
+    using C_ = F64Cfg<NB, S, W_>;
+    double *Vs = sm + C_::OFF_V;
+    for (int idx = threadIdx.x; idx < NB * S; idx += NT) {
+        const int a = idx / NB, r = idx - a * NB;
+        Vs[r * C_::LDV + a] = ldcg(Vt + (size_t)(l0 + a) * NB + r);
+    }
+}
+// Stage V block l of a DGEQRT tile (unit lower, implicit ones) as [r][a].
+template <int NB, int S, int W_>
+__device__ __forceinline__ void stage_v_unit(double *sm, const double *Vt, int l0)
+{
+    using C_ = F64Cfg<NB, S, W_>;
+    double *Vs = sm + C_::OFF_V;
+    for (int idx = threadIdx.x; idx < NB * S; idx += NT) {
+        const int a = idx / NB, r = idx - a * NB;
+        const int j = l0 + a;
+        Vs[r * C_::LDV + a] = (r < j) ? 0.0 : (r == j ? 1.0 : ldcg(Vt + (size_t)j * NB + r));
+    }
+}
+template <int NB, int S, int W_>
+__device__ __forceinline__ void stage_t(double *sm, const double *Tt, int l0)
+{
+    using C_ = F64Cfg<NB, S, W_>;
+    double *Ts = sm + C_::OFF_T;
+    for (int idx = threadIdx.x; idx < S * S; idx += NT)
+        Ts[idx] = ldcg(Tt + (size_t)l0 * S + idx);
+}
+
+// ---------------------------------------------------------------------------
+// DSSRFB (Sec. 3.2.1): [Bt; Ct] <- Q^T [Bt; Ct] with Q = H_1..H_nb from the
+// DTSQRT reflectors in Vt and the T strip Tt, blocks l = 0..t-1 in order.
+// ncols: columns of Bt/Ct to update (tile ld is NB); the factorization
+// passes NB, the Q^T application the width of its column chunk.
+template <int NB, int S, int W_ = FactorW<NB>::value>
+__device__ void task_ssrfb(double *sm, double *Bt, double *Ct, const double *Vt, const double *Tt,
+                           int ncols = NB)
+{
+    using C_ = F64Cfg<NB, S, W_>;
+    for (int c0 = 0; c0 < ncols; c0 += C_::W) {
+        const int nc = min(C_::W, ncols - c0);
+        stage_chunk<NB, S, W_>(sm, Ct, c0, nc);
+        for (int l0 = 0; l0 < NB; l0 += S) {
+            stage_v_full<NB, S, W_>(sm, Vt, l0);
+            stage_t<NB, S, W_>(sm, Tt, l0);
+            __syncthreads();
+            apply_block<NB, S, W_>(sm, Bt + (size_t)c0 * NB + l0, 0, nc);
+        }
+        store_chunk<NB, S, W_>(sm, Ct, c0, nc, 0);
+        __syncthreads();
+    }
+}
+
+// DLARFB (Sec. 3.2.1): Ct <- Q^T Ct with the DGEQRT reflectors of the
+// diagonal tile Vt (unit lower) and its T strip.
+template <int NB, int S, int W_ = FactorW<NB>::value>
+__device__ void task_larfb(double *sm, double *Ct, const double *Vt, const double *Tt,
+                           int ncols = NB)
+{
+    using C_ = F64Cfg<NB, S, W_>;
+    for (int c0 = 0; c0 < ncols; c0 += C_::W) {
+        const int nc = min(C_::W, ncols - c0);
+        stage_chunk<NB, S, W_>(sm, Ct, c0, nc);
+        for (int l0 = 0; l0 < NB; l0 += S) {
+            stage_v_unit<NB, S, W_>(sm, Vt, l0);
+            stage_t<NB, S, W_>(sm, Tt, l0);
+            __syncthreads();
+            apply_block<NB, S, W_>(sm, nullptr, l0, nc);
+        }
+        store_chunk<NB, S, W_>(sm, Ct, c0, nc, 0);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Householder panel factorization of S columns, one column at a time.
+// Column jj of the panel has its pivot alpha in the "head" array at
+// Ph[jj * ldh + jj], the rest of the head row at Ph[c * ldh + jj] (c > jj),
+// and its tail (the entries to annihilate) at Pt[jj * LDC + r] for r in
+// [t0(jj), rows).  For DGEQRT head and tail are the same array (t0 = jj + 1);
+// for DTSQRT the head is the R block and the tail the whole A column.
+// Reflector (our reading of the Householder step, Sec. 3.2.1): sigma =
+// ||tail||; sigma == 0 -> tau = 0, no reflection; else beta = -sign(alpha)
+// hypot(alpha, sigma), tau = (beta - alpha) / beta, v = tail / (alpha - beta).
+template <int NB, int S, bool TS>
+__device__ void panel_factor(double *sm, double *Pt, double *Ph, int ldh, int rows)
+{
+    using C_ = F64Cfg<NB, S>;
+    constexpr int LDC = C_::LDC;
+    double *red = sm + C_::OFF_RED;
+    double *taus = sm + C_::OFF_TAU;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int jj = 0; jj < S; jj++) {
+        const int t0 = TS ? 0 : jj + 1;
+        double *x = Pt + jj * LDC;
+        double part = 0.0;
+        for (int r = t0 + tid; r < rows; r += NT)
+            part = fma(x[r], x[r], part);
+        part = warp_allsum(part);
+        if (lane == 0)
+            red[warp] = part;
+        __syncthreads();
+        double s2 = 0.0;
+#pragma unroll
+        for (int w = 0; w < NWARP; w++)
+            s2 += red[w];
+        double scl = 1.0;  // norm = scl * sqrt(s2)
+        if (!(s2 > 1e-280 && s2 < 1e280) && s2 != 0.0) {
+            // extreme magnitudes: rescale by the largest |x| (uniform branch)
+            double mx = 0.0;
+            for (int r = t0 + tid; r < rows; r += NT)
+                mx = fmax(mx, fabs(x[r]));
+            mx = warp_allmax(mx);
+            if (lane == 0)
+                red[NWARP + warp] = mx;
+            __syncthreads();
+            mx = 0.0;
+#pragma unroll
+            for (int w = 0; w < NWARP; w++)
+                mx = fmax(mx, red[NWARP + w]);
+            const double inv = 1.0 / mx;
+            part = 0.0;
+            for (int r = t0 + tid; r < rows; r += NT)
+                part = fma(x[r] * inv, x[r] * inv, part);
+            part = warp_allsum(part);
+            __syncthreads();
+            if (lane == 0)
+                red[warp] = part;
+            __syncthreads();
+            s2 = 0.0;
+#pragma unroll
+            for (int w = 0; w < NWARP; w++)
+                s2 += red[w];
+            scl = mx;
+        }
+        const double alpha = Ph[jj * ldh + jj];
+        double beta = alpha, tau = 0.0, scale = 0.0;
+        if (s2 != 0.0) {
+            const double sigma = scl * sqrt(s2);
+            const double h = hypot(alpha, sigma);
+            beta = (alpha >= 0.0) ? -h : h;
+            tau = (beta - alpha) / beta;
+            scale = 1.0 / (alpha - beta);
+        }
+        // apply H_jj to the remaining panel columns, one warp per column
+        if (tau != 0.0) {
+            for (int c = jj + 1 + warp; c < S; c += NWARP) {
+                double *y = Pt + c * LDC;
+                double d = 0.0;
+                for (int r = t0 + lane; r < rows; r += 32)
+                    d = fma(x[r], y[r], d);
+                d = warp_allsum(d);
+                const double wv = Ph[c * ldh + jj] + scale * d;
+                const double tw = tau * wv;
+                __syncwarp();
+                if (lane == 0)
+                    Ph[c * ldh + jj] -= tw;
+                const double f = tw * scale;
+                for (int r = t0 + lane; r < rows; r += 32)
+                    y[r] = fma(-f, x[r], y[r]);
+            }
+        }
+        __syncthreads();
+        for (int r = t0 + tid; r < rows; r += NT)
+            x[r] *= scale;
+        if (tid == 0) {
+            Ph[jj * ldh + jj] = beta;
+            taus[jj] = tau;
+        }
+    }
+    __syncthreads();
+}
+
+// Build T_l (S x S upper) from the staged V_l ([r][a], rows >= r0) and the
+// taus: forward columnwise compact-WY recurrence T(0:j-1, j) = -tau_j
+// T(0:j-1, 0:j-1) V(:,0:j-1)^T v_j, T(j,j) = tau_j (Schreiber-Van Loan, the
+// accumulation named in Sec. 3.2.1).  Result in Ts; also written to the
+// global strip Tt (block at column l0), lower parts zero.
+template <int NB, int S>
+__device__ void build_t(double *sm, int r0, double *Tt, int l0)
+{
+    using C_ = F64Cfg<NB, S>;
+    constexpr int LDV = C_::LDV;
+    const double *Vs = sm + C_::OFF_V;
+    double *Ts = sm + C_::OFF_T;
+    const double *taus = sm + C_::OFF_TAU;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // Gram entries G(i,j), i < j, into the strict upper part of Ts
+    constexpr int NPAIR = S * (S - 1) / 2;
+    for (int pidx = tid; pidx < NPAIR; pidx += NT) {
+        // unrank pidx -> (i, j) with i < j, column-major over the strict upper triangle
+        int j = 1, base = 0;
+        while (base + j <= pidx) {
+            base += j;
+            j++;
+        }
+        const int i = pidx - base;
+        double g0 = 0.0, g1 = 0.0;
+        int r = r0;
+        for (; r + 1 < NB; r += 2) {
+            g0 = fma(Vs[r * LDV + i], Vs[r * LDV + j], g0);
+            g1 = fma(Vs[(r + 1) * LDV + i], Vs[(r + 1) * LDV + j], g1);
+        }
+        if (r < NB)
+            g0 = fma(Vs[r * LDV + i], Vs[r * LDV + j], g0);
+        Ts[i + j * S] = g0 + g1;
+    }
+    for (int idx = tid; idx < S * S; idx += NT) {
+        const int i = idx % S, j = idx / S;
+        if (i == j)
+            Ts[idx] = taus[j];
+        else if (i > j)
+            Ts[idx] = 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int j = 1; j < S; j++) {
+            const double tj = Ts[j + j * S];
+            double acc = 0.0;
+            if (lane < j)
+                for (int b = lane; b < j; b++)
+                    acc = fma(Ts[lane + b * S], Ts[b + j * S], acc);
+            __syncwarp();
+            if (lane < j)
+                Ts[lane + j * S] = -tj * acc;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < S * S; idx += NT)
+        stcg(Tt + (size_t)l0 * S + idx, Ts[idx]);
+}
+
+// DGEQRT (Sec. 3.2.1): QR of the diagonal tile At in place (R on and above
+// the diagonal, V below), T strip to Tt.  Inner blocks l in order: panel
+// factorization, T_l, then the block applied to the trailing tile columns.
+template <int NB, int S>
+__device__ void task_geqrt(double *sm, double *At, double *Tt)
+{
+    using C_ = F64Cfg<NB, S>;
+    constexpr int LDC = C_::LDC, LDV = C_::LDV;
+    double *Pt = sm + C_::OFF_PT;
+    double *Vs = sm + C_::OFF_V;
+    static_assert(C_::PANEL_FITS, "panel must fit in the chunk area");
+    for (int l0 = 0; l0 < NB; l0 += S) {
+        // stage panel columns l0..l0+S-1, all rows (rows < l0 are R above the block)
+        for (int idx = threadIdx.x; idx < S * NB; idx += NT) {
+            const int c = idx / NB, r = idx - c * NB;
+            Pt[c * LDC + r] = ldcg(At + (size_t)(l0 + c) * NB + r);
+        }
+        __syncthreads();
+        // the panel starts at row l0: head and tail are rows >= l0 of the same columns
+        panel_factor<NB, S, false>(sm, Pt + l0, Pt + l0, LDC, NB - l0);
+        // write the panel back; stage V_l (unit lower) as [r][a]
+        for (int idx = threadIdx.x; idx < S * NB; idx += NT) {
+            const int c = idx / NB, r = idx - c * NB;
+            const double val = Pt[c * LDC + r];
+            if (r >= l0)
+                stcg(At + (size_t)(l0 + c) * NB + r, val);
+            const int j = l0 + c;
+            Vs[r * LDV + c] = (r < j) ? 0.0 : (r == j ? 1.0 : val);
+        }
+        __syncthreads();
+        build_t<NB, S>(sm, l0, Tt, l0);
+        for (int c0 = l0 + S; c0 < NB; c0 += C_::W) {
+            const int nc = min(C_::W, NB - c0);
+            stage_chunk<NB, S, C_::W>(sm, At, c0, nc);
+            __syncthreads();
+            apply_block<NB, S, C_::W>(sm, nullptr, l0, nc);
+            store_chunk<NB, S, C_::W>(sm, At, c0, nc, l0);
+            __syncthreads();
+        }
+    }
+}
+
+// DTSQRT (Sec. 3.2.1, inner blocking Sec. 3.2.3): QR of [R; A] where R is
+// the upper triangle of the diagonal tile Rt and A the tile At; R updated in
+// place (upper triangle only: V_kk below the diagonal is left untouched), A
+// overwritten by the reflector tile, T strip to Tt.
+template <int NB, int S>
+__device__ void task_tsqrt(double *sm, double *Rt, double *At, double *Tt)
+{
+    using C_ = F64Cfg<NB, S>;
+    constexpr int LDC = C_::LDC, LDV = C_::LDV;
+    double *Pt = sm + C_::OFF_PT;
+    double *Ph = sm + C_::OFF_PH;  // S x S, column-major, ld S
+    double *Vs = sm + C_::OFF_V;
+    static_assert(C_::PANEL_FITS, "panel must fit in the chunk area");
+    for (int l0 = 0; l0 < NB; l0 += S) {
+        for (int idx = threadIdx.x; idx < S * NB; idx += NT) {
+            const int c = idx / NB, r = idx - c * NB;
+            Pt[c * LDC + r] = ldcg(At + (size_t)(l0 + c) * NB + r);
+        }
+        for (int idx = threadIdx.x; idx < S * S; idx += NT) {
+            const int c = idx / S, a = idx - c * S;
+            Ph[c * S + a] = (a <= c) ? ldcg(Rt + (size_t)(l0 + c) * NB + l0 + a) : 0.0;
+        }
+        __syncthreads();
+        panel_factor<NB, S, true>(sm, Pt, Ph, S, NB);
+        for (int idx = threadIdx.x; idx < S * NB; idx += NT) {
+            const int c = idx / NB, r = idx - c * NB;
+            const double val = Pt[c * LDC + r];
+            stcg(At + (size_t)(l0 + c) * NB + r, val);
+            Vs[r * LDV + c] = val;
+        }
+        for (int idx = threadIdx.x; idx < S * S; idx += NT) {
+            const int c = idx / S, a = idx - c * S;
+            if (a <= c)
+                stcg(Rt + (size_t)(l0 + c) * NB + l0 + a, Ph[c * S + a]);
+        }
+        __syncthreads();
+        build_t<NB, S>(sm, 0, Tt, l0);
+        for (int c0 = l0 + S; c0 < NB; c0 += C_::W) {
+            const int nc = min(C_::W, NB - c0);
+            stage_chunk<NB, S, C_::W>(sm, At, c0, nc);
+            __syncthreads();
+            apply_block<NB, S, C_::W>(sm, Rt + (size_t)c0 * NB + l0, 0, nc);
+            store_chunk<NB, S, C_::W>(sm, At, c0, nc, 0);
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace tqr

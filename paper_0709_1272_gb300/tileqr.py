@@ -1,0 +1,263 @@
+"""Thin ctypes binding of libtileqr (include/tileqr.h).
+
+Argument marshalling only: every step of the factorization, Q^T application
+and solve runs in the library's CUDA kernels.  PyTorch provides the device
+memory (the caller-side workspace) and the current CUDA stream.  There is no
+CPU fallback: if the compiled library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtileqr.so")
+
+TILEQR_FP64, TILEQR_TF32, TILEQR_SPLIT_BF16 = 0, 1, 2
+TILEQR_SCHED_DAG, TILEQR_SCHED_BULK = 0, 1
+TILEQR_FLAG_NONE, TILEQR_FLAG_TEST_WITHHOLD_LAST_TASK = 0, 1
+TILEQR_ERR_CUDA = 1001
+TILEQR_ERR_TIMEOUT = 1002
+TILEQR_ERR_NONFINITE = 1003
+TILEQR_ERR_WORKSPACE = 1004
+TILEQR_ERR_SINGULAR = 1005
+TILEQR_ERR_UNSUPPORTED = 1006
+
+EXPORTED = [
+    "tileqr_workspace_size", "tileqr_factor", "tileqr_status", "tileqr_get_R",
+    "tileqr_get_factors", "tileqr_apply_workspace_size", "tileqr_apply_qt", "tileqr_solve_ls",
+    "tileqr_strerror", "tileqr_launch_count", "tileqr_reset_launch_count",
+    "tileqr_set_profile_events",
+]
+
+
+class tileqr_desc(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+        ("nb", ctypes.c_int32), ("ib", ctypes.c_int32),
+        ("p", ctypes.c_int32), ("q", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("schedule", ctypes.c_int32),
+        ("tiles", ctypes.c_void_p), ("T", ctypes.c_void_p),
+        ("sched", ctypes.c_void_p), ("sched_bytes", ctypes.c_size_t),
+        ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+class TileQRError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {code} ({strerror(code)})")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libtileqr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libtileqr.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    i64, i32, vp, sz = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+    dp = ctypes.POINTER(tileqr_desc)
+    sig = {
+        "tileqr_workspace_size": (i32, [i64, i64, i32, i32, i32, ctypes.POINTER(sz)]),
+        "tileqr_factor": (i32, [i64, i64, vp, i64, i32, i32, i32, i32, i32, vp, sz, vp, dp]),
+        "tileqr_status": (i32, [dp, vp]),
+        "tileqr_get_R": (i32, [dp, vp, i64, vp]),
+        "tileqr_get_factors": (i32, [dp, vp, i64, vp, i64, vp]),
+        "tileqr_apply_workspace_size": (i32, [dp, i64, ctypes.POINTER(sz)]),
+        "tileqr_apply_qt": (i32, [dp, vp, i64, i64, vp, sz, vp]),
+        "tileqr_solve_ls": (i32, [dp, vp, i64, i64, vp, sz, vp]),
+        "tileqr_strerror": (ctypes.c_char_p, [i32]),
+        "tileqr_launch_count": (ctypes.c_uint64, []),
+        "tileqr_reset_launch_count": (None, []),
+        "tileqr_set_profile_events": (None, [vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().tileqr_strerror(int(code)).decode()
+    except ImportError:
+        return "library not loaded"
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise TileQRError(rc, where)
+
+
+def as_colmajor(A: torch.Tensor) -> torch.Tensor:
+    """A float64 CUDA tensor of shape (m, n) laid out column-major (stride (1, ld))."""
+    if A.dim() == 1:
+        A = A.reshape(-1, 1)
+    if A.dtype != torch.float64:
+        raise TypeError("tileqr works on float64 matrices")
+    if not A.is_cuda:
+        raise TypeError("tileqr needs CUDA tensors")
+    m, n = A.shape
+    if A.stride(0) == 1 and (n <= 1 or A.stride(1) >= max(m, 1)):
+        return A
+    return A.t().contiguous().t()
+
+
+def colmajor_empty(m: int, n: int, device="cuda") -> torch.Tensor:
+    return torch.empty((n, m), dtype=torch.float64, device=device).t()
+
+
+def to_device_colmajor(a, device="cuda") -> torch.Tensor:
+    """Copy a host matrix (numpy or torch) into a column-major device tensor."""
+    t = torch.as_tensor(a, dtype=torch.float64)
+    if t.dim() == 1:
+        t = t.reshape(-1, 1)
+    m, n = t.shape
+    out = colmajor_empty(m, n, device)
+    out.copy_(t)
+    return out
+
+
+def _ld(A: torch.Tensor) -> int:
+    return max(int(A.stride(1)) if A.shape[1] > 1 else A.shape[0], 1)
+
+
+# ---------------------------------------------------------------------------
+# The C entry points, same names.
+def tileqr_workspace_size(m: int, n: int, nb: int, ib: int, precision: int = TILEQR_FP64) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().tileqr_workspace_size(m, n, nb, ib, precision, ctypes.byref(out)), "tileqr_workspace_size")
+    return out.value
+
+
+def tileqr_factor(A: torch.Tensor, nb: int, ib: int, precision: int = TILEQR_FP64,
+                  schedule: int = TILEQR_SCHED_DAG, flags: int = 0, workspace: torch.Tensor | None = None,
+                  stream=None) -> "Factorization":
+    A = as_colmajor(A)
+    m, n = A.shape
+    need = tileqr_workspace_size(m, n, nb, ib, precision)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=A.device)
+    d = tileqr_desc()
+    rc = load().tileqr_factor(m, n, ctypes.c_void_p(A.data_ptr()), _ld(A), nb, ib, precision, schedule,
+                              flags, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                              _stream_ptr(stream), ctypes.byref(d))
+    _check(rc, "tileqr_factor")
+    return Factorization(d, workspace, A.device)
+
+
+class Factorization:
+    """A factorization living in a caller-owned (torch) workspace."""
+
+    def __init__(self, desc: tileqr_desc, workspace: torch.Tensor, device):
+        self.desc, self.workspace, self.device = desc, workspace, device
+        self._apply_ws = None
+
+    @property
+    def m(self):
+        return self.desc.m
+
+    @property
+    def n(self):
+        return self.desc.n
+
+    def status(self, stream=None) -> int:
+        """Synchronise and return the device-side status (0 = success)."""
+        return load().tileqr_status(ctypes.byref(self.desc), _stream_ptr(stream))
+
+    def check(self, stream=None):
+        _check(self.status(stream), "tileqr factorization")
+        return self
+
+    def R(self, stream=None) -> torch.Tensor:
+        k = min(self.m, self.n)
+        R = colmajor_empty(k, self.n, self.device)
+        _check(load().tileqr_get_R(ctypes.byref(self.desc), ctypes.c_void_p(R.data_ptr()), max(k, 1),
+                                   _stream_ptr(stream)), "tileqr_get_R")
+        return R
+
+    def factors(self, stream=None):
+        """(AV, T): LAPACK-style in-place factors and the (p*ib) x n T strips."""
+        d = self.desc
+        AV = colmajor_empty(d.m, d.n, self.device)
+        T = colmajor_empty(d.p * d.ib, d.n, self.device)
+        _check(load().tileqr_get_factors(ctypes.byref(d), ctypes.c_void_p(AV.data_ptr()), max(d.m, 1),
+                                         ctypes.c_void_p(T.data_ptr()), max(d.p * d.ib, 1),
+                                         _stream_ptr(stream)), "tileqr_get_factors")
+        return AV, T
+
+    def _apply_workspace(self, nrhs: int) -> torch.Tensor:
+        out = ctypes.c_size_t(0)
+        _check(load().tileqr_apply_workspace_size(ctypes.byref(self.desc), nrhs, ctypes.byref(out)),
+               "tileqr_apply_workspace_size")
+        if self._apply_ws is None or self._apply_ws.numel() < out.value:
+            self._apply_ws = torch.empty(max(out.value, 256), dtype=torch.uint8, device=self.device)
+        return self._apply_ws
+
+    def apply_qt(self, B: torch.Tensor, stream=None) -> torch.Tensor:
+        """Q^T B in place (B column-major m x nrhs); returns B."""
+        B = as_colmajor(B)
+        ws = self._apply_workspace(B.shape[1])
+        _check(load().tileqr_apply_qt(ctypes.byref(self.desc), ctypes.c_void_p(B.data_ptr()), _ld(B),
+                                      B.shape[1], ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                      _stream_ptr(stream)), "tileqr_apply_qt")
+        return B
+
+    def solve_ls(self, B: torch.Tensor, stream=None) -> torch.Tensor:
+        """min ||A X - B||: B overwritten (X in its first n rows); returns X."""
+        B = as_colmajor(B)
+        ws = self._apply_workspace(B.shape[1])
+        _check(load().tileqr_solve_ls(ctypes.byref(self.desc), ctypes.c_void_p(B.data_ptr()), _ld(B),
+                                      B.shape[1], ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                      _stream_ptr(stream)), "tileqr_solve_ls")
+        return B[: self.n]
+
+
+def tileqr_status(f: Factorization, stream=None) -> int:
+    return f.status(stream)
+
+
+def tileqr_get_R(f: Factorization, stream=None) -> torch.Tensor:
+    return f.R(stream)
+
+
+def tileqr_get_factors(f: Factorization, stream=None):
+    return f.factors(stream)
+
+
+def tileqr_apply_qt(f: Factorization, B: torch.Tensor, stream=None) -> torch.Tensor:
+    return f.apply_qt(B, stream)
+
+
+def tileqr_solve_ls(f: Factorization, B: torch.Tensor, stream=None) -> torch.Tensor:
+    return f.solve_ls(B, stream)
+
+
+def tileqr_launch_count() -> int:
+    return int(load().tileqr_launch_count())
+
+
+def tileqr_reset_launch_count() -> None:
+    load().tileqr_reset_launch_count()
+
+
+def tileqr_set_profile_events(before=None, after=None) -> None:
+    """Record torch.cuda.Event pair around the task-graph launches of later
+    factorizations (None, None disables)."""
+    b = ctypes.c_void_p(before.cuda_event) if before is not None else None
+    a = ctypes.c_void_p(after.cuda_event) if after is not None else None
+    load().tileqr_set_profile_events(b, a)
