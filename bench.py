@@ -228,6 +228,8 @@ def main():
     ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for e in ev_b + ev_a:
+        e.record(stream)    # creates the CUDA events before the timed region
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:

@@ -258,6 +258,11 @@ def tileqr_reset_launch_count() -> None:
 def tileqr_set_profile_events(before=None, after=None) -> None:
     """Record torch.cuda.Event pair around the task-graph launches of later
     factorizations (None, None disables)."""
+    # torch creates the CUDA event on its first record(): record once here so
+    # the handle exists (the library re-records it around each launch)
+    for e in (before, after):
+        if e is not None and e.cuda_event == 0:
+            e.record()
     b = ctypes.c_void_p(before.cuda_event) if before is not None else None
     a = ctypes.c_void_p(after.cuda_event) if after is not None else None
     load().tileqr_set_profile_events(b, a)

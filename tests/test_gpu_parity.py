@@ -131,10 +131,10 @@ def test_watchdog_reports_timeout_and_context_survives(tq):
 
 
 def test_singular_solve_is_reported(tq):
-    A = np.zeros((256, 128), order="F")
-    A[:, :64] = inputs.normal_matrix(256, 64, seed=3)
-    A[:, 64:] = A[:, :64]                     # rank 64: R(64:128, 64:128) == 0 exactly
+    A = np.array(inputs.normal_matrix(256, 128, seed=3), order="F")
+    A[:, 70] = 0.0       # a zero column stays exactly zero under the reflections: R(70,70) == 0
     f, _, _, _, R = _gpu_factor(tq, A, 64, 16)
+    assert R[70, 70] == 0.0
     with pytest.raises(tq.TileQRError) as e:
         f.solve_ls(tq.to_device_colmajor(np.ones((256, 1))))
     assert e.value.code in (tq.TILEQR_ERR_SINGULAR,)
