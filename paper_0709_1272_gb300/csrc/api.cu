@@ -204,7 +204,7 @@ static int apply_core(const tileqr_desc *d, const WsLayout &L, double *B, int64_
     int rc = launch_cm2rows(B, ldb, d->m, nrhs, Bt, d->nb, d->p, ncp, st);
     if (rc)
         return rc;
-    rc = launch_apply(L, (const char *)d->workspace, Bt, ncp, sched, st, watchdog_ns_default());
+    rc = launch_apply(L, d->tiles, d->T, Bt, ncp, sched, st, watchdog_ns_default());
     *Bt_out = Bt;
     *ncp_out = ncp;
     *flag_out = flag;
@@ -266,7 +266,7 @@ extern "C" int tileqr_solve_ls(const tileqr_desc *d, double *B, int64_t ldb, int
     int rc = apply_core(d, L, B, ldb, nrhs, (char *)workspace, st, &Bt, &ncp, &flag);
     if (rc)
         return rc;
-    rc = launch_trsm(L, (const char *)d->workspace, Bt, ncp, flag, st);
+    rc = launch_trsm(L, d->tiles, Bt, ncp, flag, st);
     if (rc)
         return rc;
     rc = launch_rows2cm(Bt, d->nb, d->p, ncp, d->m, nrhs, B, ldb, st);

@@ -91,8 +91,8 @@ size_t apply_sched_bytes(const WsLayout &L, int nchunk)
 }
 
 template <int NB, int S>
-static int launch_apply_t(const WsLayout &L, const char *ws, double *Bt, int64_t ncp, char *sched,
-                          cudaStream_t st, unsigned long long watchdog_ns)
+static int launch_apply_t(const WsLayout &L, const double *tiles, const double *T, double *Bt,
+                          int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns)
 {
     constexpr size_t smem = F64Cfg<NB, S, APPLY_W>::SMEM;
     static int grid_max = 0;
@@ -107,8 +107,8 @@ static int launch_apply_t(const WsLayout &L, const char *ws, double *Bt, int64_t
         grid_max = nsm * per_sm;
     }
     ApplyArgs A;
-    A.tiles = (const double *)(ws + L.off_tiles);
-    A.T = (const double *)(ws + L.off_T);
+    A.tiles = tiles;
+    A.T = T;
     A.Bt = Bt;
     A.p = L.p;
     A.q = L.q;
@@ -145,12 +145,12 @@ static int launch_apply_t(const WsLayout &L, const char *ws, double *Bt, int64_t
     return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
 }
 
-int launch_apply(const WsLayout &L, const char *ws, double *Bt, int64_t ncp, char *sched,
-                 cudaStream_t st, unsigned long long watchdog_ns)
+int launch_apply(const WsLayout &L, const double *tiles, const double *T, double *Bt, int64_t ncp,
+                 char *sched, cudaStream_t st, unsigned long long watchdog_ns)
 {
 #define TQR_CASE(NB_, S_)                                                                        \
     if (L.nb == NB_ && L.ib == S_)                                                               \
-        return launch_apply_t<NB_, S_>(L, ws, Bt, ncp, sched, st, watchdog_ns);
+        return launch_apply_t<NB_, S_>(L, tiles, T, Bt, ncp, sched, st, watchdog_ns);
     TQR_CASE(64, 16)
     TQR_CASE(64, 32)
     TQR_CASE(128, 16)
@@ -229,9 +229,8 @@ __global__ void __launch_bounds__(NT) k_trsm_update(const double *__restrict__ t
     }
 }
 
-int launch_trsm(const WsLayout &L, const char *ws, double *Bt, int64_t ncp, int *flag, cudaStream_t st)
+int launch_trsm(const WsLayout &L, const double *tiles, double *Bt, int64_t ncp, int *flag, cudaStream_t st)
 {
-    const double *tiles = (const double *)(ws + L.off_tiles);
     const int nchunk = (int)(ncp / 32);
     const size_t smem = (size_t)L.nb * 33 * sizeof(double);
     static bool attr = false;
