@@ -66,7 +66,8 @@ enum {
     TILEQR_ERR_NONFINITE = 1003, /* A holds a NaN or an infinity; nothing was factored */
     TILEQR_ERR_WORKSPACE = 1004, /* workspace too small or misaligned (256 B) */
     TILEQR_ERR_SINGULAR = 1005,  /* R has an exact zero on its diagonal (solve) */
-    TILEQR_ERR_UNSUPPORTED = 1006 /* (nb, ib, precision) combination not built */
+    TILEQR_ERR_UNSUPPORTED = 1006, /* (nb, ib, precision) combination not built */
+    TILEQR_ERR_SCRATCH_LIMIT = 1007 /* problem too large for tileqr_factor_noalloc's fixed scratch */
 };
 
 /* Factorization descriptor, filled in by tileqr_factor.  Plain data; the
@@ -116,6 +117,44 @@ int tileqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int precision, s
 int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib,
                   int precision, int schedule, int flags, void *workspace, size_t ws_bytes,
                   tileqr_stream_t stream, tileqr_desc *out);
+
+/* tileqr_factor_noalloc -- the same FP64 factorization (persistent task-graph
+ * kernel, same results as tileqr_factor with TILEQR_SCHED_DAG) for callers
+ * that cannot allocate device memory.  The paper has no counterpart: it is an
+ * interface for deployments, not part of the method.
+ *
+ * Who it is for: services that reserve all of their device memory when they
+ * start and may not allocate afterwards (a cudaMalloc can stall the device and
+ * can fail at an arbitrary later time), and plug-ins whose host framework owns
+ * every device allocation and passes them only the buffers they read and
+ * write.  Such a caller passes the input and the outputs; nothing else.
+ *
+ *   m, n, A, lda, nb, ib  as for tileqr_factor (FP64; same built (nb, ib))
+ *   tiles, tiles_bytes    device output, >= p*q*nb*nb*8 bytes: the factored
+ *                         tiles, same layout as tileqr_desc.tiles
+ *   T, T_bytes            device output, >= p*q*ib*nb*8 bytes: the T strips,
+ *                         same layout as tileqr_desc.T
+ *   out                   filled in; usable with tileqr_status, tileqr_get_R,
+ *                         tileqr_get_factors, tileqr_apply_qt, tileqr_solve_ls
+ *
+ * The scheduler's scratch (dependency counters, ready queues, status word)
+ * is one fixed 4 MiB device array inside the library; every GPU that loads
+ * the library holds it until the process exits.  Problems whose scratch would
+ * exceed it (tile grids beyond roughly 80 x 80, e.g. n > 10240 at nb 128)
+ * return TILEQR_ERR_SCRATCH_LIMIT before any device work.  Allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library call.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * on a device share the array, which keeps the previous call's contents; each
+ * call clears it on its stream before use.  Calls whose executions overlap on
+ * the GPU (other streams, other host threads) race on it, and the device-side
+ * status read by tileqr_status(out) is only valid until the next call of this
+ * entry point on the same device.  Asynchronous; returns 0, -i,
+ * TILEQR_ERR_UNSUPPORTED, TILEQR_ERR_SCRATCH_LIMIT or TILEQR_ERR_CUDA. */
+int tileqr_factor_noalloc(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib,
+                          double *tiles, size_t tiles_bytes, double *T, size_t T_bytes,
+                          tileqr_stream_t stream, tileqr_desc *out);
 
 /* Synchronises `stream` and returns the device-side status of the last
  * factorization run on `d`: 0, TILEQR_ERR_TIMEOUT or TILEQR_ERR_NONFINITE

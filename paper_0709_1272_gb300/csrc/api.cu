@@ -301,6 +301,7 @@ extern "C" const char *tileqr_strerror(int code)
     case TILEQR_ERR_WORKSPACE: return "workspace too small or misaligned";
     case TILEQR_ERR_SINGULAR: return "R has an exact zero on its diagonal";
     case TILEQR_ERR_UNSUPPORTED: return "unsupported (nb, ib, precision)";
+    case TILEQR_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed scratch of tileqr_factor_noalloc";
     default: return "unknown error";
     }
 }

@@ -255,3 +255,65 @@ int launch_factor(const WsLayout &L, char *ws, int schedule, int flags, cudaStre
 }
 
 }  // namespace tqr
+
+namespace tqr {
+
+template <int NB, int S>
+static int launch_factor_dag_at_t(const WsLayout &L, double *tiles, double *T, char *sched,
+                                  cudaStream_t st, unsigned long long watchdog_ns)
+{
+    constexpr size_t smem = F64Cfg<NB, S>::SMEM;
+    static int grid_dag = 0;
+    if (grid_dag == 0) {
+        cudaFuncSetAttribute(k_factor_dag<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0, nsm = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_dag<NB, S>, NT, smem);
+        if (per_sm < 1 || cudaGetLastError() != cudaSuccess)
+            return TILEQR_ERR_CUDA;
+        grid_dag = nsm * per_sm;
+    }
+    FactorArgs F;
+    F.tiles = tiles;
+    F.T = T;
+    F.p = L.p;
+    F.q = L.q;
+    F.steps = L.steps;
+    Queues Q;
+    Q.ctrl = (SchedCtrl *)sched;
+    Q.cnt = (unsigned int *)(sched + (L.off_cnt - L.off_ctrl));
+    for (int t = 0; t < K_NKIND; t++) {
+        Q.slot[t] = (unsigned long long *)(sched + (L.off_q[t] - L.off_ctrl));
+        Q.cap[t] = L.cap[t];
+    }
+    Q.total = L.total;
+    Q.watchdog_ns = watchdog_ns;
+    Q.withheld = ~0ull;
+    Q.trace = nullptr;
+    Q.trace_cap = 0;
+    int grid = grid_dag;
+    if ((unsigned)grid > L.total)
+        grid = (int)L.total;
+    k_factor_dag<NB, S><<<grid, NT, smem, st>>>(F, Q);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
+}
+
+int launch_factor_dag_at(const WsLayout &L, double *tiles, double *T, char *sched, cudaStream_t st,
+                         unsigned long long watchdog_ns)
+{
+#define TQR_CASE(NB_, S_)                                                                        \
+    if (L.nb == NB_ && L.ib == S_)                                                               \
+        return launch_factor_dag_at_t<NB_, S_>(L, tiles, T, sched, st, watchdog_ns);
+    TQR_CASE(64, 16)
+    TQR_CASE(64, 32)
+    TQR_CASE(128, 16)
+    TQR_CASE(128, 32)
+    TQR_CASE(256, 16)
+    TQR_CASE(256, 32)
+#undef TQR_CASE
+    return TILEQR_ERR_UNSUPPORTED;
+}
+
+}  // namespace tqr

@@ -37,3 +37,11 @@ int launch_apply(const WsLayout &L, const double *tiles, const double *T, double
 int launch_trsm(const WsLayout &L, const double *tiles, double *Bt, int64_t ncp, int *flag, cudaStream_t st);
 
 }  // namespace tqr
+
+namespace tqr {
+// Launch the persistent task-graph kernel with the tiles, the T strips and
+// the scheduler state at explicit addresses (the state laid out as in
+// WsLayout, relative to L.off_ctrl).  The state must already be zeroed.
+int launch_factor_dag_at(const WsLayout &L, double *tiles, double *T, char *sched, cudaStream_t st,
+                         unsigned long long watchdog_ns);
+}  // namespace tqr

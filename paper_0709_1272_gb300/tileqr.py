@@ -24,12 +24,13 @@ TILEQR_ERR_NONFINITE = 1003
 TILEQR_ERR_WORKSPACE = 1004
 TILEQR_ERR_SINGULAR = 1005
 TILEQR_ERR_UNSUPPORTED = 1006
+TILEQR_ERR_SCRATCH_LIMIT = 1007
 
 EXPORTED = [
     "tileqr_workspace_size", "tileqr_factor", "tileqr_status", "tileqr_get_R",
     "tileqr_get_factors", "tileqr_apply_workspace_size", "tileqr_apply_qt", "tileqr_solve_ls",
     "tileqr_strerror", "tileqr_launch_count", "tileqr_reset_launch_count",
-    "tileqr_set_profile_events",
+    "tileqr_set_profile_events", "tileqr_factor_noalloc",
 ]
 
 
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_launch_count": (ctypes.c_uint64, []),
         "tileqr_reset_launch_count": (None, []),
         "tileqr_set_profile_events": (None, [vp, vp]),
+        "tileqr_factor_noalloc": (i32, [i64, i64, vp, i64, i32, i32, vp, sz, vp, sz, vp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
