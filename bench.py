@@ -1,5 +1,5 @@
 """Benchmark: plain FP64 tiled QR of a 16384 x 16384 N(0,1) matrix (nb 128,
-ib 32) on one GB300 through libtileqr's C ABI, reported as Gflop/s with the
+ib 16) on one GB300 through libtileqr's C ABI, reported as Gflop/s with the
 LAPACK operation count 2 n^2 (m - n/3) (the paper's rate convention, Sec. 5)
 and as a fraction of the FP64 peak.
 
@@ -179,7 +179,7 @@ def main():
     ap.add_argument("--m", type=int, default=16384)
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--nb", type=int, default=128)
-    ap.add_argument("--ib", type=int, default=32)
+    ap.add_argument("--ib", type=int, default=16)
     ap.add_argument("--schedule", default="dag", choices=["dag", "bulk"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-n", type=int, default=2048)

@@ -204,6 +204,16 @@ uint64_t tileqr_launch_count(void);
 void tileqr_reset_launch_count(void);
 void tileqr_set_profile_events(void *before, void *after);
 
+/* Task trace (the execution-flow view of Sec. 4, Fig. 6): if `records` is a
+ * device buffer of `capacity` records of 4 uint64 each, every later
+ * tileqr_factor with TILEQR_SCHED_DAG writes one record per executed task:
+ * {task code (k << 42 | i << 21 | j), start ns, end ns (%globaltimer), SM id}.
+ * Records beyond `capacity` are dropped; the number written is readable with
+ * tileqr_trace_count after the factorization (synchronises the stream).
+ * NULL disables tracing. Host only. */
+void tileqr_set_trace(void *records, uint64_t capacity);
+int tileqr_trace_count(const tileqr_desc *d, tileqr_stream_t stream, uint64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

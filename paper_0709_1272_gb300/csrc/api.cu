@@ -11,6 +11,8 @@
 namespace tqr {
 static std::atomic<unsigned long long> g_launches{0};
 static cudaEvent_t g_ev_before = nullptr, g_ev_after = nullptr;
+static unsigned long long *g_trace = nullptr;
+static unsigned long long g_trace_cap = 0;
 void count_launch(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 static unsigned long long watchdog_ns_default()
@@ -120,7 +122,8 @@ extern "C" int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda,
     }
     if (g_ev_before && g_ev_after && cudaEventRecord(g_ev_before, st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
-    rc = launch_factor(L, ws, schedule, flags, st, wd, nullptr, 0);
+    rc = launch_factor(L, ws, schedule, flags, st, wd, g_trace,
+                       (unsigned int)(g_trace_cap > 0xffffffffull ? 0xffffffffull : g_trace_cap));
     if (rc == 0 && g_ev_before && g_ev_after && cudaEventRecord(g_ev_after, st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
     return rc;
@@ -308,6 +311,30 @@ extern "C" const char *tileqr_strerror(int code)
 
 extern "C" uint64_t tileqr_launch_count(void) { return g_launches.load(); }
 extern "C" void tileqr_reset_launch_count(void) { g_launches.store(0); }
+extern "C" void tileqr_set_trace(void *records, uint64_t capacity)
+{
+    g_trace = (unsigned long long *)records;
+    g_trace_cap = records ? capacity : 0;
+}
+
+extern "C" int tileqr_trace_count(const tileqr_desc *d, tileqr_stream_t stream, uint64_t *count)
+{
+    if (d == nullptr)
+        return -1;
+    if (count == nullptr)
+        return -3;
+    *count = 0;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    if (d->m == 0 || d->n == 0)
+        return 0;
+    SchedCtrl c;
+    if (cudaMemcpy(&c, d->sched, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    *count = c.trace_cursor;
+    return 0;
+}
+
 extern "C" void tileqr_set_profile_events(void *before, void *after)
 {
     g_ev_before = (cudaEvent_t)before;

@@ -86,7 +86,7 @@ __device__ void release_factor(const Queues &Q, const FactorArgs &F, int k, int 
 }
 
 template <int NB, int S>
-__global__ void __launch_bounds__(NT, 1) k_factor_dag(FactorArgs F, Queues Q)
+__global__ void __launch_bounds__(NT, F64Cfg<NB, S>::CTAS_PER_SM) k_factor_dag(FactorArgs F, Queues Q)
 {
     extern __shared__ double sm[];
     __shared__ unsigned long long s_code;

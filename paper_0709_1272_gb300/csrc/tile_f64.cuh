@@ -14,16 +14,19 @@
 
 namespace tqr {
 
-// Column-chunk width of the updates inside the factorization.
+// Column-chunk width of the updates inside the factorization: 64 columns
+// keeps a task's shared memory near 94 KB at nb 128 / ib 16, so two task CTAs
+// share an SM and one's barriers and latency-bound panel steps overlap the
+// other's DFMA stream.
 template <int NB>
 struct FactorW {
-    static constexpr int value = NB >= 256 ? 64 : NB;
+    static constexpr int value = NB >= 128 ? 64 : NB;
 };
 
 template <int NB, int S, int W_ = FactorW<NB>::value>
 struct F64Cfg {
     static_assert(NB % S == 0, "ib must divide nb");
-    static_assert(S % NWARP == 0 && S >= NWARP && S <= 32, "ib in {8,16,32}");
+    static_assert(S % (2 * NWARP) == 0 && S <= 32, "ib in {16,32}");
     static_assert(W_ % 32 == 0 && W_ <= NB, "chunk width: multiple of 32, at most nb");
     static constexpr int W = W_;                   // column-chunk width of the updates
     static constexpr int LDC = NB + 1;             // shared ld of a staged column chunk
@@ -45,6 +48,8 @@ struct F64Cfg {
     static constexpr int OFF_PH = OFF_C + S * LDC;
     static constexpr bool PANEL_FITS = S * LDC + S * S <= W * LDC;
     static_assert(SMEM <= 232448, "shared memory budget of one CTA");
+    // CTAs per SM the shared memory allows (1 KB of the 228 KB per SM is reserved per CTA)
+    static constexpr int CTAS_PER_SM = (2 * (SMEM + 1024) <= 233472) ? 2 : 1;
 };
 
 // ---------------------------------------------------------------------------
@@ -67,7 +72,15 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
     double *Ys = sm + C_::OFF_Y;
     const double *Ts = sm + C_::OFF_T;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int a0 = warp * AW;
+    // Rows a of the inner block owned by this warp in phases A and B, mirrored
+    // in pairs (w, 2*NWARP-1-w, ...) so the triangular work of phase B
+    // (row a costs a+1 terms) is the same for every warp.
+    int arow[AW];
+#pragma unroll
+    for (int ai = 0; ai < AW; ai++) {
+        const int pair = ai >> 1, odd = ai & 1;
+        arow[ai] = pair * 2 * NWARP + (odd ? 2 * NWARP - 1 - warp : warp);
+    }
 
     // Phase A: Y = B + V^T C
     double y[AW][CU];
@@ -76,19 +89,22 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
 #pragma unroll
         for (int u = 0; u < CU; u++)
             y[ai][u] = 0.0;
+    // column groups u with 32 u >= nc hold no data: skip them (warp-uniform)
     for (int r = r0; r < NB; r++) {
         double v[AW], cc[CU];
 #pragma unroll
         for (int ai = 0; ai < AW; ai++)
-            v[ai] = Vs[r * LDV + a0 + ai];
+            v[ai] = Vs[r * LDV + arow[ai]];
 #pragma unroll
         for (int u = 0; u < CU; u++)
-            cc[u] = Cs[(lane + 32 * u) * LDC + r];
+            if (32 * u < nc)
+                cc[u] = Cs[(lane + 32 * u) * LDC + r];
 #pragma unroll
-        for (int ai = 0; ai < AW; ai++)
+        for (int u = 0; u < CU; u++)
+            if (32 * u < nc)
 #pragma unroll
-            for (int u = 0; u < CU; u++)
-                y[ai][u] = fma(v[ai], cc[u], y[ai][u]);
+                for (int ai = 0; ai < AW; ai++)
+                    y[ai][u] = fma(v[ai], cc[u], y[ai][u]);
     }
     double b[AW][CU];
 #pragma unroll
@@ -96,8 +112,8 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
 #pragma unroll
         for (int u = 0; u < CU; u++) {
             const int c = lane + 32 * u;
-            b[ai][u] = (Bg != nullptr && c < nc) ? ldcg(Bg + (size_t)c * NB + a0 + ai) : 0.0;
-            Ys[(a0 + ai) * W + c] = y[ai][u] + b[ai][u];
+            b[ai][u] = (Bg != nullptr && c < nc) ? ldcg(Bg + (size_t)c * NB + arow[ai]) : 0.0;
+            Ys[arow[ai] * W + c] = y[ai][u] + b[ai][u];
         }
     __syncthreads();
 
@@ -105,7 +121,7 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
     double w[AW][CU];
 #pragma unroll
     for (int ai = 0; ai < AW; ai++) {
-        const int a = a0 + ai;
+        const int a = arow[ai];
 #pragma unroll
         for (int u = 0; u < CU; u++)
             w[ai][u] = 0.0;
@@ -113,7 +129,8 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
             const double t = Ts[bb + a * S];
 #pragma unroll
             for (int u = 0; u < CU; u++)
-                w[ai][u] = fma(t, Ys[bb * W + lane + 32 * u], w[ai][u]);
+                if (32 * u < nc)
+                    w[ai][u] = fma(t, Ys[bb * W + lane + 32 * u], w[ai][u]);
         }
     }
     __syncthreads();
@@ -122,9 +139,9 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
 #pragma unroll
         for (int u = 0; u < CU; u++) {
             const int c = lane + 32 * u;
-            Ys[(a0 + ai) * W + c] = w[ai][u];
+            Ys[arow[ai] * W + c] = w[ai][u];
             if (Bg != nullptr && c < nc)
-                stcg(Bg + (size_t)c * NB + a0 + ai, b[ai][u] - w[ai][u]);
+                stcg(Bg + (size_t)c * NB + arow[ai], b[ai][u] - w[ai][u]);
         }
     __syncthreads();
 
@@ -141,13 +158,14 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
             double wv[CU];
 #pragma unroll
             for (int u = 0; u < CU; u++)
-                wv[u] = Ys[a * W + lane + 32 * u];
+                wv[u] = (32 * u < nc) ? Ys[a * W + lane + 32 * u] : 0.0;
 #pragma unroll
             for (int v = 0; v < RV; v++) {
                 const double vv = Vs[(rbase + v) * LDV + a];
 #pragma unroll
                 for (int u = 0; u < CU; u++)
-                    acc[v][u] = fma(-vv, wv[u], acc[v][u]);
+                    if (32 * u < nc)
+                        acc[v][u] = fma(-vv, wv[u], acc[v][u]);
             }
         }
 #pragma unroll
@@ -222,7 +240,7 @@ __device__ __forceinline__ void stage_t(double *sm, const double *Tt, int l0)
 // ncols: columns of Bt/Ct to update (tile ld is NB); the factorization
 // passes NB, the Q^T application the width of its column chunk.
 template <int NB, int S, int W_ = FactorW<NB>::value>
-__device__ void task_ssrfb(double *sm, double *Bt, double *Ct, const double *Vt, const double *Tt,
+__device__ __noinline__ void task_ssrfb(double *sm, double *Bt, double *Ct, const double *Vt, const double *Tt,
                            int ncols = NB)
 {
     using C_ = F64Cfg<NB, S, W_>;
@@ -243,7 +261,7 @@ __device__ void task_ssrfb(double *sm, double *Bt, double *Ct, const double *Vt,
 // DLARFB (Sec. 3.2.1): Ct <- Q^T Ct with the DGEQRT reflectors of the
 // diagonal tile Vt (unit lower) and its T strip.
 template <int NB, int S, int W_ = FactorW<NB>::value>
-__device__ void task_larfb(double *sm, double *Ct, const double *Vt, const double *Tt,
+__device__ __noinline__ void task_larfb(double *sm, double *Ct, const double *Vt, const double *Tt,
                            int ncols = NB)
 {
     using C_ = F64Cfg<NB, S, W_>;
@@ -271,14 +289,31 @@ __device__ void task_larfb(double *sm, double *Ct, const double *Vt, const doubl
 // Reflector (our reading of the Householder step, Sec. 3.2.1): sigma =
 // ||tail||; sigma == 0 -> tau = 0, no reflection; else beta = -sign(alpha)
 // hypot(alpha, sigma), tau = (beta - alpha) / beta, v = tail / (alpha - beta).
+// Sum of squares of x[t0:rows) for extreme magnitudes (rare path, one
+// thread): returns s2 and scl with ||x|| = scl * sqrt(s2), scl = max |x|.
+__device__ __noinline__ static void rescaled_sumsq(const double *x, int t0, int rows, double *s2,
+                                                   double *scl)
+{
+    double mx = 0.0;
+    for (int r = t0; r < rows; r++)
+        mx = fmax(mx, fabs(x[r]));
+    const double inv = 1.0 / mx;
+    double acc = 0.0;
+    for (int r = t0; r < rows; r++)
+        acc = fma(x[r] * inv, x[r] * inv, acc);
+    *s2 = acc;
+    *scl = mx;
+}
+
 template <int NB, int S, bool TS>
-__device__ void panel_factor(double *sm, double *Pt, double *Ph, int ldh, int rows)
+__device__ __noinline__ void panel_factor(double *sm, double *Pt, double *Ph, int ldh, int rows)
 {
     using C_ = F64Cfg<NB, S>;
     constexpr int LDC = C_::LDC;
     double *red = sm + C_::OFF_RED;
     double *taus = sm + C_::OFF_TAU;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+#pragma unroll 1
     for (int jj = 0; jj < S; jj++) {
         const int t0 = TS ? 0 : jj + 1;
         double *x = Pt + jj * LDC;
@@ -289,64 +324,77 @@ __device__ void panel_factor(double *sm, double *Pt, double *Ph, int ldh, int ro
         if (lane == 0)
             red[warp] = part;
         __syncthreads();
-        double s2 = 0.0;
-#pragma unroll
-        for (int w = 0; w < NWARP; w++)
-            s2 += red[w];
-        double scl = 1.0;  // norm = scl * sqrt(s2)
-        if (!(s2 > 1e-280 && s2 < 1e280) && s2 != 0.0) {
-            // extreme magnitudes: rescale by the largest |x| (uniform branch)
-            double mx = 0.0;
-            for (int r = t0 + tid; r < rows; r += NT)
-                mx = fmax(mx, fabs(x[r]));
-            mx = warp_allmax(mx);
-            if (lane == 0)
-                red[NWARP + warp] = mx;
-            __syncthreads();
-            mx = 0.0;
-#pragma unroll
-            for (int w = 0; w < NWARP; w++)
-                mx = fmax(mx, red[NWARP + w]);
-            const double inv = 1.0 / mx;
-            part = 0.0;
-            for (int r = t0 + tid; r < rows; r += NT)
-                part = fma(x[r] * inv, x[r] * inv, part);
-            part = warp_allsum(part);
-            __syncthreads();
-            if (lane == 0)
-                red[warp] = part;
-            __syncthreads();
-            s2 = 0.0;
-#pragma unroll
-            for (int w = 0; w < NWARP; w++)
-                s2 += red[w];
-            scl = mx;
+        // one thread forms the reflector scalars (FP64 sqrt, hypot and
+        // divisions are long sequences on the FP64 pipe: computing them once
+        // instead of in every warp keeps the pipe free)
+        if (tid == 0) {
+            // tree sum of the warp partials (3 dependent adds instead of 8)
+            const double s01 = red[0] + red[1], s23 = red[2] + red[3];
+            const double s45 = red[4] + red[5], s67 = red[6] + red[7];
+            double s2 = (s01 + s23) + (s45 + s67);
+            static_assert(NWARP == 8, "partial-sum tree assumes 8 warps");
+            const double alpha = Ph[jj * ldh + jj];
+            double beta = alpha, tau = 0.0, scale = 0.0;
+            if (s2 != 0.0) {
+                if (s2 > 1e-280 && s2 < 1e280 && fabs(alpha) < 1e140) {
+                    // common case: alpha^2 + sigma^2 (and beta * d below) stay in
+                    // range, so one sqrt and one reciprocal suffice:
+                    // tau = (beta - alpha) / beta = -d^2 / (beta d), scale = 1/d = beta / (beta d)
+                    const double h = sqrt(fma(alpha, alpha, s2));
+                    beta = (alpha >= 0.0) ? -h : h;
+                    const double d = alpha - beta;
+                    const double inv = 1.0 / (beta * d);
+                    tau = -d * d * inv;
+                    scale = beta * inv;
+                } else {
+                    // extreme magnitudes (rare): rescaled norm, hypot, two divisions
+                    double scl = 1.0;
+                    if (!(s2 > 1e-280 && s2 < 1e280))
+                        rescaled_sumsq(x, t0, rows, &s2, &scl);
+                    const double h = hypot(alpha, scl * sqrt(s2));
+                    beta = (alpha >= 0.0) ? -h : h;
+                    tau = (beta - alpha) / beta;
+                    scale = 1.0 / (alpha - beta);
+                }
+            }
+            red[2 * NWARP - 3] = beta;
+            red[2 * NWARP - 2] = tau;
+            red[2 * NWARP - 1] = scale;
         }
-        const double alpha = Ph[jj * ldh + jj];
-        double beta = alpha, tau = 0.0, scale = 0.0;
-        if (s2 != 0.0) {
-            const double sigma = scl * sqrt(s2);
-            const double h = hypot(alpha, sigma);
-            beta = (alpha >= 0.0) ? -h : h;
-            tau = (beta - alpha) / beta;
-            scale = 1.0 / (alpha - beta);
-        }
-        // apply H_jj to the remaining panel columns, one warp per column
-        if (tau != 0.0) {
+        __syncthreads();
+        const double beta = red[2 * NWARP - 3], tau = red[2 * NWARP - 2], scale = red[2 * NWARP - 1];
+        // apply H_jj to the remaining panel columns, one warp per column.  Each
+        // lane scales its slice of the tail once (v = x / (alpha - beta)), so
+        // the dot products see O(1) reflector entries and neither under- nor
+        // overflow for extreme column magnitudes.
+        if (tau != 0.0 && jj + 1 + warp < S) {
+            constexpr int RPL = (NB + 31) / 32;   // tail rows per lane
+            double vs[RPL];
+#pragma unroll
+            for (int k = 0; k < RPL; k++) {
+                const int r = t0 + lane + 32 * k;
+                vs[k] = (r < rows) ? x[r] * scale : 0.0;
+            }
             for (int c = jj + 1 + warp; c < S; c += NWARP) {
                 double *y = Pt + c * LDC;
                 double d = 0.0;
-                for (int r = t0 + lane; r < rows; r += 32)
-                    d = fma(x[r], y[r], d);
+#pragma unroll
+                for (int k = 0; k < RPL; k++) {
+                    const int r = t0 + lane + 32 * k;
+                    if (r < rows)
+                        d = fma(vs[k], y[r], d);
+                }
                 d = warp_allsum(d);
-                const double wv = Ph[c * ldh + jj] + scale * d;
-                const double tw = tau * wv;
+                const double tw = tau * (Ph[c * ldh + jj] + d);
                 __syncwarp();
                 if (lane == 0)
                     Ph[c * ldh + jj] -= tw;
-                const double f = tw * scale;
-                for (int r = t0 + lane; r < rows; r += 32)
-                    y[r] = fma(-f, x[r], y[r]);
+#pragma unroll
+                for (int k = 0; k < RPL; k++) {
+                    const int r = t0 + lane + 32 * k;
+                    if (r < rows)
+                        y[r] = fma(-tw, vs[k], y[r]);
+                }
             }
         }
         __syncthreads();
@@ -366,7 +414,7 @@ __device__ void panel_factor(double *sm, double *Pt, double *Ph, int ldh, int ro
 // accumulation named in Sec. 3.2.1).  Result in Ts; also written to the
 // global strip Tt (block at column l0), lower parts zero.
 template <int NB, int S>
-__device__ void build_t(double *sm, int r0, double *Tt, int l0)
+__device__ __noinline__ void build_t(double *sm, int r0, double *Tt, int l0)
 {
     using C_ = F64Cfg<NB, S>;
     constexpr int LDV = C_::LDV;
@@ -420,11 +468,28 @@ __device__ void build_t(double *sm, int r0, double *Tt, int l0)
         stcg(Tt + (size_t)l0 * S + idx, Ts[idx]);
 }
 
+// Apply inner block l (V_l, T_l already staged) to the tile columns right of
+// the block, [l0 + S, NB), chunk by chunk: the trailing update inside DGEQRT
+// (Rt == nullptr, rows >= r0 = l0) and DTSQRT (B rows l0.. of the R tile Rt).
+template <int NB, int S>
+__device__ __noinline__ void trailing_update(double *sm, double *At, double *Rt, int l0, int r0)
+{
+    using C_ = F64Cfg<NB, S>;
+    for (int c0 = l0 + S; c0 < NB; c0 += C_::W) {
+        const int nc = min(C_::W, NB - c0);
+        stage_chunk<NB, S, C_::W>(sm, At, c0, nc);
+        __syncthreads();
+        apply_block<NB, S, C_::W>(sm, Rt ? Rt + (size_t)c0 * NB + l0 : nullptr, r0, nc);
+        store_chunk<NB, S, C_::W>(sm, At, c0, nc, r0);
+        __syncthreads();
+    }
+}
+
 // DGEQRT (Sec. 3.2.1): QR of the diagonal tile At in place (R on and above
 // the diagonal, V below), T strip to Tt.  Inner blocks l in order: panel
 // factorization, T_l, then the block applied to the trailing tile columns.
 template <int NB, int S>
-__device__ void task_geqrt(double *sm, double *At, double *Tt)
+__device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt)
 {
     using C_ = F64Cfg<NB, S>;
     constexpr int LDC = C_::LDC, LDV = C_::LDV;
@@ -451,14 +516,7 @@ __device__ void task_geqrt(double *sm, double *At, double *Tt)
         }
         __syncthreads();
         build_t<NB, S>(sm, l0, Tt, l0);
-        for (int c0 = l0 + S; c0 < NB; c0 += C_::W) {
-            const int nc = min(C_::W, NB - c0);
-            stage_chunk<NB, S, C_::W>(sm, At, c0, nc);
-            __syncthreads();
-            apply_block<NB, S, C_::W>(sm, nullptr, l0, nc);
-            store_chunk<NB, S, C_::W>(sm, At, c0, nc, l0);
-            __syncthreads();
-        }
+        trailing_update<NB, S>(sm, At, nullptr, l0, l0);
     }
 }
 
@@ -467,7 +525,7 @@ __device__ void task_geqrt(double *sm, double *At, double *Tt)
 // place (upper triangle only: V_kk below the diagonal is left untouched), A
 // overwritten by the reflector tile, T strip to Tt.
 template <int NB, int S>
-__device__ void task_tsqrt(double *sm, double *Rt, double *At, double *Tt)
+__device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, double *Tt)
 {
     using C_ = F64Cfg<NB, S>;
     constexpr int LDC = C_::LDC, LDV = C_::LDV;
@@ -499,14 +557,7 @@ __device__ void task_tsqrt(double *sm, double *Rt, double *At, double *Tt)
         }
         __syncthreads();
         build_t<NB, S>(sm, 0, Tt, l0);
-        for (int c0 = l0 + S; c0 < NB; c0 += C_::W) {
-            const int nc = min(C_::W, NB - c0);
-            stage_chunk<NB, S, C_::W>(sm, At, c0, nc);
-            __syncthreads();
-            apply_block<NB, S, C_::W>(sm, Rt + (size_t)c0 * NB + l0, 0, nc);
-            store_chunk<NB, S, C_::W>(sm, At, c0, nc, 0);
-            __syncthreads();
-        }
+        trailing_update<NB, S>(sm, At, Rt, l0, 0);
     }
 }
 

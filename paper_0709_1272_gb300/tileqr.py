@@ -30,7 +30,7 @@ EXPORTED = [
     "tileqr_workspace_size", "tileqr_factor", "tileqr_status", "tileqr_get_R",
     "tileqr_get_factors", "tileqr_apply_workspace_size", "tileqr_apply_qt", "tileqr_solve_ls",
     "tileqr_strerror", "tileqr_launch_count", "tileqr_reset_launch_count",
-    "tileqr_set_profile_events", "tileqr_factor_noalloc",
+    "tileqr_set_profile_events", "tileqr_factor_noalloc", "tileqr_set_trace", "tileqr_trace_count",
 ]
 
 
@@ -79,6 +79,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_reset_launch_count": (None, []),
         "tileqr_set_profile_events": (None, [vp, vp]),
         "tileqr_factor_noalloc": (i32, [i64, i64, vp, i64, i32, i32, vp, sz, vp, sz, vp, dp]),
+        "tileqr_set_trace": (None, [vp, ctypes.c_uint64]),
+        "tileqr_trace_count": (i32, [dp, vp, ctypes.POINTER(ctypes.c_uint64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -268,3 +270,20 @@ def tileqr_set_profile_events(before=None, after=None) -> None:
     b = ctypes.c_void_p(before.cuda_event) if before is not None else None
     a = ctypes.c_void_p(after.cuda_event) if after is not None else None
     load().tileqr_set_profile_events(b, a)
+
+
+def tileqr_set_trace(records: torch.Tensor | None) -> None:
+    """Trace every task of later factorizations into `records` (an int64 CUDA
+    tensor of shape (capacity, 4)); None disables tracing."""
+    if records is None:
+        load().tileqr_set_trace(None, 0)
+        return
+    assert records.dtype == torch.int64 and records.is_cuda and records.dim() == 2 and records.shape[1] == 4
+    load().tileqr_set_trace(ctypes.c_void_p(records.data_ptr()), records.shape[0])
+
+
+def tileqr_trace_count(f: "Factorization", stream=None) -> int:
+    out = ctypes.c_uint64(0)
+    _check(load().tileqr_trace_count(ctypes.byref(f.desc), _stream_ptr(stream), ctypes.byref(out)),
+           "tileqr_trace_count")
+    return int(out.value)

@@ -109,6 +109,19 @@ def test_apply_qt_and_solve_match_oracle(tq, m, n, nb, ib, nrhs):
         assert np.linalg.norm(r) / (np.linalg.norm(A) * np.linalg.norm(X)) <= 20 * n * EPS
 
 
+@pytest.mark.parametrize("scale", [1e150, 1e-160])
+def test_extreme_magnitudes(tq, scale):
+    """Columns whose squared norms over- or underflow take the rescaled-norm
+    path of the panel kernels; results must still match the oracle, which
+    always accumulates norms with scaling."""
+    A = inputs.normal_matrix(300, 200, seed=31) * scale
+    f, _, AV, T, R = _gpu_factor(tq, A, 64, 16)
+    ref = oracle.tiled_qr(A, 64, 16)
+    assert np.all(np.isfinite(AV)) and np.all(np.isfinite(T))
+    assert _rel(AV, ref.A) <= TOL
+    assert _rel(T, ref.T) <= TOL
+
+
 def test_nonfinite_input_is_reported(tq):
     A = inputs.normal_matrix(300, 200, seed=1)
     A[17, 33] = np.nan
