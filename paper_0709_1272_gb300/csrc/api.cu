@@ -81,7 +81,11 @@ extern "C" int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda,
         return -8;
     if (out == nullptr)
         return -13;
-    if (precision != TILEQR_FP64 || !factor_supported(nb, ib))
+    if (precision == TILEQR_SPLIT_BF16)
+        return TILEQR_ERR_UNSUPPORTED;
+    if (precision == TILEQR_FP64 && !factor_supported(nb, ib))
+        return TILEQR_ERR_UNSUPPORTED;
+    if (precision == TILEQR_TF32 && (schedule != TILEQR_SCHED_DAG || !factor_mixed_supported(nb, ib)))
         return TILEQR_ERR_UNSUPPORTED;
     const WsLayout L = make_layout(m, n, nb, ib);
     if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < L.end)
@@ -122,8 +126,11 @@ extern "C" int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda,
     }
     if (g_ev_before && g_ev_after && cudaEventRecord(g_ev_before, st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
-    rc = launch_factor(L, ws, schedule, flags, st, wd, g_trace,
-                       (unsigned int)(g_trace_cap > 0xffffffffull ? 0xffffffffull : g_trace_cap));
+    const unsigned int tcap = (unsigned int)(g_trace_cap > 0xffffffffull ? 0xffffffffull : g_trace_cap);
+    if (precision == TILEQR_TF32)
+        rc = launch_factor_mixed(L, ws, flags, st, wd, g_trace, tcap);
+    else
+        rc = launch_factor(L, ws, schedule, flags, st, wd, g_trace, tcap);
     if (rc == 0 && g_ev_before && g_ev_after && cudaEventRecord(g_ev_after, st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
     return rc;

@@ -1,0 +1,162 @@
+// dag.cuh -- the persistent task-graph kernel of the tiled QR (Algorithm 2
+// executed as the DAG of Sec. 4), shared by the FP64 and mixed-precision
+// builds.  With MIXED, the DLARFB/DSSRFB tasks run on the tcgen05 tensor
+// cores (tile_mixed.cuh) while DGEQRT/DTSQRT stay in FP64.
+#pragma once
+#include "sched.cuh"
+#include "tile_f64.cuh"
+#include "tile_mixed.cuh"
+
+namespace tqr {
+
+struct FactorArgs {
+    double *tiles;
+    double *T;
+    int p, q, steps;
+};
+
+template <int NB, int S>
+__device__ __forceinline__ double *tile_ptr(const FactorArgs &F, int i, int j)
+{
+    return F.tiles + ((size_t)j * F.p + i) * (size_t)NB * NB;
+}
+template <int NB, int S>
+__device__ __forceinline__ double *strip_ptr(const FactorArgs &F, int i, int k)
+{
+    return F.T + ((size_t)k * F.p + i) * (size_t)S * NB;
+}
+
+template <int NB, int S>
+__device__ void run_factor_task(double *sm, const FactorArgs &F, int k, int i, int j)
+{
+    switch (task_kind(i, j, k)) {
+    case K_GEQRT:
+        task_geqrt<NB, S>(sm, tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k));
+        break;
+    case K_LARFB:
+        task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, k, k),
+                          strip_ptr<NB, S>(F, k, k));
+        break;
+    case K_TSQRT:
+        task_tsqrt<NB, S>(sm, tile_ptr<NB, S>(F, k, k), tile_ptr<NB, S>(F, i, k),
+                          strip_ptr<NB, S>(F, i, k));
+        break;
+    default:
+        task_ssrfb<NB, S>(sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, i, j),
+                          tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
+        break;
+    }
+}
+
+// Successors of task (k, i, j) in the graph of Algorithm 2 (the mirror of
+// task_ndeps): signalled cooperatively by all threads of the CTA.
+__device__ static void release_factor(const Queues &Q, const FactorArgs &F, int k, int i, int j)
+{
+    const int p = F.p, q = F.q;
+    const int kind = task_kind(i, j, k);
+    int nsucc = 0;
+    switch (kind) {
+    case K_GEQRT: nsucc = (q - k - 1) + (k + 1 < p ? 1 : 0); break;
+    case K_LARFB: nsucc = (k + 1 < p) ? 1 : 0; break;
+    case K_TSQRT: nsucc = (q - k - 1) + (i + 1 < p ? 1 : 0); break;
+    default: nsucc = (i + 1 < p ? 1 : 0) + 1; break;
+    }
+    for (int s = threadIdx.x; s < nsucc; s += NT) {
+        int ks, is, js;
+        switch (kind) {
+        case K_GEQRT:
+            if (s < q - k - 1) { ks = k; is = k; js = k + 1 + s; }     // LARFB(k, j)
+            else { ks = k; is = k + 1; js = k; }                       // TSQRT(k+1, k)
+            break;
+        case K_LARFB:
+            ks = k; is = k + 1; js = j;                                // SSRFB(k+1, j, k)
+            break;
+        case K_TSQRT:
+            if (s < q - k - 1) { ks = k; is = i; js = k + 1 + s; }     // SSRFB(i, j, k)
+            else { ks = k; is = i + 1; js = k; }                       // TSQRT(i+1, k)
+            break;
+        default:
+            if (s == 0 && i + 1 < p) { ks = k; is = i + 1; js = j; }   // SSRFB(i+1, j, k)
+            else { ks = k + 1; is = i; js = j; }                       // next step on tile (i,j)
+            break;
+        }
+        const size_t idx = ((size_t)ks * p + is) * q + js;
+        q_signal(Q, idx, task_ndeps(is, js, ks), task_kind(is, js, ks), encode_task(ks, is, js));
+    }
+}
+
+// Dynamic shared memory and CTAs per SM of the persistent kernel.
+template <int NB, int S, bool MIXED>
+struct DagCfg {
+    static constexpr size_t SMEM = MIXED ? (F64Cfg<NB, S>::SMEM > (size_t)MixCfg<S>::SMEM ? F64Cfg<NB, S>::SMEM
+                                                                                           : (size_t)MixCfg<S>::SMEM)
+                                         : F64Cfg<NB, S>::SMEM;
+    static constexpr int CTAS_PER_SM = MIXED ? 1 : F64Cfg<NB, S>::CTAS_PER_SM;
+};
+
+template <int NB, int S, bool MIXED>
+__global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_factor_dag(FactorArgs F, Queues Q)
+{
+    extern __shared__ double sm[];
+    __shared__ unsigned long long s_code;
+    __shared__ int s_cmd;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    uint32_t tmem = 0, mphase = 0;
+    if (MIXED) {
+        // one tensor-memory allocation and one mbarrier per persistent CTA
+        if ((threadIdx.x >> 5) == 0)
+            tc::tmem_alloc(&s_tmem, MixCfg<S>::TMEM_COLS);
+        if (threadIdx.x == 0)
+            tc::mbar_init(&s_mbar, 1);
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tmem = s_tmem;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (ld_relaxed_s32(&Q.ctrl->nonfinite) != 0)
+            atomicCAS(&Q.ctrl->error, 0, TILEQR_ERR_NONFINITE);
+        else
+            q_push(Q, K_GEQRT, encode_task(0, 0, 0));
+    }
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_cmd = q_acquire(Q, s_code);
+        __syncthreads();
+        if (s_cmd != CMD_RUN)
+            break;
+        int k, i, j;
+        decode_task(s_code, k, i, j);
+        const unsigned long long t0 = Q.trace ? globaltimer_ns() : 0ull;
+        const int kind = task_kind(i, j, k);
+        if (MIXED && kind == K_SSRFB) {
+            task_update_mixed<S, false>((unsigned char *)sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, i, j),
+                                        tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), tmem, &s_mbar,
+                                        mphase, &Q.ctrl->error);
+        } else if (MIXED && kind == K_LARFB) {
+            task_update_mixed<S, true>((unsigned char *)sm, nullptr, tile_ptr<NB, S>(F, k, j),
+                                       tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k), tmem, &s_mbar, mphase,
+                                       &Q.ctrl->error);
+        } else {
+            run_factor_task<NB, S>(sm, F, k, i, j);
+        }
+        __syncthreads();
+        release_factor(Q, F, k, i, j);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (Q.trace)
+                trace_record(Q, encode_task(k, i, j), t0, globaltimer_ns());
+            __threadfence();
+            atomicAdd(&Q.ctrl->completed, 1u);
+        }
+    }
+    if (MIXED) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0)
+            tc::tmem_dealloc(tmem, MixCfg<S>::TMEM_COLS);
+    }
+}
+
+}  // namespace tqr

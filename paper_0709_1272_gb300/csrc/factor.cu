@@ -3,121 +3,10 @@
 // comparator (one launch per task kind per step).
 #include <cstdio>
 
+#include "dag.cuh"
 #include "factor.h"
-#include "sched.cuh"
-#include "tile_f64.cuh"
 
 namespace tqr {
-
-struct FactorArgs {
-    double *tiles;
-    double *T;
-    int p, q, steps;
-};
-
-template <int NB, int S>
-__device__ __forceinline__ double *tile_ptr(const FactorArgs &F, int i, int j)
-{
-    return F.tiles + ((size_t)j * F.p + i) * (size_t)NB * NB;
-}
-template <int NB, int S>
-__device__ __forceinline__ double *strip_ptr(const FactorArgs &F, int i, int k)
-{
-    return F.T + ((size_t)k * F.p + i) * (size_t)S * NB;
-}
-
-template <int NB, int S>
-__device__ void run_factor_task(double *sm, const FactorArgs &F, int k, int i, int j)
-{
-    switch (task_kind(i, j, k)) {
-    case K_GEQRT:
-        task_geqrt<NB, S>(sm, tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k));
-        break;
-    case K_LARFB:
-        task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, k, k),
-                          strip_ptr<NB, S>(F, k, k));
-        break;
-    case K_TSQRT:
-        task_tsqrt<NB, S>(sm, tile_ptr<NB, S>(F, k, k), tile_ptr<NB, S>(F, i, k),
-                          strip_ptr<NB, S>(F, i, k));
-        break;
-    default:
-        task_ssrfb<NB, S>(sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, i, j),
-                          tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
-        break;
-    }
-}
-
-// Successors of task (k, i, j) in the graph of Algorithm 2 (the mirror of
-// task_ndeps): signalled cooperatively by all threads of the CTA.
-__device__ void release_factor(const Queues &Q, const FactorArgs &F, int k, int i, int j)
-{
-    const int p = F.p, q = F.q;
-    const int kind = task_kind(i, j, k);
-    int nsucc = 0;
-    switch (kind) {
-    case K_GEQRT: nsucc = (q - k - 1) + (k + 1 < p ? 1 : 0); break;
-    case K_LARFB: nsucc = (k + 1 < p) ? 1 : 0; break;
-    case K_TSQRT: nsucc = (q - k - 1) + (i + 1 < p ? 1 : 0); break;
-    default: nsucc = (i + 1 < p ? 1 : 0) + 1; break;
-    }
-    for (int s = threadIdx.x; s < nsucc; s += NT) {
-        int ks, is, js;
-        switch (kind) {
-        case K_GEQRT:
-            if (s < q - k - 1) { ks = k; is = k; js = k + 1 + s; }     // LARFB(k, j)
-            else { ks = k; is = k + 1; js = k; }                       // TSQRT(k+1, k)
-            break;
-        case K_LARFB:
-            ks = k; is = k + 1; js = j;                                // SSRFB(k+1, j, k)
-            break;
-        case K_TSQRT:
-            if (s < q - k - 1) { ks = k; is = i; js = k + 1 + s; }     // SSRFB(i, j, k)
-            else { ks = k; is = i + 1; js = k; }                       // TSQRT(i+1, k)
-            break;
-        default:
-            if (s == 0 && i + 1 < p) { ks = k; is = i + 1; js = j; }   // SSRFB(i+1, j, k)
-            else { ks = k + 1; is = i; js = j; }                       // next step on tile (i,j)
-            break;
-        }
-        const size_t idx = ((size_t)ks * p + is) * q + js;
-        q_signal(Q, idx, task_ndeps(is, js, ks), task_kind(is, js, ks), encode_task(ks, is, js));
-    }
-}
-
-template <int NB, int S>
-__global__ void __launch_bounds__(NT, F64Cfg<NB, S>::CTAS_PER_SM) k_factor_dag(FactorArgs F, Queues Q)
-{
-    extern __shared__ double sm[];
-    __shared__ unsigned long long s_code;
-    __shared__ int s_cmd;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (ld_relaxed_s32(&Q.ctrl->nonfinite) != 0)
-            atomicCAS(&Q.ctrl->error, 0, TILEQR_ERR_NONFINITE);
-        else
-            q_push(Q, K_GEQRT, encode_task(0, 0, 0));
-    }
-    for (;;) {
-        if (threadIdx.x == 0)
-            s_cmd = q_acquire(Q, s_code);
-        __syncthreads();
-        if (s_cmd != CMD_RUN)
-            break;
-        int k, i, j;
-        decode_task(s_code, k, i, j);
-        const unsigned long long t0 = Q.trace ? globaltimer_ns() : 0ull;
-        run_factor_task<NB, S>(sm, F, k, i, j);
-        __syncthreads();
-        release_factor(Q, F, k, i, j);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (Q.trace)
-                trace_record(Q, encode_task(k, i, j), t0, globaltimer_ns());
-            __threadfence();
-            atomicAdd(&Q.ctrl->completed, 1u);
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Fork-join comparator: per step k the host launches GEQRT, then the LARFB
@@ -170,7 +59,7 @@ static int launch_factor_t(const WsLayout &L, char *ws, int schedule, int flags,
     static bool attr_done = false;
     static int grid_dag = 0;
     if (!attr_done) {
-        cudaFuncSetAttribute(k_factor_dag<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_factor_dag<NB, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_bulk_geqrt<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_bulk_larfb<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_bulk_tsqrt<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -178,7 +67,7 @@ static int launch_factor_t(const WsLayout &L, char *ws, int schedule, int flags,
         int dev = 0, nsm = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_dag<NB, S>, NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_dag<NB, S, false>, NT, smem);
         if (per_sm < 1)
             return TILEQR_ERR_CUDA;
         grid_dag = nsm * per_sm;
@@ -210,7 +99,7 @@ static int launch_factor_t(const WsLayout &L, char *ws, int schedule, int flags,
         int grid = grid_dag;
         if ((unsigned)grid > L.total)
             grid = (int)L.total;
-        k_factor_dag<NB, S><<<grid, NT, smem, st>>>(F, Q);
+        k_factor_dag<NB, S, false><<<grid, NT, smem, st>>>(F, Q);
         count_launch();
     } else {
         for (int k = 0; k < L.steps; k++) {
@@ -265,11 +154,11 @@ static int launch_factor_dag_at_t(const WsLayout &L, double *tiles, double *T, c
     constexpr size_t smem = F64Cfg<NB, S>::SMEM;
     static int grid_dag = 0;
     if (grid_dag == 0) {
-        cudaFuncSetAttribute(k_factor_dag<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_factor_dag<NB, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int dev = 0, nsm = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_dag<NB, S>, NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_dag<NB, S, false>, NT, smem);
         if (per_sm < 1 || cudaGetLastError() != cudaSuccess)
             return TILEQR_ERR_CUDA;
         grid_dag = nsm * per_sm;
@@ -295,7 +184,7 @@ static int launch_factor_dag_at_t(const WsLayout &L, double *tiles, double *T, c
     int grid = grid_dag;
     if ((unsigned)grid > L.total)
         grid = (int)L.total;
-    k_factor_dag<NB, S><<<grid, NT, smem, st>>>(F, Q);
+    k_factor_dag<NB, S, false><<<grid, NT, smem, st>>>(F, Q);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
 }

@@ -7,6 +7,12 @@
 namespace tqr {
 
 bool factor_supported(int nb, int ib);
+bool factor_mixed_supported(int nb, int ib);
+
+// Mixed-precision (TILEQR_TF32) factorization of the tiles in the workspace:
+// the persistent task-graph kernel with DLARFB/DSSRFB on the tensor cores.
+int launch_factor_mixed(const WsLayout &L, char *ws, int flags, cudaStream_t st, unsigned long long watchdog_ns,
+                        unsigned long long *trace, unsigned int trace_cap);
 
 // Launch the factorization of the tiles already in the workspace.
 int launch_factor(const WsLayout &L, char *ws, int schedule, int flags, cudaStream_t st,

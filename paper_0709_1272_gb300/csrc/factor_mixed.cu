@@ -1,0 +1,69 @@
+// factor_mixed.cu -- the mixed-precision build of the persistent task-graph
+// kernel (TILEQR_TF32): DLARFB / DSSRFB as 3xTF32 products on the tcgen05
+// tensor cores with FP32 accumulation, DGEQRT / DTSQRT in FP64 (nb = 128).
+#include "dag.cuh"
+#include "factor.h"
+
+namespace tqr {
+
+template <int S>
+static int launch_factor_mixed_t(const WsLayout &L, char *ws, int flags, cudaStream_t st,
+                                 unsigned long long watchdog_ns, unsigned long long *trace, unsigned int trace_cap)
+{
+    constexpr int NB = 128;
+    constexpr size_t smem = DagCfg<NB, S, true>::SMEM;
+    static int grid_dag = 0;
+    if (grid_dag == 0) {
+        cudaFuncSetAttribute(k_factor_dag<NB, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0, nsm = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_dag<NB, S, true>, NT, smem);
+        if (per_sm < 1 || cudaGetLastError() != cudaSuccess)
+            return TILEQR_ERR_CUDA;
+        // one CTA per SM: each holds 256 of the SM's 512 tensor-memory columns
+        grid_dag = nsm;
+    }
+    FactorArgs F;
+    F.tiles = (double *)(ws + L.off_tiles);
+    F.T = (double *)(ws + L.off_T);
+    F.p = L.p;
+    F.q = L.q;
+    F.steps = L.steps;
+    Queues Q;
+    Q.ctrl = (SchedCtrl *)(ws + L.off_ctrl);
+    Q.cnt = (unsigned int *)(ws + L.off_cnt);
+    for (int t = 0; t < K_NKIND; t++) {
+        Q.slot[t] = (unsigned long long *)(ws + L.off_q[t]);
+        Q.cap[t] = L.cap[t];
+    }
+    Q.total = L.total;
+    Q.watchdog_ns = watchdog_ns;
+    Q.withheld = ~0ull;
+    if (flags & TILEQR_FLAG_TEST_WITHHOLD_LAST_TASK)
+        Q.withheld = encode_task(L.steps - 1, L.steps - 1, L.steps - 1);
+    Q.trace = trace;
+    Q.trace_cap = trace_cap;
+    int grid = grid_dag;
+    if ((unsigned)grid > L.total)
+        grid = (int)L.total;
+    k_factor_dag<NB, S, true><<<grid, NT, smem, st>>>(F, Q);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
+}
+
+bool factor_mixed_supported(int nb, int ib) { return nb == 128 && (ib == 16 || ib == 32); }
+
+int launch_factor_mixed(const WsLayout &L, char *ws, int flags, cudaStream_t st, unsigned long long watchdog_ns,
+                        unsigned long long *trace, unsigned int trace_cap)
+{
+    if (L.nb != 128)
+        return TILEQR_ERR_UNSUPPORTED;
+    if (L.ib == 16)
+        return launch_factor_mixed_t<16>(L, ws, flags, st, watchdog_ns, trace, trace_cap);
+    if (L.ib == 32)
+        return launch_factor_mixed_t<32>(L, ws, flags, st, watchdog_ns, trace, trace_cap);
+    return TILEQR_ERR_UNSUPPORTED;
+}
+
+}  // namespace tqr

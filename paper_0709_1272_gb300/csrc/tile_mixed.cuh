@@ -1,0 +1,308 @@
+// tile_mixed.cuh -- mixed-precision DSSRFB / DLARFB on the tcgen05 tensor
+// cores (nb = 128), for the TILEQR_TF32 precision mode.
+//
+// The tiles stay FP64.  One update task computes, with V the task's
+// reflectors (b x b: the full DTSQRT tile, or the unit-lower DGEQRT tile),
+// T_l its s x s T blocks, B the top tile's rows (DSSRFB only) and C the
+// updated tile:
+//   P = V^T C,  G = V^T V                       (tcgen05, K = 128)
+//   W_l = T_l^T (B_l + P_l - G_{l,<l} W_{<l}),  l = 0..t-1   (FP32, CUDA cores)
+//   B -= W (FP64),  D = V W (tcgen05),  C -= D (FP64)
+// This is the inner-blocked application of Sec. 3.2.3 (blocks applied in
+// order, each with its own T_l) reassociated so that the block recurrence
+// only touches s x b panels: Y_l = B_l + V_l^T (C - sum_{l'<l} V_l' W_l')
+// = B_l + P_l - sum_{l'<l} (V_l^T V_l') W_l'.  For DSSRFB, V = [I; V_A]
+// and the identity parts of distinct blocks are orthogonal, so G = V_A^T V_A.
+//
+// Products: 3xTF32 (x = hi + lo, hi*hi + hi*lo + lo*hi), FP32 accumulation
+// in tensor memory.  FP64 <-> FP32 conversions use integer bit operations
+// (the F2F instructions run at the FP64 rate on GB300, ~2/clk/SM).
+#pragma once
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace tqr {
+
+template <int S>
+struct MixCfg {
+    static constexpr int NB = 128;
+    static constexpr int KC = 32;                    // K extent of a staged operand chunk
+    static constexpr int OPB = NB * KC * 4;          // one 128 x 32 tf32 operand: 16 KB
+    static constexpr int LDF = NB + 1;               // ld of the FP32 128 x 128 panels
+    static constexpr int OFF_AHI = 0;
+    static constexpr int OFF_ALO = OPB;
+    static constexpr int OFF_BHI = 2 * OPB;
+    static constexpr int OFF_BLO = 3 * OPB;
+    static constexpr int OFF_PW = 4 * OPB;                          // P, then W (FP32)
+    static constexpr int OFF_G = OFF_PW + NB * LDF * 4;             // G (FP32)
+    static constexpr int OFF_T = OFF_G + NB * LDF * 4;              // T strip (FP32, s x 128)
+    static constexpr int SMEM = OFF_T + S * NB * 4;
+    static constexpr int TMEM_COLS = 256;                           // P / D at 0, G at 128
+    static_assert(S == 16 || S == 32, "ib 16 or 32");
+    static_assert(SMEM <= 232448, "shared memory budget");
+};
+
+// FP64 -> FP32 with integer operations: exponent rebias, mantissa funnel
+// shift, round half away from zero; |x| below the FP32 normal range flushes
+// to a signed zero, above it (or Inf/NaN) saturates to a signed infinity.
+__device__ __forceinline__ float f64_to_f32_bits(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    const uint32_t sgn = hi & 0x80000000u;
+    uint32_t f = __funnelshift_l(lo, hi - 0x38000000u, 3);   // ((hi - (896 << 20)) << 3) | (lo >> 29)
+    f = (f & 0x7FFFFFFFu) | sgn;
+    f += (lo >> 28) & 1u;
+    f = (e < 897u) ? sgn : f;
+    f = (e > 1150u) ? (sgn | 0x7F800000u) : f;
+    return __uint_as_float(f);
+}
+
+// FP32 -> FP64 (exact) with integer operations; zeros and FP32 denormals map
+// to a signed zero (finite inputs assumed).
+__device__ __forceinline__ double f32_to_f64_bits(float v)
+{
+    const uint32_t f = __float_as_uint(v);
+    const uint32_t sgn = f & 0x80000000u;
+    uint32_t hi = sgn | (((f & 0x7FFFFFFFu) >> 3) + 0x38000000u);
+    uint32_t lo = f << 29;
+    const bool zero = (f & 0x7F800000u) == 0u;
+    hi = zero ? sgn : hi;
+    lo = zero ? 0u : lo;
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
+// Element (trow, tcol) of a reflector tile; UNIT: a DGEQRT tile, whose
+// reflectors are unit lower triangular (zeros above the diagonal, implicit
+// ones on it; R occupies the upper part of the stored tile).
+template <bool UNIT>
+__device__ __forceinline__ double mixed_v_elem(const double *Vt, int trow, int tcol)
+{
+    if (UNIT) {
+        if (trow < tcol)
+            return 0.0;
+        if (trow == tcol)
+            return 1.0;
+    }
+    return ldcg(Vt + (size_t)tcol * 128 + trow);
+}
+
+// Split four FP32 values (consecutive K of one operand row) and store them
+// as one 16-byte vector in each of the hi and lo operand buffers.
+__device__ __forceinline__ void store_split4(unsigned char *sm, int off_hi, int off_lo, uint32_t byte_off,
+                                             float x0, float x1, float x2, float x3)
+{
+    float4 h, l;
+    tc::split_tf32(x0, h.x, l.x);
+    tc::split_tf32(x1, h.y, l.y);
+    tc::split_tf32(x2, h.z, l.z);
+    tc::split_tf32(x3, h.w, l.w);
+    *(float4 *)(sm + off_hi + byte_off) = h;
+    *(float4 *)(sm + off_lo + byte_off) = l;
+}
+
+// One MMA round: make the staged operands visible to the tensor core, issue
+// the products from thread 0, commit, and wait (bounded).  Returns false
+// (and records an error) if the wait gives up.
+template <typename IssueFn>
+__device__ __forceinline__ bool mixed_mma_round(uint64_t *mbar, uint32_t &phase, int *err, IssueFn issue)
+{
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x == 0) {
+        issue();
+        tc::commit(mbar);
+    }
+    const bool ok = tc::mbar_wait(mbar, phase);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!ok && threadIdx.x == 0)
+        atomicCAS(err, 0, TILEQR_ERR_TIMEOUT);
+    return ok;
+}
+
+// Mixed DSSRFB (Bt != nullptr, V = full DTSQRT tile) or DLARFB (Bt ==
+// nullptr, V = unit-lower DGEQRT tile) on FP64 tiles.  Returns false on a
+// tensor-core wait timeout (an error is recorded; the tile contents are then
+// undefined).
+template <int S, bool UNIT>
+__device__ __noinline__ bool task_update_mixed(unsigned char *sm, double *Bt, double *Ct, const double *Vt,
+                                               const double *Tt, uint32_t tmem, uint64_t *mbar, uint32_t &phase,
+                                               int *err)
+{
+    using M = MixCfg<S>;
+    constexpr int NB = 128, KC = M::KC, LDF = M::LDF, T_ = NB / S;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float *PW = (float *)(sm + M::OFF_PW);
+    float *GS = (float *)(sm + M::OFF_G);
+    float *TS = (float *)(sm + M::OFF_T);
+    const uint32_t sbase = tc::smem_addr(sm);
+    const uint32_t idesc = tc::idesc_tf32(128, 128);
+    const uint32_t SBO = KC * 32, LBO = 128;
+
+    // ---- phase 1: P = V^T C and G = V^T V, K (tile rows) in chunks of 32
+    for (int r0 = 0; r0 < NB; r0 += KC) {
+        // unit u: operand row m (reflector a for A, tile column c for B), K = tile
+        // rows r0 + 4j .. +3; 8 lanes cover 32 contiguous doubles of one column
+        for (int u = tid; u < NB * (KC / 4); u += NT) {
+            const int j = u & 7, m = u >> 3, r = r0 + 4 * j;
+            const uint32_t off = tc::kmajor_off(m, 4 * j, KC);
+            store_split4(sm, M::OFF_AHI, M::OFF_ALO, off, f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r, m)),
+                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r + 1, m)),
+                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r + 2, m)),
+                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r + 3, m)));
+            const double *cp = Ct + (size_t)m * NB + r;
+            store_split4(sm, M::OFF_BHI, M::OFF_BLO, off, f64_to_f32_bits(ldcg(cp)), f64_to_f32_bits(ldcg(cp + 1)),
+                         f64_to_f32_bits(ldcg(cp + 2)), f64_to_f32_bits(ldcg(cp + 3)));
+        }
+        const uint32_t acc0 = r0 > 0 ? 1u : 0u;
+        const bool ok = mixed_mma_round(mbar, phase, err, [&]() {
+            for (int ks = 0; ks < KC / 8; ks++) {
+                const uint32_t o = ks * 256;
+                const uint64_t ah = tc::smem_desc(sbase + M::OFF_AHI + o, LBO, SBO);
+                const uint64_t al = tc::smem_desc(sbase + M::OFF_ALO + o, LBO, SBO);
+                const uint64_t bh = tc::smem_desc(sbase + M::OFF_BHI + o, LBO, SBO);
+                const uint64_t bl = tc::smem_desc(sbase + M::OFF_BLO + o, LBO, SBO);
+                const uint32_t acc = (acc0 | (uint32_t)ks) ? 1u : 0u;
+                tc::mma_tf32(tmem, ah, bh, idesc, acc);          // P
+                tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+                tc::mma_tf32(tmem, al, bh, idesc, 1u);
+                tc::mma_tf32(tmem + 128, ah, ah, idesc, acc);    // G
+                tc::mma_tf32(tmem + 128, ah, al, idesc, 1u);
+                tc::mma_tf32(tmem + 128, al, ah, idesc, 1u);
+            }
+        });
+        if (!ok)
+            return false;
+    }
+
+    // ---- phase 2: P, G to shared memory; T strip to FP32; W recurrence
+    {
+        const int row = 32 * (warp & 3) + lane;
+        const int cbase = (warp >> 2) * 64;
+        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+        for (int h = 0; h < 2; h++) {
+            float v[32];
+            tc::tmem_ld32(tmem + lane_off + cbase + 32 * h, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                PW[row * LDF + cbase + 32 * h + j] = v[j];
+            tc::tmem_ld32(tmem + 128 + lane_off + cbase + 32 * h, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                GS[row * LDF + cbase + 32 * h + j] = v[j];
+        }
+    }
+    for (int idx = tid; idx < S * NB; idx += NT)
+        TS[idx] = f64_to_f32_bits(ldcg(Tt + idx));
+    tc::fence_before_sync();
+    __syncthreads();
+
+    {
+        const int c = tid & (NB - 1);
+        const int half = tid >> 7;
+        constexpr int HR = S / 2;   // rows of a block per thread
+        for (int l = 0; l < T_; l++) {
+            const int a0 = l * S + half * HR;
+            const int kdone = l * S;   // rows of W already final
+            float y[HR];
+            double bv[HR];
+#pragma unroll
+            for (int i = 0; i < HR; i++) {
+                bv[i] = Bt ? ldcg(Bt + (size_t)c * NB + a0 + i) : 0.0;
+                y[i] = PW[(a0 + i) * LDF + c] + (Bt ? f64_to_f32_bits(bv[i]) : 0.0f);
+            }
+            for (int ap = 0; ap < kdone; ap += 4) {
+                const float w0 = PW[(ap + 0) * LDF + c], w1 = PW[(ap + 1) * LDF + c];
+                const float w2 = PW[(ap + 2) * LDF + c], w3 = PW[(ap + 3) * LDF + c];
+#pragma unroll
+                for (int i = 0; i < HR; i++) {
+                    const float *g = GS + (a0 + i) * LDF + ap;
+                    y[i] = fmaf(-g[0], w0, y[i]);
+                    y[i] = fmaf(-g[1], w1, y[i]);
+                    y[i] = fmaf(-g[2], w2, y[i]);
+                    y[i] = fmaf(-g[3], w3, y[i]);
+                }
+            }
+            // Y_l rows go into PW (P_l is consumed), then W_l = T_l^T Y_l
+#pragma unroll
+            for (int i = 0; i < HR; i++)
+                PW[(a0 + i) * LDF + c] = y[i];
+            __syncthreads();
+            float w[HR];
+#pragma unroll
+            for (int i = 0; i < HR; i++) {
+                const int a = half * HR + i;   // row within the block
+                float acc = 0.0f;
+                for (int a2 = 0; a2 <= a; a2++)
+                    acc = fmaf(TS[(l * S + a) * S + a2], PW[(l * S + a2) * LDF + c], acc);
+                w[i] = acc;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < HR; i++) {
+                PW[(a0 + i) * LDF + c] = w[i];
+                if (Bt)
+                    stcg(Bt + (size_t)c * NB + a0 + i, bv[i] - f32_to_f64_bits(w[i]));
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- phase 3: D = V W, K (reflectors) in chunks of 32
+    for (int k0 = 0; k0 < NB; k0 += KC) {
+        // unit u: operand row r (tile row for A, tile column c = r for B),
+        // K = reflectors k0 + 4j .. +3; lanes run over consecutive rows
+        for (int u = tid; u < NB * (KC / 4); u += NT) {
+            const int r = u & (NB - 1), j = u >> 7, k = k0 + 4 * j;
+            const uint32_t off = tc::kmajor_off(r, 4 * j, KC);
+            store_split4(sm, M::OFF_AHI, M::OFF_ALO, off, f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r, k)),
+                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r, k + 1)),
+                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r, k + 2)),
+                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r, k + 3)));
+            // B operand (column c = r, reflector k) = W[k][c]
+            store_split4(sm, M::OFF_BHI, M::OFF_BLO, off, PW[k * LDF + r], PW[(k + 1) * LDF + r],
+                         PW[(k + 2) * LDF + r], PW[(k + 3) * LDF + r]);
+        }
+        const uint32_t acc0 = k0 > 0 ? 1u : 0u;
+        const bool ok = mixed_mma_round(mbar, phase, err, [&]() {
+            for (int ks = 0; ks < KC / 8; ks++) {
+                const uint32_t o = ks * 256;
+                const uint64_t ah = tc::smem_desc(sbase + M::OFF_AHI + o, LBO, SBO);
+                const uint64_t al = tc::smem_desc(sbase + M::OFF_ALO + o, LBO, SBO);
+                const uint64_t bh = tc::smem_desc(sbase + M::OFF_BHI + o, LBO, SBO);
+                const uint64_t bl = tc::smem_desc(sbase + M::OFF_BLO + o, LBO, SBO);
+                const uint32_t acc = (acc0 | (uint32_t)ks) ? 1u : 0u;
+                tc::mma_tf32(tmem, ah, bh, idesc, acc);
+                tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+                tc::mma_tf32(tmem, al, bh, idesc, 1u);
+            }
+        });
+        if (!ok)
+            return false;
+    }
+
+    // ---- phase 4: C -= D (FP64), row r = TMEM lane
+    {
+        const int r = 32 * (warp & 3) + lane;
+        const int cbase = (warp >> 2) * 64;
+        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+        for (int h = 0; h < 2; h++) {
+            float v[32];
+            tc::tmem_ld32(tmem + lane_off + cbase + 32 * h, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                double *p = Ct + (size_t)(cbase + 32 * h + j) * NB + r;
+                stcg(p, ldcg(p) - f32_to_f64_bits(v[j]));
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    return true;
+}
+
+}  // namespace tqr
