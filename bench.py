@@ -184,6 +184,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-n", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision + FP64 refinement measurement")
+    ap.add_argument("--kappa", type=float, default=1e6)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -295,6 +298,52 @@ def main():
                "steps": args.e2e_steps,
                "path": "pinned host A -> cudaMemcpyAsync -> tileqr_factor -> tileqr_get_R -> pinned host R"}
 
+    # ---- mixed precision (tcgen05 updates) + FP64 iterative refinement of the
+    # solve A x = b, A = (I-2uu^T) diag(s) (I-2vv^T), cond(A) = kappa, same size
+    mixed = None
+    if not args.no_mixed and m == n and nb == 128:
+        del ws
+        torch.cuda.empty_cache()
+        Ak, _, _, _ = inputs.kappa_matrix(n, args.kappa, seed=20070709 + 4 + 1000 * rank)
+        xt = inputs.normal_matrix(n, 1, seed=20070709 + 5).reshape(-1)
+        bk = torch.from_numpy(Ak @ xt).to(dev)
+        Akd = tileqr.to_device_colmajor(Ak, dev)
+        del Ak
+        wsm = torch.empty(tileqr.tileqr_workspace_size(m, n, nb, ib, tileqr.TILEQR_TF32), dtype=torch.uint8,
+                          device=dev)
+        steps_m = max(2, min(args.steps, 3))
+        fac_t, ref_t, infos = [], [], []
+        for it in range(1 + steps_m):
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fm = tileqr.tileqr_factor(Akd, nb, ib, precision=tileqr.TILEQR_TF32, workspace=wsm)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            xk, info = fm.solve_refine(Akd, bk, max_iter=40, tol=1e-12)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            if it > 0:
+                fac_t.append(t1 - t0)
+                ref_t.append(t2 - t1)
+                infos.append(info.as_dict())
+        assert fm.status() == 0
+        tm = statistics.mean([a + b for a, b in zip(fac_t, ref_t)])
+        if dist is not None:
+            t = torch.tensor([tm], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tm = float(t.item())
+        mixed = {"workload": f"TF32-update tile QR + FP64 refinement of A x = b, {m}x{n}, "
+                             f"A = (I-2uu^T) diag(s) (I-2vv^T), cond {args.kappa:.0e}, nb={nb}, ib={ib}",
+                 "value": world * ops / tm / 1e9, "unit": UNIT, "ms_per_step": tm * 1e3,
+                 "factor_ms": statistics.mean(fac_t) * 1e3, "refine_ms": statistics.mean(ref_t) * 1e3,
+                 "steps": steps_m, "rel_residual": max(i["rel_residual"] for i in infos),
+                 "refine_iterations": infos[-1]["iterations"], "refine_method":
+                     {1: "classical", 2: "flexible GMRES"}.get(infos[-1]["method"], "none"),
+                 "initial_rel_residual": infos[-1]["initial_rel_residual"],
+                 "speedup_vs_fp64_factorization": (world * ops / tm / 1e9) / value,
+                 "timing": "wall clock around factor+refine (the refinement synchronises), max over ranks"}
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -329,6 +378,8 @@ def main():
     }
     if e2e:
         out["e2e"] = e2e
+    if mixed:
+        out["mixed_ls"] = mixed
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(nb, ib)
     print(json.dumps(out), flush=True)

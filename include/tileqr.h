@@ -191,6 +191,40 @@ int tileqr_apply_qt(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, 
 int tileqr_solve_ls(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
                     size_t ws_bytes, tileqr_stream_t stream);
 
+/* Outcome of tileqr_solve_refine. */
+typedef struct tileqr_refine_info {
+    int iterations;             /* refinement steps taken */
+    int inner_iterations;       /* GMRES iterations in total (method 2) */
+    int method;                 /* 1 = classical refinement, 2 = flexible GMRES-IR */
+    int converged;              /* rel_residual <= tol */
+    double initial_rel_residual; /* ||b - A x0|| / ||b||, x0 from the factors alone */
+    double rel_residual;        /* final ||b - A x|| / ||b|| (FP64) */
+} tileqr_refine_info;
+
+/* Bytes of workspace tileqr_solve_refine needs for the factorization d. */
+int tileqr_refine_workspace_size(const tileqr_desc *d, size_t *bytes);
+
+/* Solve A x = b (square, or tall and consistent: m >= n) to relative
+ * residual ||b - A x||_2 / ||b||_2 <= tol with FP64 iterative refinement on
+ * top of a factorization d of A (nb 128; any precision, meant for
+ * TILEQR_TF32).  The correction solves use an FP32 copy of the factors
+ * (Q^T applied as the task graph of Algorithm 2 on one column, R^{-1} by a
+ * tiled back substitution with inverted diagonal tiles); residuals, x and the
+ * Krylov vectors are FP64.  Classical refinement x += M^{-1} r runs first; if
+ * it stops converging (kappa(A) u_factor not small) the remaining steps are
+ * restarted flexible GMRES(40) on A d = r with M^{-1} as right
+ * preconditioner.  This mixed-precision refinement is an addition to the
+ * paper's method (it is not in the paper).
+ *   A, lda   the original matrix (device, column-major, FP64)
+ *   b        device, m entries;   x  device, n entries (output)
+ *   max_iter refinement steps (outer iterations) at most
+ * Synchronous.  Returns 0 (also when not converged: see info), -i,
+ * TILEQR_ERR_SINGULAR, TILEQR_ERR_WORKSPACE, TILEQR_ERR_UNSUPPORTED,
+ * TILEQR_ERR_CUDA. */
+int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_t lda, const double *b, double *x,
+                        int max_iter, double tol, void *workspace, size_t ws_bytes, tileqr_stream_t stream,
+                        tileqr_refine_info *info);
+
 /* Human-readable text for a return code (static storage). */
 const char *tileqr_strerror(int code);
 

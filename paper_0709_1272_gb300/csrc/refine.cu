@@ -1,0 +1,698 @@
+// refine.cu -- least-squares solve with FP64 iterative refinement for the
+// mixed-precision factorization (square or tall A, one right-hand side).
+//
+// The correction solves use an FP32 copy of the factors: M^{-1} v =
+// R^{-1} (Q^T v)(0:n) with Q^T applied as the task graph of Algorithm 2
+// restricted to one column (DLARFB / DSSRFB on vectors, single precision) and
+// R^{-1} as a tiled back substitution with precomputed inverses of R's
+// diagonal tiles.  Residuals r = b - A x, the Krylov vectors and x are FP64.
+// Classical refinement (x += M^{-1} r) is tried first; if the residual stops
+// shrinking, the solve continues with restarted flexible GMRES on A d = r
+// with M^{-1} as the right preconditioner (GMRES-IR).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "factor.h"
+#include "sched.cuh"
+#include "tile_mixed.cuh"
+
+namespace tqr {
+
+// ---------------------------------------------------------------------------
+// FP64 -> FP32 copies of the tiles and T strips (integer conversion).
+__global__ void k_to_f32(const double *__restrict__ src, float *__restrict__ dst, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = f64_to_f32_bits(src[i]);
+}
+
+// Inverse of the upper triangle of diagonal tile j (nb = 128), written as
+// FP32 tile Rinv_j (column-major).  Padded columns (beyond n) get a zero
+// column and row.  One CTA per tile, thread c computes column c of the
+// inverse by back substitution in FP64.
+__global__ void __launch_bounds__(128) k_inv_diag(const double *__restrict__ tiles, int p, int q, int64_t n,
+                                                  float *__restrict__ rinv, int *singular)
+{
+    extern __shared__ double U[];   // 128 x 129, [r][c] row-major padded
+    double *rcp = U + 128 * 129;
+    const int j = blockIdx.x, c = threadIdx.x;
+    const double *T = tiles + ((size_t)j * p + j) * 128 * 128;
+    for (int idx = c; idx < 128 * 128; idx += 128) {
+        const int cc = idx >> 7, r = idx & 127;
+        U[r * 129 + cc] = ldcg(T + idx);
+    }
+    __syncthreads();
+    const int nvalid = (int)((n - (int64_t)j * 128) < 128 ? (n - (int64_t)j * 128) : 128);
+    if (c < nvalid) {
+        const double d = U[c * 129 + c];
+        if (d == 0.0)
+            atomicCAS(singular, 0, j * 128 + c + 1);
+        rcp[c] = d != 0.0 ? 1.0 / d : 0.0;
+    } else {
+        rcp[c] = 0.0;
+    }
+    __syncthreads();
+    // column c of X = U^{-1}: X(c,c) = 1/U(c,c); X(r,c) = -(sum_{k=r+1..c} U(r,k) X(k,c)) / U(r,r)
+    double x[128];
+#pragma unroll 1
+    for (int r = 0; r < 128; r++)
+        x[r] = 0.0;
+    float *out = rinv + (size_t)j * 128 * 128 + (size_t)c * 128;
+    if (c < nvalid) {
+        x[c] = rcp[c];
+#pragma unroll 1
+        for (int r = c - 1; r >= 0; r--) {
+            double acc = 0.0;
+#pragma unroll 1
+            for (int k = r + 1; k <= c; k++)
+                acc = fma(U[r * 129 + k], x[k], acc);
+            x[r] = -acc * rcp[r];
+        }
+    }
+#pragma unroll 1
+    for (int r = 0; r < 128; r++)
+        out[r] = f64_to_f32_bits(x[r]);
+}
+
+// ---------------------------------------------------------------------------
+// Q^T v in FP32 for single columns: the task graph LB(k) / SB(i,k) per
+// column (same dependencies as the FP64 apply), one 128-thread CTA per task.
+struct Apply32Args {
+    const float *tiles;   // FP32 copy of the factored tiles
+    const float *T;       // FP32 copy of the T strips
+    float *X;             // p row blocks of 128 x ncol (ld 128)
+    int p, steps, ncol, S;
+};
+
+__global__ void __launch_bounds__(128) k_apply32_dag(Apply32Args A, Queues Q)
+{
+    __shared__ float Vs[128 * 33];   // V_l as [r][a], ld s+1 (s <= 32)
+    __shared__ float Ts[32 * 32];
+    __shared__ float xk[128], xi[128];
+    __shared__ float part[4][32];
+    __shared__ float yw[32];
+    __shared__ unsigned long long s_code;
+    __shared__ int s_cmd;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int S = A.S;
+    if (blockIdx.x == 0)
+        for (int c = tid; c < A.ncol; c += 128)
+            q_push(Q, 0, encode_task(0, 0, c));
+    for (;;) {
+        if (tid == 0)
+            s_cmd = q_acquire(Q, s_code);
+        __syncthreads();
+        if (s_cmd != CMD_RUN)
+            break;
+        int k, i, col;
+        decode_task(s_code, k, i, col);
+        const bool lb = (i == k);
+        const float *Vt = A.tiles + ((size_t)k * A.p + i) * 128 * 128;
+        const float *Tt = A.T + ((size_t)k * A.p + i) * (size_t)S * 128;
+        float *gxk = A.X + ((size_t)k * A.ncol + col) * 128;
+        float *gxi = A.X + ((size_t)i * A.ncol + col) * 128;
+        // other CTAs write these blocks in this launch: read them from L2
+        xk[tid] = __ldcg(gxk + tid);
+        if (!lb)
+            xi[tid] = __ldcg(gxi + tid);
+        for (int l0 = 0; l0 < 128; l0 += S) {
+            __syncthreads();
+            for (int idx = tid; idx < 128 * S; idx += 128) {
+                const int a = idx >> 7, r = idx & 127;
+                const int jj = l0 + a;
+                float v = Vt[(size_t)jj * 128 + r];
+                if (lb)
+                    v = (r < jj) ? 0.0f : (r == jj ? 1.0f : v);
+                Vs[r * 33 + a] = v;
+            }
+            for (int idx = tid; idx < S * S; idx += 128)
+                Ts[idx] = Tt[(size_t)l0 * S + idx];
+            __syncthreads();
+            // y(a) = [x_k(l0+a)] + sum_r V(r,a) x(r)   (x = x_i for SB, x_k for LB)
+            const float *xv = lb ? xk : xi;
+            float acc = 0.0f;
+            if (lane < S) {
+#pragma unroll 4
+                for (int r = warp * 32; r < warp * 32 + 32; r++)
+                    acc = fmaf(Vs[r * 33 + lane], xv[r], acc);
+                part[warp][lane] = acc;
+            }
+            __syncthreads();
+            if (tid < S) {
+                float y = part[0][tid] + part[1][tid] + part[2][tid] + part[3][tid];
+                if (!lb)
+                    y += xk[l0 + tid];
+                yw[tid] = y;
+            }
+            __syncthreads();
+            float w = 0.0f;
+            if (tid < S)
+                for (int b = 0; b <= tid; b++)
+                    w = fmaf(Ts[tid * S + b], yw[b], w);
+            __syncthreads();
+            if (tid < S) {
+                yw[tid] = w;
+                if (!lb)
+                    xk[l0 + tid] -= w;
+            }
+            __syncthreads();
+            float d = 0.0f;
+            for (int a = 0; a < S; a++)
+                d = fmaf(Vs[tid * 33 + a], yw[a], d);
+            if (lb)
+                xk[tid] -= d;
+            else
+                xi[tid] -= d;
+        }
+        __syncthreads();
+        __stcg(gxk + tid, xk[tid]);
+        if (!lb)
+            __stcg(gxi + tid, xi[tid]);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            const size_t base = (size_t)A.ncol;
+            if (lb) {
+                if (k + 1 < A.p)
+                    q_signal(Q, ((size_t)k * A.p + k + 1) * base + col, 1 + (k > 0 ? 1 : 0), 1,
+                             encode_task(k, k + 1, col));
+            } else {
+                if (i + 1 < A.p)
+                    q_signal(Q, ((size_t)k * A.p + i + 1) * base + col, 1 + (k > 0 ? 1 : 0), 1,
+                             encode_task(k, i + 1, col));
+                if (k + 1 < A.steps) {
+                    if (i == k + 1)
+                        q_signal(Q, ((size_t)(k + 1) * A.p + i) * base + col, 1, 0, encode_task(k + 1, i, col));
+                    else
+                        q_signal(Q, ((size_t)(k + 1) * A.p + i) * base + col, 2, 1, encode_task(k + 1, i, col));
+                }
+            }
+            __threadfence();
+            atomicAdd(&Q.ctrl->completed, 1u);
+        }
+    }
+}
+
+// Tiled back substitution in FP32 with inverted diagonal tiles, for block
+// column j: x_j = Rinv_j y_j (one CTA per column), then y_i -= R_ij x_j
+// (one CTA per (i < j, column)).
+__global__ void __launch_bounds__(128) k_trsv32_diag(const float *__restrict__ rinv, float *X, int ncol, int j)
+{
+    __shared__ float y[128];
+    const int col = blockIdx.x, r = threadIdx.x;
+    float *xj = X + ((size_t)j * ncol + col) * 128;
+    y[r] = xj[r];
+    __syncthreads();
+    const float *Ri = rinv + (size_t)j * 128 * 128;
+    float acc0 = 0.0f, acc1 = 0.0f;
+    for (int c = 0; c < 128; c += 2) {
+        acc0 = fmaf(Ri[(size_t)c * 128 + r], y[c], acc0);
+        acc1 = fmaf(Ri[(size_t)(c + 1) * 128 + r], y[c + 1], acc1);
+    }
+    xj[r] = acc0 + acc1;
+}
+__global__ void __launch_bounds__(128) k_trsv32_update(const float *__restrict__ tiles, float *X, int p, int ncol,
+                                                       int j)
+{
+    __shared__ float x[128];
+    const int i = blockIdx.x, col = blockIdx.y, r = threadIdx.x;
+    x[r] = X[((size_t)j * ncol + col) * 128 + r];
+    __syncthreads();
+    const float *R = tiles + ((size_t)j * p + i) * 128 * 128;
+    float acc0 = 0.0f, acc1 = 0.0f;
+    for (int c = 0; c < 128; c += 2) {
+        acc0 = fmaf(R[(size_t)c * 128 + r], x[c], acc0);
+        acc1 = fmaf(R[(size_t)(c + 1) * 128 + r], x[c + 1], acc1);
+    }
+    X[((size_t)i * ncol + col) * 128 + r] -= acc0 + acc1;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 vector kernels.
+// r = b - A x  (A column-major m x n); one thread per row, columns split
+// across blockIdx.y with atomic accumulation into r (pre-set to b).
+__global__ void k_residual(const double *__restrict__ A, int64_t lda, int64_t m, int64_t n,
+                           const double *__restrict__ x, double *r, int64_t cols_per_block)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.y * cols_per_block;
+    const int64_t c1 = c0 + cols_per_block < n ? c0 + cols_per_block : n;
+    if (row >= m)
+        return;
+    double a0 = 0.0, a1 = 0.0;
+    int64_t c = c0;
+    for (; c + 1 < c1; c += 2) {
+        a0 = fma(A[c * lda + row], x[c], a0);
+        a1 = fma(A[(c + 1) * lda + row], x[c + 1], a1);
+    }
+    if (c < c1)
+        a0 = fma(A[c * lda + row], x[c], a0);
+    atomicAdd(r + row, -(a0 + a1));
+}
+
+// partial sums of x.y into out[blockIdx.x]
+__global__ void k_dot(const double *__restrict__ x, const double *__restrict__ y, int64_t n, double *out)
+{
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(x[i], y[i], acc);
+    acc = warp_allsum(acc);
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++)
+            s += red[w];
+        out[blockIdx.x] = s;
+    }
+}
+
+// y += alpha * x, alpha read from device memory (alpha_scale * *alpha_ptr)
+__global__ void k_axpy(double alpha, const double *__restrict__ x, double *y, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = fma(alpha, x[i], y[i]);
+}
+__global__ void k_scale_copy(double alpha, const double *__restrict__ x, double *y, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = alpha * x[i];
+}
+// FP64 vector (length m) -> FP32 row blocks X (p x 128, zero-padded), and back (first n rows)
+__global__ void k_vec_to_blocks(const double *__restrict__ v, int64_t m, float *X, int p)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)p * 128;
+         i += (int64_t)gridDim.x * blockDim.x)
+        X[i] = i < m ? f64_to_f32_bits(v[i]) : 0.0f;
+}
+__global__ void k_blocks_to_vec(const float *__restrict__ X, int64_t n, double *v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = f32_to_f64_bits(X[i]);
+}
+
+}  // namespace tqr
+
+// ---------------------------------------------------------------------------
+// Host side.
+namespace tqr {
+
+// multi-dot: out[c * nb + b] = partial over block b of V(:,c) . w
+__global__ void k_multidot(const double *__restrict__ V, int64_t ldv, int ncols, const double *__restrict__ w,
+                           int64_t n, double *out)
+{
+    __shared__ double red[8];
+    for (int c = 0; c < ncols; c++) {
+        double acc = 0.0;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            acc = fma(V[(size_t)c * ldv + i], w[i], acc);
+        acc = warp_allsum(acc);
+        if ((threadIdx.x & 31) == 0)
+            red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int ww = 0; ww < (int)(blockDim.x >> 5); ww++)
+                s += red[ww];
+            out[(size_t)c * gridDim.x + blockIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+// w -= V h (h on the device, ncols entries)
+__global__ void k_multiaxpy(const double *__restrict__ V, int64_t ldv, int ncols, const double *__restrict__ h,
+                            double *w, int64_t n, double sign)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = w[i];
+        for (int c = 0; c < ncols; c++)
+            acc = fma(sign * h[c], V[(size_t)c * ldv + i], acc);
+        w[i] = acc;
+    }
+}
+
+namespace {
+
+constexpr int DOT_BLOCKS = 152;
+constexpr int GMRES_RESTART = 40;
+
+struct RefineLayout {
+    size_t tiles32, T32, rinv, X, sched, vecs, dots, flag, end;
+    size_t sched_bytes;
+    int64_t m, n;
+    int p, q, steps, S;
+};
+
+RefineLayout refine_layout(const tileqr_desc *d)
+{
+    RefineLayout R{};
+    R.m = d->m;
+    R.n = d->n;
+    R.p = d->p;
+    R.q = d->q;
+    R.steps = d->p < d->q ? d->p : d->q;
+    R.S = d->ib;
+    size_t off = 0;
+    R.tiles32 = off;
+    off += align256((size_t)d->p * d->q * 128 * 128 * 4);
+    R.T32 = off;
+    off += align256((size_t)d->p * d->q * d->ib * 128 * 4);
+    R.rinv = off;
+    off += align256((size_t)d->q * 128 * 128 * 4);
+    R.X = off;
+    off += align256((size_t)d->p * 128 * 4);
+    // scheduler of the one-column FP32 apply: control block, counters, 2 queues
+    const unsigned long long nlb = (unsigned long long)R.steps;
+    unsigned long long nsb = 0;
+    for (int k = 0; k < R.steps; k++)
+        nsb += (unsigned long long)(d->p - k - 1);
+    R.sched = off;
+    R.sched_bytes = 256 + align256((size_t)R.steps * d->p * 4) + align256((nlb ? nlb : 1) * 8) +
+                    align256((nsb ? nsb : 1) * 8);
+    off += R.sched_bytes;
+    // FP64 vectors: r (m), b copy (m), d (n), w (m), V (m x (restart+1)), Z (n x restart)
+    const int64_t mm = d->m > d->n ? d->m : d->n;
+    R.vecs = off;
+    off += align256((size_t)mm * 8 * (4 + (GMRES_RESTART + 1) + GMRES_RESTART));
+    R.dots = off;
+    off += align256((size_t)(GMRES_RESTART + 2) * DOT_BLOCKS * 8);
+    R.flag = off;
+    off += 256;
+    R.end = off;
+    return R;
+}
+
+struct Refiner {
+    const tileqr_desc *d;
+    RefineLayout L;
+    char *ws;
+    cudaStream_t st;
+    int grid_apply = 0;
+    const double *A;
+    int64_t lda;
+    double *r, *bc, *dv, *w, *V, *Z, *dots;
+    int64_t mm;
+    std::vector<double> hdots;
+
+    int gemv_residual(const double *x, double *out, const double *rhs, bool negate_only)
+    {
+        // out = rhs - A x   (rhs == nullptr: out = -A x)
+        if (rhs)
+            cudaMemcpyAsync(out, rhs, (size_t)L.m * 8, cudaMemcpyDeviceToDevice, st);
+        else
+            cudaMemsetAsync(out, 0, (size_t)L.m * 8, st);
+        // rows over threads (coalesced), columns over 8 blocks (8 atomics per row)
+        const int64_t cpb = (L.n + 7) / 8 > 0 ? (L.n + 7) / 8 : 1;
+        dim3 grid((unsigned)((L.m + 255) / 256), (unsigned)((L.n + cpb - 1) / cpb));
+        k_residual<<<grid, 256, 0, st>>>(A, lda, L.m, L.n, x, out, cpb);
+        count_launch();
+        (void)negate_only;
+        return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
+    }
+
+    double dot(const double *x, const double *y, int64_t n)
+    {
+        k_dot<<<DOT_BLOCKS, 256, 0, st>>>(x, y, n, dots);
+        count_launch();
+        double h[DOT_BLOCKS];
+        cudaMemcpyAsync(h, dots, sizeof(h), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        double s = 0.0;
+        for (int b = 0; b < DOT_BLOCKS; b++)
+            s += h[b];
+        return s;
+    }
+
+    // z (n, FP64) = R^{-1} (Q^T v)(0:n) with the FP32 factors; v has m entries
+    int precond(const double *v, double *z)
+    {
+        float *X = (float *)(ws + L.X);
+        k_vec_to_blocks<<<DOT_BLOCKS, 256, 0, st>>>(v, L.m, X, L.p);
+        count_launch();
+        // Q^T on one column
+        char *sched = ws + L.sched;
+        if (cudaMemsetAsync(sched, 0, L.sched_bytes, st) != cudaSuccess)
+            return TILEQR_ERR_CUDA;
+        Apply32Args a;
+        a.tiles = (const float *)(ws + L.tiles32);
+        a.T = (const float *)(ws + L.T32);
+        a.X = X;
+        a.p = L.p;
+        a.steps = L.steps;
+        a.ncol = 1;
+        a.S = L.S;
+        const size_t cnt_bytes = align256((size_t)L.steps * L.p * 4);
+        const unsigned long long nlb = (unsigned long long)L.steps;
+        unsigned long long nsb = 0;
+        for (int k = 0; k < L.steps; k++)
+            nsb += (unsigned long long)(L.p - k - 1);
+        Queues Q;
+        Q.ctrl = (SchedCtrl *)sched;
+        Q.cnt = (unsigned int *)(sched + 256);
+        Q.slot[0] = (unsigned long long *)(sched + 256 + cnt_bytes);
+        Q.slot[1] = (unsigned long long *)(sched + 256 + cnt_bytes + align256((nlb ? nlb : 1) * 8));
+        Q.slot[2] = Q.slot[3] = nullptr;
+        Q.cap[0] = (unsigned int)nlb;
+        Q.cap[1] = (unsigned int)nsb;
+        Q.cap[2] = Q.cap[3] = 0;
+        Q.total = (unsigned int)(nlb + nsb);
+        Q.watchdog_ns = 10000ull * 1000000ull;
+        Q.withheld = ~0ull;
+        Q.trace = nullptr;
+        Q.trace_cap = 0;
+        int grid = grid_apply;
+        if ((unsigned)grid > Q.total)
+            grid = (int)Q.total;
+        if (grid > 0) {
+            k_apply32_dag<<<grid, 128, 0, st>>>(a, Q);
+            count_launch();
+        }
+        // R^{-1} on the first q blocks
+        const float *rinv = (const float *)(ws + L.rinv);
+        const float *t32 = (const float *)(ws + L.tiles32);
+        for (int j = L.q - 1; j >= 0; j--) {
+            k_trsv32_diag<<<1, 128, 0, st>>>(rinv, X, 1, j);
+            count_launch();
+            if (j > 0) {
+                k_trsv32_update<<<dim3(j, 1), 128, 0, st>>>(t32, X, L.p, 1, j);
+                count_launch();
+            }
+        }
+        k_blocks_to_vec<<<DOT_BLOCKS, 256, 0, st>>>(X, L.n, z);
+        count_launch();
+        return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
+    }
+};
+
+}  // namespace
+}  // namespace tqr
+
+using namespace tqr;
+
+extern "C" int tileqr_refine_workspace_size(const tileqr_desc *d, size_t *bytes)
+{
+    if (d == nullptr)
+        return -1;
+    if (bytes == nullptr)
+        return -2;
+    *bytes = refine_layout(d).end;
+    return 0;
+}
+
+extern "C" int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_t lda, const double *b, double *x,
+                                   int max_iter, double tol, void *workspace, size_t ws_bytes,
+                                   tileqr_stream_t stream, tileqr_refine_info *info)
+{
+    if (d == nullptr)
+        return -1;
+    if (d->m < d->n)
+        return -1;
+    if (A == nullptr && d->m > 0)
+        return -2;
+    if (lda < (d->m > 1 ? d->m : 1))
+        return -3;
+    if (b == nullptr && d->m > 0)
+        return -4;
+    if (x == nullptr && d->n > 0)
+        return -5;
+    if (max_iter < 0)
+        return -6;
+    if (!(tol > 0.0))
+        return -7;
+    if (d->nb != 128)
+        return TILEQR_ERR_UNSUPPORTED;
+    const RefineLayout L = refine_layout(d);
+    if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < L.end)
+        return TILEQR_ERR_WORKSPACE;
+    tileqr_refine_info loc{};
+    if (info == nullptr)
+        info = &loc;
+    std::memset(info, 0, sizeof(*info));
+    if (d->n == 0)
+        return 0;
+    Refiner R;
+    R.d = d;
+    R.L = L;
+    R.ws = (char *)workspace;
+    R.st = (cudaStream_t)stream;
+    R.A = A;
+    R.lda = lda;
+    R.mm = d->m;
+    double *vecs = (double *)(R.ws + L.vecs);
+    R.r = vecs;
+    R.bc = vecs + R.mm;
+    R.dv = vecs + 2 * R.mm;
+    R.w = vecs + 3 * R.mm;
+    R.V = vecs + 4 * R.mm;
+    R.Z = R.V + (size_t)(GMRES_RESTART + 1) * R.mm;
+    R.dots = (double *)(R.ws + L.dots);
+    cudaStream_t st = R.st;
+    {
+        static int grid = 0;
+        if (grid == 0) {
+            int dev = 0, nsm = 0, per = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply32_dag, 128, 0);
+            grid = nsm * (per > 0 ? per : 1);
+            cudaFuncSetAttribute(k_inv_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (128 * 129 + 128) * 8);
+        }
+        R.grid_apply = grid;
+    }
+    // FP32 factors and inverted diagonal tiles of R
+    int *flag = (int *)(R.ws + L.flag);
+    cudaMemsetAsync(flag, 0, 256, st);
+    const size_t ntile = (size_t)d->p * d->q * 128 * 128, nT = (size_t)d->p * d->q * d->ib * 128;
+    k_to_f32<<<4 * DOT_BLOCKS, 256, 0, st>>>(d->tiles, (float *)(R.ws + L.tiles32), ntile);
+    k_to_f32<<<DOT_BLOCKS, 256, 0, st>>>(d->T, (float *)(R.ws + L.T32), nT);
+    k_inv_diag<<<d->q, 128, (128 * 129 + 128) * 8, st>>>(d->tiles, d->p, d->q, d->n, (float *)(R.ws + L.rinv), flag);
+    count_launch(3);
+    if (cudaGetLastError() != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    int hflag = 0;
+    cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (hflag)
+        return TILEQR_ERR_SINGULAR;
+
+    const double bnorm = std::sqrt(R.dot(b, b, d->m));
+    if (bnorm == 0.0) {
+        cudaMemsetAsync(x, 0, (size_t)d->n * 8, st);
+        info->converged = 1;
+        return 0;
+    }
+    // x0 = M^{-1} b
+    int rc = R.precond(b, x);
+    if (rc)
+        return rc;
+    rc = R.gemv_residual(x, R.r, b, false);
+    if (rc)
+        return rc;
+    double rnorm = std::sqrt(R.dot(R.r, R.r, d->m));
+    info->initial_rel_residual = rnorm / bnorm;
+    info->method = 1;
+    int outer = 0;
+    bool use_gmres = false;
+    while (rnorm / bnorm > tol && outer < max_iter) {
+        outer++;
+        if (!use_gmres) {
+            // classical refinement: x += M^{-1} r
+            rc = R.precond(R.r, R.dv);
+            if (rc)
+                return rc;
+            k_axpy<<<DOT_BLOCKS, 256, 0, st>>>(1.0, R.dv, x, d->n);
+            count_launch();
+        } else {
+            // flexible GMRES(restart) on A d = r, right preconditioner M^{-1}
+            info->method = 2;
+            const double beta = rnorm;
+            k_scale_copy<<<DOT_BLOCKS, 256, 0, st>>>(1.0 / beta, R.r, R.V, d->m);
+            count_launch();
+            const int mr = GMRES_RESTART;
+            std::vector<double> H((size_t)(mr + 1) * mr, 0.0), cs(mr), sn(mr), g(mr + 1, 0.0);
+            g[0] = beta;
+            int jdone = 0;
+            for (int j = 0; j < mr; j++) {
+                double *vj = R.V + (size_t)j * R.mm, *zj = R.Z + (size_t)j * R.mm;
+                rc = R.precond(vj, zj);
+                if (rc)
+                    return rc;
+                rc = R.gemv_residual(zj, R.w, nullptr, true);   // w = -A z_j
+                if (rc)
+                    return rc;
+                k_scale_copy<<<DOT_BLOCKS, 256, 0, st>>>(-1.0, R.w, R.w, d->m);
+                count_launch();
+                // classical Gram-Schmidt, twice
+                std::vector<double> h(j + 1, 0.0);
+                double *hdev = R.dots + (size_t)(GMRES_RESTART + 1) * DOT_BLOCKS;
+                for (int pass = 0; pass < 2; pass++) {
+                    k_multidot<<<DOT_BLOCKS, 256, 0, st>>>(R.V, R.mm, j + 1, R.w, d->m, R.dots);
+                    count_launch();
+                    std::vector<double> part((size_t)(j + 1) * DOT_BLOCKS);
+                    cudaMemcpyAsync(part.data(), R.dots, part.size() * 8, cudaMemcpyDeviceToHost, st);
+                    cudaStreamSynchronize(st);
+                    std::vector<double> hp(j + 1, 0.0);
+                    for (int c = 0; c <= j; c++)
+                        for (int bb = 0; bb < DOT_BLOCKS; bb++)
+                            hp[c] += part[(size_t)c * DOT_BLOCKS + bb];
+                    for (int c = 0; c <= j; c++)
+                        h[c] += hp[c];
+                    cudaMemcpyAsync(hdev, hp.data(), (j + 1) * 8, cudaMemcpyHostToDevice, st);
+                    k_multiaxpy<<<DOT_BLOCKS, 256, 0, st>>>(R.V, R.mm, j + 1, hdev, R.w, d->m, -1.0);
+                    count_launch();
+                }
+                const double hn = std::sqrt(R.dot(R.w, R.w, d->m));
+                for (int c = 0; c <= j; c++)
+                    H[(size_t)j * (mr + 1) + c] = h[c];
+                H[(size_t)j * (mr + 1) + j + 1] = hn;
+                // apply previous Givens rotations to column j, then a new one
+                for (int c = 0; c < j; c++) {
+                    double *hc = &H[(size_t)j * (mr + 1) + c];
+                    const double t = cs[c] * hc[0] + sn[c] * hc[1];
+                    hc[1] = -sn[c] * hc[0] + cs[c] * hc[1];
+                    hc[0] = t;
+                }
+                double *hj = &H[(size_t)j * (mr + 1) + j];
+                const double den = std::hypot(hj[0], hj[1]);
+                cs[j] = den > 0 ? hj[0] / den : 1.0;
+                sn[j] = den > 0 ? hj[1] / den : 0.0;
+                hj[0] = den;
+                hj[1] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                jdone = j + 1;
+                info->inner_iterations++;
+                if (std::fabs(g[j + 1]) <= 0.1 * tol * bnorm || hn == 0.0)
+                    break;
+                if (j + 1 < mr)
+                    k_scale_copy<<<DOT_BLOCKS, 256, 0, st>>>(1.0 / hn, R.w, R.V + (size_t)(j + 1) * R.mm, d->m);
+            }
+            // y = H^{-1} g (upper triangular jdone x jdone), d = Z y
+            std::vector<double> y(jdone, 0.0);
+            for (int rr = jdone - 1; rr >= 0; rr--) {
+                double acc = g[rr];
+                for (int c = rr + 1; c < jdone; c++)
+                    acc -= H[(size_t)c * (mr + 1) + rr] * y[c];
+                y[rr] = acc / H[(size_t)rr * (mr + 1) + rr];
+            }
+            double *hdev = R.dots + (size_t)(GMRES_RESTART + 1) * DOT_BLOCKS;
+            cudaMemcpyAsync(hdev, y.data(), jdone * 8, cudaMemcpyHostToDevice, st);
+            k_multiaxpy<<<DOT_BLOCKS, 256, 0, st>>>(R.Z, R.mm, jdone, hdev, x, d->n, 1.0);
+            count_launch();
+        }
+        rc = R.gemv_residual(x, R.r, b, false);
+        if (rc)
+            return rc;
+        const double rn = std::sqrt(R.dot(R.r, R.r, d->m));
+        if (!use_gmres && rn > 0.5 * rnorm)
+            use_gmres = true;   // classical refinement stalls: kappa * u_factor is not small
+        rnorm = rn;
+    }
+    info->iterations = outer;
+    info->rel_residual = rnorm / bnorm;
+    info->converged = rnorm / bnorm <= tol;
+    return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
+}

@@ -31,6 +31,7 @@ EXPORTED = [
     "tileqr_get_factors", "tileqr_apply_workspace_size", "tileqr_apply_qt", "tileqr_solve_ls",
     "tileqr_strerror", "tileqr_launch_count", "tileqr_reset_launch_count",
     "tileqr_set_profile_events", "tileqr_factor_noalloc", "tileqr_set_trace", "tileqr_trace_count",
+    "tileqr_refine_workspace_size", "tileqr_solve_refine",
 ]
 
 
@@ -44,6 +45,17 @@ class tileqr_desc(ctypes.Structure):
         ("sched", ctypes.c_void_p), ("sched_bytes", ctypes.c_size_t),
         ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
     ]
+
+
+class tileqr_refine_info(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int), ("inner_iterations", ctypes.c_int), ("method", ctypes.c_int),
+        ("converged", ctypes.c_int), ("initial_rel_residual", ctypes.c_double),
+        ("rel_residual", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class TileQRError(RuntimeError):
@@ -80,6 +92,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_set_profile_events": (None, [vp, vp]),
         "tileqr_factor_noalloc": (i32, [i64, i64, vp, i64, i32, i32, vp, sz, vp, sz, vp, dp]),
         "tileqr_set_trace": (None, [vp, ctypes.c_uint64]),
+        "tileqr_refine_workspace_size": (i32, [dp, ctypes.POINTER(sz)]),
+        "tileqr_solve_refine": (i32, [dp, vp, i64, vp, vp, i32, ctypes.c_double, vp, sz, vp,
+                                      ctypes.POINTER(tileqr_refine_info)]),
         "tileqr_trace_count": (i32, [dp, vp, ctypes.POINTER(ctypes.c_uint64)]),
     }
     for name, (res, args) in sig.items():
@@ -220,6 +235,24 @@ class Factorization:
                                       B.shape[1], ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                       _stream_ptr(stream)), "tileqr_apply_qt")
         return B
+
+    def solve_refine(self, A: torch.Tensor, b: torch.Tensor, max_iter: int = 30, tol: float = 1e-12,
+                     stream=None):
+        """x with ||b - A x|| / ||b|| <= tol by FP64 iterative refinement on
+        this factorization of A (see tileqr_solve_refine); returns (x, info)."""
+        A = as_colmajor(A)
+        b = b.reshape(-1).contiguous()
+        need = ctypes.c_size_t(0)
+        _check(load().tileqr_refine_workspace_size(ctypes.byref(self.desc), ctypes.byref(need)),
+               "tileqr_refine_workspace_size")
+        ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=self.device)
+        x = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        info = tileqr_refine_info()
+        _check(load().tileqr_solve_refine(ctypes.byref(self.desc), ctypes.c_void_p(A.data_ptr()), _ld(A),
+                                          ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), max_iter,
+                                          tol, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream),
+                                          ctypes.byref(info)), "tileqr_solve_refine")
+        return x, info
 
     def solve_ls(self, B: torch.Tensor, stream=None) -> torch.Tensor:
         """min ||A X - B||: B overwritten (X in its first n rows); returns X."""
