@@ -170,6 +170,83 @@ def run_reference(args, rank):
     return 0
 
 
+def run_batched(args, dev, rank, world, barrier, dist):
+    import numpy as np
+    import torch
+
+    from paper_0709_1272_gb300 import autotune, inputs, tileqr
+    shapes = inputs.batch_shapes(args.batch_count, seed=20070709 + 5 + 1000 * rank)
+    pool, offs = inputs.batch_pool(shapes, seed=20070709 + 5 + 1000 * rank)
+    pool_d = torch.from_numpy(pool).to(dev)
+    del pool
+    mats = [pool_d[o:o + m * n].view(n, m).t() for (m, n), o in zip(shapes, offs)]
+    flops = sum(2.0 * n * n * (m - n / 3.0) for (m, n) in shapes)
+
+    def graph_time(bt, reps=2):
+        bt.run()                                  # first call outside capture
+        assert bt.status() == 0
+        s = torch.cuda.Stream(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                bt.run(stream=s)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        assert bt.status() == 0
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        if dist is not None:
+            tt = torch.tensor([t], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t
+
+    def loop_time(sub, nb, ib, precision):
+        ws = torch.empty(max(tileqr.tileqr_workspace_size(a.shape[0], a.shape[1], nb, ib, precision)
+                             for a in sub), dtype=torch.uint8, device=dev)
+        for a in sub[:4]:
+            tileqr.tileqr_factor(a, nb, ib, precision=precision, workspace=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for a in sub:
+            f = tileqr.tileqr_factor(a, nb, ib, precision=precision, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        assert f.status() == 0
+        return e0.elapsed_time(e1) / 1e3
+
+    out = {"workload": f"{len(shapes)} independent matrices, m ~ U[64,2048], n ~ U[32,m], entries U[-1,1)",
+           "count": len(shapes), "flops": flops, "unit": UNIT, "timing": "CUDA-graph replay, events"}
+    for label, prec in (("fp64", tileqr.TILEQR_FP64), ("tf32", tileqr.TILEQR_TF32)):
+        nb, ib, tune_ms = autotune.tune_batched(mats, prec, sample=256)
+        bt = tileqr.Batch(mats, nb, ib, prec)
+        t = graph_time(bt)
+        out[label] = {"value": world * flops / t / 1e9, "ms": t * 1e3, "nb": nb, "ib": ib,
+                      "autotune_ms_on_sample": tune_ms}
+        del bt
+        torch.cuda.empty_cache()
+        k = min(args.loop_subset, len(mats))
+        sub = mats[:k]
+        sflops = sum(2.0 * n * n * (m - n / 3.0) for (m, n) in shapes[:k])
+        tl = loop_time(sub, nb, ib, prec)
+        tb = graph_time(tileqr.Batch(sub, nb, ib, prec))
+        out[label]["loop_subset"] = {"count": k, "per_matrix_loop_ms": tl * 1e3, "batched_ms": tb * 1e3,
+                                     "speedup": tl / tb, "loop_value": sflops / tl / 1e9,
+                                     "batched_value": sflops / tb / 1e9}
+        torch.cuda.empty_cache()
+    out["tf32_speedup_vs_fp64"] = out["fp64"]["ms"] / out["tf32"]["ms"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -187,6 +264,10 @@ def main():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision + FP64 refinement measurement")
     ap.add_argument("--kappa", type=float, default=1e6)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched (4096 ragged matrices) measurement")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--loop-subset", type=int, default=512)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -343,6 +424,14 @@ def main():
                  "initial_rel_residual": infos[-1]["initial_rel_residual"],
                  "speedup_vs_fp64_factorization": (world * ops / tm / 1e9) / value,
                  "timing": "wall clock around factor+refine (the refinement synchronises), max over ranks"}
+        del wsm, Akd, bk, fm
+
+    # ---- batched: 4096 independent matrices, m ~ U[64, 2048], n ~ U[32, m],
+    # entries U[-1, 1), one persistent launch replayed from a CUDA graph
+    batched = None
+    if not args.no_batched:
+        torch.cuda.empty_cache()
+        batched = run_batched(args, dev, rank, world, barrier, dist)
 
     if rank != 0:
         if dist is not None:
@@ -380,6 +469,8 @@ def main():
         out["e2e"] = e2e
     if mixed:
         out["mixed_ls"] = mixed
+    if batched:
+        out["batched"] = batched
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(nb, ib)
     print(json.dumps(out), flush=True)

@@ -191,6 +191,41 @@ int tileqr_apply_qt(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, 
 int tileqr_solve_ls(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
                     size_t ws_bytes, tileqr_stream_t stream);
 
+/* Batched form: many independent factorizations (shapes may all differ) in
+ * one persistent launch.  tileqr_batched_prepare lays the batch out in the
+ * caller's workspace and uploads a per-matrix table (synchronous);
+ * tileqr_factor_batched then only enqueues a memset and two kernels (layout
+ * conversion of every matrix, then one task-graph kernel over all tasks of
+ * all matrices, Sec. 4 priorities shared across the batch), so it can be
+ * captured in a CUDA graph and replayed.  Call it once outside any capture
+ * first (it sets kernel attributes on first use).  The paper factors one
+ * matrix at a time; batching is an addition of this library. */
+typedef struct tileqr_batch {
+    int count, nb, ib, precision;
+    uint64_t total_tasks;
+    uint32_t cap[4];
+    size_t off_ctrl, off_cnt, off_q[4], off_mats, sched_bytes;
+    void *workspace;
+    size_t workspace_bytes;
+    double flops;   /* LAPACK operation count of the whole batch */
+} tileqr_batch;
+
+/* Workspace bytes for a batch of `count` matrices m[b] x n[b] (host arrays). */
+int tileqr_batched_workspace_size(int count, const int64_t *m, const int64_t *n, int nb, int ib, int precision,
+                                  size_t *bytes);
+/* A[b]: device pointer of matrix b (column-major, lda[b] >= m[b]); host
+ * arrays of `count` entries. Fills *out. Synchronous on `stream`. */
+int tileqr_batched_prepare(int count, const int64_t *m, const int64_t *n, const double *const *A,
+                           const int64_t *lda, int nb, int ib, int precision, void *workspace, size_t ws_bytes,
+                           tileqr_stream_t stream, tileqr_batch *out);
+/* Factor every matrix of a prepared batch (asynchronous, graph-capturable). */
+int tileqr_factor_batched(const tileqr_batch *bt, tileqr_stream_t stream);
+/* Synchronise and return the batch's device-side status (as tileqr_status). */
+int tileqr_batched_status(const tileqr_batch *bt, tileqr_stream_t stream);
+/* Descriptor of matrix `index` of a factored batch (usable with tileqr_get_R,
+ * tileqr_get_factors, tileqr_apply_qt, tileqr_solve_ls). */
+int tileqr_batched_get(const tileqr_batch *bt, int index, tileqr_desc *out);
+
 /* Outcome of tileqr_solve_refine. */
 typedef struct tileqr_refine_info {
     int iterations;             /* refinement steps taken */

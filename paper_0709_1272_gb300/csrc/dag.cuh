@@ -160,3 +160,157 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_fac
 }
 
 }  // namespace tqr
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent matrices factored by one persistent launch.
+// Every matrix has its own tiles, T strips and task counters; the four
+// priority queues are shared, so tasks of all matrices interleave and the
+// GPU stays full while small matrices finish.
+namespace tqr {
+
+struct MatInfo {
+    double *tiles;
+    double *T;
+    const double *A;
+    int64_t m, n, lda;
+    int p, q, steps, pad;
+    size_t cnt_off;   // first task counter of this matrix
+};
+
+// batch task code: matrix (20 bits) | k (14) | i (15) | j (15)
+__host__ __device__ inline unsigned long long encode_btask(int mat, int k, int i, int j)
+{
+    return ((unsigned long long)mat << 44) | ((unsigned long long)k << 30) | ((unsigned long long)i << 15) |
+           (unsigned long long)j;
+}
+__host__ __device__ inline void decode_btask(unsigned long long c, int &mat, int &k, int &i, int &j)
+{
+    mat = (int)(c >> 44);
+    k = (int)((c >> 30) & 0x3FFF);
+    i = (int)((c >> 15) & 0x7FFF);
+    j = (int)(c & 0x7FFF);
+}
+
+// Successors of task (k, i, j) of matrix `mat` (same graph as release_factor).
+__device__ static void release_batched(const Queues &Q, const FactorArgs &F, size_t cnt_off, int mat, int k, int i,
+                                       int j)
+{
+    const int p = F.p, q = F.q;
+    const int kind = task_kind(i, j, k);
+    int nsucc = 0;
+    switch (kind) {
+    case K_GEQRT: nsucc = (q - k - 1) + (k + 1 < p ? 1 : 0); break;
+    case K_LARFB: nsucc = (k + 1 < p) ? 1 : 0; break;
+    case K_TSQRT: nsucc = (q - k - 1) + (i + 1 < p ? 1 : 0); break;
+    default: nsucc = (i + 1 < p ? 1 : 0) + 1; break;
+    }
+    for (int s = threadIdx.x; s < nsucc; s += NT) {
+        int ks, is, js;
+        switch (kind) {
+        case K_GEQRT:
+            if (s < q - k - 1) { ks = k; is = k; js = k + 1 + s; }
+            else { ks = k; is = k + 1; js = k; }
+            break;
+        case K_LARFB:
+            ks = k; is = k + 1; js = j;
+            break;
+        case K_TSQRT:
+            if (s < q - k - 1) { ks = k; is = i; js = k + 1 + s; }
+            else { ks = k; is = i + 1; js = k; }
+            break;
+        default:
+            if (s == 0 && i + 1 < p) { ks = k; is = i + 1; js = j; }
+            else { ks = k + 1; is = i; js = j; }
+            break;
+        }
+        const size_t idx = cnt_off + ((size_t)ks * p + is) * q + js;
+        q_signal(Q, idx, task_ndeps(is, js, ks), task_kind(is, js, ks), encode_btask(mat, ks, is, js));
+    }
+}
+
+template <int NB, int S, bool MIXED>
+__global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
+    k_factor_dag_batched(const MatInfo *__restrict__ mats, int count, Queues Q)
+{
+    extern __shared__ double sm[];
+    __shared__ unsigned long long s_code;
+    __shared__ int s_cmd;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ FactorArgs s_F;
+    __shared__ size_t s_cnt;
+    uint32_t tmem = 0, mphase = 0;
+    if (MIXED) {
+        if ((threadIdx.x >> 5) == 0)
+            tc::tmem_alloc(&s_tmem, MixCfg<S>::TMEM_COLS);
+        if (threadIdx.x == 0)
+            tc::mbar_init(&s_mbar, 1);
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tmem = s_tmem;
+    }
+    if (blockIdx.x == 0) {
+        if (ld_relaxed_s32(&Q.ctrl->nonfinite) != 0) {
+            if (threadIdx.x == 0)
+                atomicCAS(&Q.ctrl->error, 0, TILEQR_ERR_NONFINITE);
+        } else {
+            for (int b = threadIdx.x; b < count; b += NT)
+                if (mats[b].steps > 0)
+                    q_push(Q, K_GEQRT, encode_btask(b, 0, 0, 0));
+        }
+    }
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_cmd = q_acquire(Q, s_code);
+            if (s_cmd == CMD_RUN) {
+                int mat, k, i, j;
+                decode_btask(s_code, mat, k, i, j);
+                const MatInfo &mi = mats[mat];
+                s_F.tiles = mi.tiles;
+                s_F.T = mi.T;
+                s_F.p = mi.p;
+                s_F.q = mi.q;
+                s_F.steps = mi.steps;
+                s_cnt = mi.cnt_off;
+            }
+        }
+        __syncthreads();
+        if (s_cmd != CMD_RUN)
+            break;
+        int mat, k, i, j;
+        decode_btask(s_code, mat, k, i, j);
+        const FactorArgs F = s_F;
+        const size_t cnt_off = s_cnt;
+        const unsigned long long t0 = Q.trace ? globaltimer_ns() : 0ull;
+        const int kind = task_kind(i, j, k);
+        if (MIXED && kind == K_SSRFB) {
+            task_update_mixed<S, false>((unsigned char *)sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, i, j),
+                                        tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), tmem, &s_mbar,
+                                        mphase, &Q.ctrl->error);
+        } else if (MIXED && kind == K_LARFB) {
+            task_update_mixed<S, true>((unsigned char *)sm, nullptr, tile_ptr<NB, S>(F, k, j),
+                                       tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k), tmem, &s_mbar, mphase,
+                                       &Q.ctrl->error);
+        } else {
+            run_factor_task<NB, S>(sm, F, k, i, j);
+        }
+        __syncthreads();
+        release_batched(Q, F, cnt_off, mat, k, i, j);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (Q.trace)
+                trace_record(Q, s_code, t0, globaltimer_ns());
+            __threadfence();
+            atomicAdd(&Q.ctrl->completed, 1u);
+        }
+    }
+    if (MIXED) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0)
+            tc::tmem_dealloc(tmem, MixCfg<S>::TMEM_COLS);
+    }
+}
+
+}  // namespace tqr

@@ -64,3 +64,26 @@ def batch_shapes(count: int, seed: int, m_lo: int = 64, m_hi: int = 2048, n_lo: 
 def batch_matrices(shapes, seed: int):
     """One uniform[-1,1) matrix per shape, item b drawn from seed + 1 + b."""
     return [uniform_matrix(m, n, seed + 1 + b) for b, (m, n) in enumerate(shapes)]
+
+
+def batch_pool(shapes, seed: int, threads: int | None = None):
+    """All matrices of a batch in one flat float64 buffer (matrix b occupies
+    m_b * n_b consecutive values, column-major), drawn exactly as
+    batch_matrices(shapes, seed) would draw them, in parallel threads (numpy's
+    generators release the GIL).  Returns (pool, offsets)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    offsets, tot = [], 0
+    for (m, n) in shapes:
+        offsets.append(tot)
+        tot += m * n
+    pool = np.empty(tot, dtype=np.float64)
+
+    def fill(b):
+        m, n = shapes[b]
+        pool[offsets[b]:offsets[b] + m * n] = _rng(seed + 1 + b).uniform(-1.0, 1.0, size=m * n)
+
+    with ThreadPoolExecutor(threads or os.cpu_count() or 4) as ex:
+        list(ex.map(fill, range(len(shapes))))
+    return pool, offsets

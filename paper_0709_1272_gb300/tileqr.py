@@ -32,6 +32,8 @@ EXPORTED = [
     "tileqr_strerror", "tileqr_launch_count", "tileqr_reset_launch_count",
     "tileqr_set_profile_events", "tileqr_factor_noalloc", "tileqr_set_trace", "tileqr_trace_count",
     "tileqr_refine_workspace_size", "tileqr_solve_refine",
+    "tileqr_batched_workspace_size", "tileqr_batched_prepare", "tileqr_factor_batched",
+    "tileqr_batched_status", "tileqr_batched_get",
 ]
 
 
@@ -56,6 +58,16 @@ class tileqr_refine_info(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class tileqr_batch(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int), ("nb", ctypes.c_int), ("ib", ctypes.c_int), ("precision", ctypes.c_int),
+        ("total_tasks", ctypes.c_uint64), ("cap", ctypes.c_uint32 * 4),
+        ("off_ctrl", ctypes.c_size_t), ("off_cnt", ctypes.c_size_t), ("off_q", ctypes.c_size_t * 4),
+        ("off_mats", ctypes.c_size_t), ("sched_bytes", ctypes.c_size_t),
+        ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("flops", ctypes.c_double),
+    ]
 
 
 class TileQRError(RuntimeError):
@@ -93,6 +105,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_factor_noalloc": (i32, [i64, i64, vp, i64, i32, i32, vp, sz, vp, sz, vp, dp]),
         "tileqr_set_trace": (None, [vp, ctypes.c_uint64]),
         "tileqr_refine_workspace_size": (i32, [dp, ctypes.POINTER(sz)]),
+        "tileqr_batched_workspace_size": (i32, [i32, vp, vp, i32, i32, i32, ctypes.POINTER(sz)]),
+        "tileqr_batched_prepare": (i32, [i32, vp, vp, vp, vp, i32, i32, i32, vp, sz, vp,
+                                         ctypes.POINTER(tileqr_batch)]),
+        "tileqr_factor_batched": (i32, [ctypes.POINTER(tileqr_batch), vp]),
+        "tileqr_batched_status": (i32, [ctypes.POINTER(tileqr_batch), vp]),
+        "tileqr_batched_get": (i32, [ctypes.POINTER(tileqr_batch), i32, dp]),
         "tileqr_solve_refine": (i32, [dp, vp, i64, vp, vp, i32, ctypes.c_double, vp, sz, vp,
                                       ctypes.POINTER(tileqr_refine_info)]),
         "tileqr_trace_count": (i32, [dp, vp, ctypes.POINTER(ctypes.c_uint64)]),
@@ -320,3 +338,48 @@ def tileqr_trace_count(f: "Factorization", stream=None) -> int:
     _check(load().tileqr_trace_count(ctypes.byref(f.desc), _stream_ptr(stream), ctypes.byref(out)),
            "tileqr_trace_count")
     return int(out.value)
+
+
+class Batch:
+    """A prepared batch of independent factorizations (tileqr_batched_prepare).
+
+    `mats` are column-major float64 CUDA tensors; they must stay alive while
+    the batch is used.  run() enqueues the factorization of all of them
+    (graph-capturable); get(b) returns the Factorization of matrix b."""
+
+    def __init__(self, mats, nb: int, ib: int, precision: int = TILEQR_FP64, stream=None):
+        import numpy as np
+        self.mats = [as_colmajor(a) for a in mats]
+        count = len(self.mats)
+        self._m = np.array([a.shape[0] for a in self.mats], dtype=np.int64)
+        self._n = np.array([a.shape[1] for a in self.mats], dtype=np.int64)
+        self._lda = np.array([_ld(a) for a in self.mats], dtype=np.int64)
+        self._ptrs = (ctypes.c_void_p * max(count, 1))(*[a.data_ptr() for a in self.mats])
+        need = ctypes.c_size_t(0)
+        mp = self._m.ctypes.data_as(ctypes.c_void_p)
+        np_ = self._n.ctypes.data_as(ctypes.c_void_p)
+        _check(load().tileqr_batched_workspace_size(count, mp, np_, nb, ib, precision, ctypes.byref(need)),
+               "tileqr_batched_workspace_size")
+        dev = self.mats[0].device if count else torch.device("cuda")
+        self.workspace = torch.empty(max(need.value, 256), dtype=torch.uint8, device=dev)
+        self.device = dev
+        self.bt = tileqr_batch()
+        _check(load().tileqr_batched_prepare(count, mp, np_, self._ptrs, self._lda.ctypes.data_as(ctypes.c_void_p),
+                                             nb, ib, precision, ctypes.c_void_p(self.workspace.data_ptr()),
+                                             self.workspace.numel(), _stream_ptr(stream), ctypes.byref(self.bt)),
+               "tileqr_batched_prepare")
+
+    @property
+    def flops(self) -> float:
+        return self.bt.flops
+
+    def run(self, stream=None) -> None:
+        _check(load().tileqr_factor_batched(ctypes.byref(self.bt), _stream_ptr(stream)), "tileqr_factor_batched")
+
+    def status(self, stream=None) -> int:
+        return load().tileqr_batched_status(ctypes.byref(self.bt), _stream_ptr(stream))
+
+    def get(self, b: int) -> "Factorization":
+        d = tileqr_desc()
+        _check(load().tileqr_batched_get(ctypes.byref(self.bt), b, ctypes.byref(d)), "tileqr_batched_get")
+        return Factorization(d, self.workspace, self.device)
