@@ -174,7 +174,7 @@ def run_batched(args, dev, rank, world, barrier, dist):
     import numpy as np
     import torch
 
-    from paper_0709_1272_gb300 import autotune, inputs, tileqr
+    from paper_0709_1272_gb300 import autotune, inputs, replicas, tileqr
     shapes = inputs.batch_shapes(args.batch_count, seed=20070709 + 5 + 1000 * rank)
     pool, offs = inputs.batch_pool(shapes, seed=20070709 + 5 + 1000 * rank)
     pool_d = torch.from_numpy(pool).to(dev)
@@ -202,12 +202,7 @@ def run_batched(args, dev, rank, world, barrier, dist):
         e1.record()
         torch.cuda.synchronize()
         assert bt.status() == 0
-        t = e0.elapsed_time(e1) / 1e3 / reps
-        if dist is not None:
-            tt = torch.tensor([t], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return t
+        return replicas.max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps, dist, dev)
 
     def loop_time(sub, nb, ib, precision):
         ws = torch.empty(max(tileqr.tileqr_workspace_size(a.shape[0], a.shape[1], nb, ib, precision)
@@ -287,7 +282,7 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    from paper_0709_1272_gb300 import build, inputs, tileqr
+    from paper_0709_1272_gb300 import build, inputs, replicas, tileqr
     build.build()
     tileqr.load()
     sched = tileqr.TILEQR_SCHED_DAG if args.schedule == "dag" else tileqr.TILEQR_SCHED_BULK
@@ -339,10 +334,7 @@ def main():
         raise SystemExit(f"factorization failed: {tileqr.strerror(status)}")
     elapsed = t_start.elapsed_time(t_end) / 1e3
     dag_times = [ev_b[s].elapsed_time(ev_a[s]) / 1e3 for s in range(args.steps)]
-    if dist is not None:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = replicas.max_over_ranks(elapsed, dist, dev)
     ops = lapack_opcount(m, n)
     value = world * args.steps * ops / elapsed / 1e9
 
@@ -369,10 +361,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         et = e0.elapsed_time(e1) / 1e3
-        if dist is not None:
-            t = torch.tensor([et], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
+        et = replicas.max_over_ranks(et, dist, dev)
         assert g.status() == 0
         e2e = {"value": world * args.e2e_steps * ops / et / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": k * n * 8,
@@ -410,10 +399,7 @@ def main():
                 infos.append(info.as_dict())
         assert fm.status() == 0
         tm = statistics.mean([a + b for a, b in zip(fac_t, ref_t)])
-        if dist is not None:
-            t = torch.tensor([tm], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tm = float(t.item())
+        tm = replicas.max_over_ranks(tm, dist, dev)
         mixed = {"workload": f"TF32-update tile QR + FP64 refinement of A x = b, {m}x{n}, "
                              f"A = (I-2uu^T) diag(s) (I-2vv^T), cond {args.kappa:.0e}, nb={nb}, ib={ib}",
                  "value": world * ops / tm / 1e9, "unit": UNIT, "ms_per_step": tm * 1e3,
