@@ -26,20 +26,20 @@ __device__ __forceinline__ double *strip_ptr(const FactorArgs &F, int i, int k)
     return F.T + ((size_t)k * F.p + i) * (size_t)S * NB;
 }
 
-template <int NB, int S>
+template <int NB, int S, bool MIXED = false>
 __device__ void run_factor_task(double *sm, const FactorArgs &F, int k, int i, int j)
 {
     switch (task_kind(i, j, k)) {
     case K_GEQRT:
-        task_geqrt<NB, S>(sm, tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k));
+        task_geqrt<NB, S, MIXED>(sm, tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k));
         break;
     case K_LARFB:
         task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, k, k),
                           strip_ptr<NB, S>(F, k, k));
         break;
     case K_TSQRT:
-        task_tsqrt<NB, S>(sm, tile_ptr<NB, S>(F, k, k), tile_ptr<NB, S>(F, i, k),
-                          strip_ptr<NB, S>(F, i, k));
+        task_tsqrt<NB, S, MIXED>(sm, tile_ptr<NB, S>(F, k, k), tile_ptr<NB, S>(F, i, k),
+                                 strip_ptr<NB, S>(F, i, k));
         break;
     default:
         task_ssrfb<NB, S>(sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, i, j),
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_fac
                                        tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k), tmem, &s_mbar, mphase,
                                        &Q.ctrl->error);
         } else {
-            run_factor_task<NB, S>(sm, F, k, i, j);
+            run_factor_task<NB, S, MIXED>(sm, F, k, i, j);
         }
         __syncthreads();
         release_factor(Q, F, k, i, j);
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
                                        tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k), tmem, &s_mbar, mphase,
                                        &Q.ctrl->error);
         } else {
-            run_factor_task<NB, S>(sm, F, k, i, j);
+            run_factor_task<NB, S, MIXED>(sm, F, k, i, j);
         }
         __syncthreads();
         release_batched(Q, F, cnt_off, mat, k, i, j);

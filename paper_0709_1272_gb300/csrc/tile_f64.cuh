@@ -485,10 +485,142 @@ __device__ __noinline__ void trailing_update(double *sm, double *At, double *Rt,
     }
 }
 
+// FP64 <-> FP32 by integer operations (the F2F instructions run at the FP64
+// rate on GB300): see tile_mixed.cuh for the same conversions on the tensor-
+// core path.
+__device__ __forceinline__ float panel_f64_to_f32(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    const uint32_t sgn = hi & 0x80000000u;
+    uint32_t f = __funnelshift_l(lo, hi - 0x38000000u, 3);
+    f = (f & 0x7FFFFFFFu) | sgn;
+    f += (lo >> 28) & 1u;
+    f = (e < 897u) ? sgn : f;
+    f = (e > 1150u) ? (sgn | 0x7F800000u) : f;
+    return __uint_as_float(f);
+}
+__device__ __forceinline__ double panel_f32_to_f64(float v)
+{
+    const uint32_t f = __float_as_uint(v);
+    const uint32_t sgn = f & 0x80000000u;
+    uint32_t hi = sgn | (((f & 0x7FFFFFFFu) >> 3) + 0x38000000u);
+    uint32_t lo = f << 29;
+    const bool zero = (f & 0x7F800000u) == 0u;
+    hi = zero ? sgn : hi;
+    lo = zero ? 0u : lo;
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
+// Mixed-precision form of trailing_update (TILEQR_TF32 builds): the block
+// product Y = B_l + V_l^T C, W = T_l^T Y and the delta V_l W are formed in
+// FP32 on the CUDA cores; the FP64 tile then receives C -= delta and
+// B_l -= W with one FP64 subtraction per element.  The reflectors, tau and
+// T_l were formed in FP64 by the panel and are only read here.
+template <int NB, int S>
+__device__ __noinline__ void trailing_update_mixed(double *sm, double *At, double *Rt, int l0, int r0)
+{
+    using C_ = F64Cfg<NB, S>;
+    constexpr int W = C_::W, LDF = NB + 1, LDVF = S + 1;
+    static_assert(W == 64 && NB == 128, "mixed panels: nb 128");
+    // FP32 work arrays carved from the chunk area (the panel is done with it)
+    float *Cf = (float *)(sm + C_::OFF_C);           // W x (NB+1), [c][r]
+    float *Vf = Cf + W * LDF;                         // NB x (S+1), [r][a]
+    float *Yf = Vf + NB * LDVF;                       // S x W, [a][c]
+    float *Tf = Yf + S * W;                           // S x S, T(b,a) at b + a*S
+    static_assert((W * LDF + NB * LDVF + S * W + S * S) * 4 <= W * (NB + 1) * 8, "fits the chunk area");
+    const double *Vs = sm + C_::OFF_V;
+    const double *Ts = sm + C_::OFF_T;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < NB * S; idx += NT) {
+        const int r = idx / S, a = idx - r * S;
+        Vf[r * LDVF + a] = panel_f64_to_f32(Vs[r * C_::LDV + a]);
+    }
+    for (int idx = tid; idx < S * S; idx += NT)
+        Tf[idx] = panel_f64_to_f32(Ts[idx]);
+    for (int c0 = l0 + S; c0 < NB; c0 += W) {
+        const int nc = min(W, NB - c0);
+        __syncthreads();
+        for (int idx = tid; idx < W * NB; idx += NT) {
+            const int c = idx / NB, r = idx - c * NB;
+            Cf[c * LDF + r] = (c < nc && r >= r0) ? panel_f64_to_f32(ldcg(At + (size_t)(c0 + c) * NB + r)) : 0.0f;
+        }
+        __syncthreads();
+        // Y = B_l + V^T C: thread (c, quarter of the block rows)
+        {
+            const int c = tid & (W - 1), ag = tid >> 6;
+            constexpr int AQ = S / 4;
+            float y[AQ];
+            double bv[AQ];
+#pragma unroll
+            for (int i = 0; i < AQ; i++) {
+                const int a = ag * AQ + i;
+                bv[i] = (Rt != nullptr && c < nc) ? ldcg(Rt + (size_t)(c0 + c) * NB + l0 + a) : 0.0;
+                y[i] = panel_f64_to_f32(bv[i]);
+            }
+            for (int r = r0; r < NB; r++) {
+                const float cv = Cf[c * LDF + r];
+#pragma unroll
+                for (int i = 0; i < AQ; i++)
+                    y[i] = fmaf(Vf[r * LDVF + ag * AQ + i], cv, y[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < AQ; i++)
+                Yf[(ag * AQ + i) * W + c] = y[i];
+            __syncthreads();
+            float w[AQ];
+#pragma unroll
+            for (int i = 0; i < AQ; i++) {
+                const int a = ag * AQ + i;
+                float acc = 0.0f;
+                for (int b = 0; b <= a; b++)
+                    acc = fmaf(Tf[b + a * S], Yf[b * W + c], acc);
+                w[i] = acc;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < AQ; i++) {
+                const int a = ag * AQ + i;
+                Yf[a * W + c] = w[i];
+                if (Rt != nullptr && c < nc)
+                    stcg(Rt + (size_t)(c0 + c) * NB + l0 + a, bv[i] - panel_f32_to_f64(w[i]));
+            }
+            __syncthreads();
+        }
+        // C -= V W: thread (row r, half of the chunk columns), lanes along rows
+        {
+            const int r = tid & (NB - 1), half = tid >> 7;
+            if (r >= r0) {
+                constexpr int CH = W / 2;
+                float d[CH];
+#pragma unroll
+                for (int j = 0; j < CH; j++)
+                    d[j] = 0.0f;
+                for (int a = 0; a < S; a++) {
+                    const float v = Vf[r * LDVF + a];
+#pragma unroll
+                    for (int j = 0; j < CH; j++)
+                        d[j] = fmaf(v, Yf[a * W + half * CH + j], d[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < CH; j++) {
+                    const int c = half * CH + j;
+                    if (c < nc) {
+                        double *p = At + (size_t)(c0 + c) * NB + r;
+                        stcg(p, ldcg(p) - panel_f32_to_f64(d[j]));
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // DGEQRT (Sec. 3.2.1): QR of the diagonal tile At in place (R on and above
 // the diagonal, V below), T strip to Tt.  Inner blocks l in order: panel
 // factorization, T_l, then the block applied to the trailing tile columns.
-template <int NB, int S>
+template <int NB, int S, bool MIXED = false>
 __device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt)
 {
     using C_ = F64Cfg<NB, S>;
@@ -516,7 +648,10 @@ __device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt)
         }
         __syncthreads();
         build_t<NB, S>(sm, l0, Tt, l0);
-        trailing_update<NB, S>(sm, At, nullptr, l0, l0);
+        if constexpr (MIXED)
+            trailing_update_mixed<NB, S>(sm, At, nullptr, l0, l0);
+        else
+            trailing_update<NB, S>(sm, At, nullptr, l0, l0);
     }
 }
 
@@ -524,7 +659,7 @@ __device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt)
 // the upper triangle of the diagonal tile Rt and A the tile At; R updated in
 // place (upper triangle only: V_kk below the diagonal is left untouched), A
 // overwritten by the reflector tile, T strip to Tt.
-template <int NB, int S>
+template <int NB, int S, bool MIXED = false>
 __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, double *Tt)
 {
     using C_ = F64Cfg<NB, S>;
@@ -557,7 +692,10 @@ __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, doub
         }
         __syncthreads();
         build_t<NB, S>(sm, 0, Tt, l0);
-        trailing_update<NB, S>(sm, At, Rt, l0, 0);
+        if constexpr (MIXED)
+            trailing_update_mixed<NB, S>(sm, At, Rt, l0, 0);
+        else
+            trailing_update<NB, S>(sm, At, Rt, l0, 0);
     }
 }
 
