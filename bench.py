@@ -50,8 +50,9 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_0709_1272_gb300/csrc/tile_f64.cuh", "paper_0709_1272_gb300/csrc/factor.cu",
-                "paper_0709_1272_gb300/csrc/sched.cuh"):
+    for rel in ("paper_0709_1272_gb300/csrc/common.cuh", "paper_0709_1272_gb300/csrc/sched.cuh",
+                "paper_0709_1272_gb300/csrc/tile_f64.cuh", "paper_0709_1272_gb300/csrc/dag.cuh",
+                "paper_0709_1272_gb300/csrc/factor.cu"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
