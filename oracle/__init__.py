@@ -57,10 +57,16 @@ def _load():
         lib.oracle_apply_qt.argtypes = [i64, i64, dp, i64, i32, i32, dp, i64, i64, dp, i64]
         lib.oracle_solve_ls.argtypes = [i64, i64, dp, i64, i32, i32, dp, i64, i64, dp, i64]
         lib.oracle_unblocked_qr.argtypes = [i64, i64, dp, i64]
+        lib.oracle_tiled_qr_tree.argtypes = [i64, i64, dp, i64, i32, i32, i32, dp, i64, dp, i64]
+        lib.oracle_tiled_qr_tree_ordered.argtypes = [i64, i64, dp, i64, i32, i32, i32, dp, i64, dp, i64,
+                                                     i64, ctypes.POINTER(ctypes.c_int32)]
+        lib.oracle_apply_qt_tree.argtypes = [i64, i64, dp, i64, i32, i32, i32, dp, i64, dp, i64, i64, dp,
+                                             i64]
         lib.oracle_flops.restype = ctypes.c_double
         lib.oracle_set_mutation.argtypes = [i32]
         for f in (lib.oracle_tiled_qr, lib.oracle_tiled_qr_ordered, lib.oracle_apply_qt,
-                  lib.oracle_solve_ls, lib.oracle_unblocked_qr):
+                  lib.oracle_solve_ls, lib.oracle_unblocked_qr, lib.oracle_tiled_qr_tree,
+                  lib.oracle_tiled_qr_tree_ordered, lib.oracle_apply_qt_tree):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -89,8 +95,9 @@ class Factored:
     tile (i, k) being rows i*ib..i*ib+ib-1 and columns k*nb..k*nb+nc(k)-1.
     """
 
-    def __init__(self, A, T, m, n, nb, ib):
+    def __init__(self, A, T, m, n, nb, ib, T2=None, h=0):
         self.A, self.T, self.m, self.n, self.nb, self.ib = A, T, m, n, nb, ib
+        self.T2, self.h = T2, h   # tree variant: DTTQRT T strips and domain size
 
     def R(self) -> np.ndarray:
         """The min(m,n) x n upper-trapezoidal R factor."""
@@ -104,6 +111,10 @@ class Factored:
     def tstrip(self, i, k):
         nb, ib = self.nb, self.ib
         return self.T[i * ib:(i + 1) * ib, k * nb:(k + 1) * nb]
+
+    def tstrip2(self, i, k):
+        nb, ib = self.nb, self.ib
+        return self.T2[i * ib:(i + 1) * ib, k * nb:(k + 1) * nb]
 
 
 def tiled_qr(A, nb: int, ib: int) -> Factored:
@@ -135,12 +146,54 @@ def tiled_qr_ordered(A, nb: int, ib: int, tasks) -> Factored:
     return Factored(A, T, m, n, nb, ib)
 
 
+def _tree_arrays(m, n, nb, ib):
+    p = -(-m // nb) if m else 0
+    T = np.zeros((max(p * ib, 1), max(n, 1)), dtype=np.float64, order="F")
+    return T, np.zeros_like(T, order="F")
+
+
+def tiled_qr_tree(A, nb: int, ib: int, h: int) -> Factored:
+    """The tree variant on a copy of A: domains of h tile rows per step,
+    heads merged pairwise by DTTQRT (h <= 0 or h >= p: Algorithm 2)."""
+    lib = _load()
+    A = _fortran(A)
+    m, n = A.shape
+    T, T2 = _tree_arrays(m, n, nb, ib)
+    rc = lib.oracle_tiled_qr_tree(m, n, _dp(A), max(m, 1), nb, ib, int(h), _dp(T), T.shape[0], _dp(T2),
+                                  T2.shape[0])
+    if rc:
+        raise ValueError(f"oracle_tiled_qr_tree: illegal argument {rc}")
+    return Factored(A, T, m, n, nb, ib, T2, h)
+
+
+def tiled_qr_tree_ordered(A, nb: int, ib: int, h: int, tasks) -> Factored:
+    """The tree variant with its tasks run in the given order (rows {kind,i,j,k})."""
+    lib = _load()
+    A = _fortran(A)
+    m, n = A.shape
+    T, T2 = _tree_arrays(m, n, nb, ib)
+    tk = np.ascontiguousarray(np.asarray(tasks, dtype=np.int32).reshape(-1, 4))
+    rc = lib.oracle_tiled_qr_tree_ordered(m, n, _dp(A), max(m, 1), nb, ib, int(h), _dp(T), T.shape[0],
+                                          _dp(T2), T2.shape[0], tk.shape[0],
+                                          tk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc:
+        raise ValueError(f"oracle_tiled_qr_tree_ordered: illegal argument {rc}")
+    return Factored(A, T, m, n, nb, ib, T2, h)
+
+
 def apply_qt(f: Factored, B) -> np.ndarray:
     """Q^T B for the Q held (as V and T) in a Factored result."""
     lib = _load()
     B = _fortran(B)
     if B.ndim == 1:
         B = B.reshape(-1, 1, order="F")
+    if f.T2 is not None:
+        rc = lib.oracle_apply_qt_tree(f.m, f.n, _dp(f.A), max(f.m, 1), f.nb, f.ib, int(f.h), _dp(f.T),
+                                      f.T.shape[0], _dp(f.T2), f.T2.shape[0], B.shape[1], _dp(B),
+                                      max(f.m, 1))
+        if rc:
+            raise ValueError(f"oracle_apply_qt_tree: illegal argument {rc}")
+        return B
     rc = lib.oracle_apply_qt(f.m, f.n, _dp(f.A), max(f.m, 1), f.nb, f.ib, _dp(f.T),
                              f.T.shape[0], B.shape[1], _dp(B), max(f.m, 1))
     if rc:
@@ -150,6 +203,17 @@ def apply_qt(f: Factored, B) -> np.ndarray:
 
 def solve_ls(f: Factored, B) -> np.ndarray:
     """argmin_X ||A X - B||_F for m >= n: Q^T B then back substitution with R."""
+    if f.T2 is not None:
+        # tree variant: Q^T B, then the triangular solve (library routine)
+        import scipy.linalg
+        if f.m < f.n:
+            raise ValueError("solve_ls needs m >= n")
+        Y = apply_qt(f, B)
+        R = f.A[:f.n, :f.n]
+        d = np.diag(R)
+        if np.any(d == 0.0):
+            raise np.linalg.LinAlgError(f"R({int(np.argmax(d == 0.0))},...) is exactly zero")
+        return scipy.linalg.solve_triangular(np.triu(R), Y[:f.n, :], lower=False)
     lib = _load()
     B = _fortran(B)
     if B.ndim == 1:
@@ -204,6 +268,137 @@ def task_list(m: int, n: int, nb: int):
     return out
 
 
+TASK_TTQRT, TASK_TTSSRFB = 4, 5
+
+
+def _domain(p: int, h: int) -> int:
+    return p if (h <= 0 or h > p) else h
+
+
+def tt_partner(k: int, H: int, e: int) -> int:
+    """Head row that domain head e is merged into at step k (level ctz(d))."""
+    d = (e - k) // H
+    lev = (d & -d).bit_length() - 1
+    return k + (d - (1 << lev)) * H
+
+
+def task_list_tree(m: int, n: int, nb: int, h: int):
+    """Tasks {kind, i, j, k} of the tree variant in the oracle's sequential
+    order (oracle_tiled_qr_tree); h <= 0 or h >= p gives task_list."""
+    p, q, _, _ = geometry(m, n, nb)
+    H = _domain(p, h)
+    out = []
+    for k in range(min(p, q)):
+        ndom = -(-(p - k) // H)
+        for d in range(ndom):
+            hd = k + d * H
+            last = min(hd + H, p) - 1
+            out.append((TASK_GEQRT, hd, k, k))
+            for j in range(k + 1, q):
+                out.append((TASK_LARFB, hd, j, k))
+            for i in range(hd + 1, last + 1):
+                out.append((TASK_TSQRT, i, k, k))
+                for j in range(k + 1, q):
+                    out.append((TASK_SSRFB, i, j, k))
+        lev = 0
+        while (1 << lev) < ndom:
+            for d in range(0, ndom - (1 << lev), 2 << lev):
+                e = k + (d + (1 << lev)) * H
+                out.append((TASK_TTQRT, e, k, k))
+                for j in range(k + 1, q):
+                    out.append((TASK_TTSSRFB, e, j, k))
+            lev += 1
+    return out
+
+
+def task_access_tree(kind: int, i: int, j: int, k: int, H: int):
+    """(reads, writes) of a task of the tree variant.  A head tile's upper
+    triangle ('R', r, k) holds its R (then the DTTQRT reflectors), its strict
+    lower part ('V', r, k) the DGEQRT reflectors; ('T2', r, k) is the DTTQRT
+    T strip."""
+    if kind == TASK_GEQRT:
+        return {("A", i, k)}, {("R", i, k), ("V", i, k), ("T", i, k)}
+    if kind == TASK_LARFB:
+        return {("V", i, k), ("T", i, k)}, {("A", i, j)}
+    if kind == TASK_TSQRT:
+        return set(), {("R", k + ((i - k) // H) * H, k), ("A", i, k), ("T", i, k)}
+    if kind == TASK_SSRFB:
+        return {("A", i, k), ("T", i, k)}, {("A", k + ((i - k) // H) * H, j), ("A", i, j)}
+    if kind == TASK_TTQRT:
+        return set(), {("R", tt_partner(k, H, i), k), ("R", i, k), ("T2", i, k)}
+    return {("R", i, k), ("T2", i, k)}, {("A", tt_partner(k, H, i), j), ("A", i, j)}
+
+
+def _mechanical_deps(tasks, access):
+    last_w, readers = {}, {}
+    preds = {}
+    for t in tasks:
+        r, w = access(t)
+        ps = set()
+        for d in r | w:
+            if d in last_w:
+                ps.add(last_w[d])
+        for d in w:
+            ps |= readers.get(d, set())
+        preds[t] = ps - {t}
+        for d in r:
+            readers.setdefault(d, set()).add(t)
+        for d in w:
+            last_w[d] = t
+            readers[d] = set()
+    return preds
+
+
+def dependencies_tree(m: int, n: int, nb: int, h: int):
+    """Predecessor sets of the tree variant, derived from the reads and
+    writes of its sequential order exactly as dependencies() does."""
+    p, _, _, _ = geometry(m, n, nb)
+    H = _domain(p, h)
+    tasks = task_list_tree(m, n, nb, h)
+    return tasks, _mechanical_deps(tasks, lambda t: task_access_tree(*t, H))
+
+
+def apply_task_list_tree(m: int, n: int, nb: int, h: int):
+    """Q^T applied to one block column of right-hand sides: the update tasks
+    of the tree variant replayed on the row blocks of B, as {kind, i, k}
+    (kind TASK_LARFB / TASK_SSRFB / TASK_TTSSRFB) in sequential order."""
+    p, q, _, _ = geometry(m, n, nb)
+    H = _domain(p, h)
+    out = []
+    for k in range(min(p, q)):
+        ndom = -(-(p - k) // H)
+        for d in range(ndom):
+            hd = k + d * H
+            last = min(hd + H, p) - 1
+            out.append((TASK_LARFB, hd, k))
+            for i in range(hd + 1, last + 1):
+                out.append((TASK_SSRFB, i, k))
+        lev = 0
+        while (1 << lev) < ndom:
+            for d in range(0, ndom - (1 << lev), 2 << lev):
+                out.append((TASK_TTSSRFB, k + (d + (1 << lev)) * H, k))
+            lev += 1
+    return out
+
+
+def apply_dependencies_tree(m: int, n: int, nb: int, h: int):
+    """Predecessor sets of the Q^T application on one block column, from the
+    row blocks of B each task reads and writes."""
+    p, _, _, _ = geometry(m, n, nb)
+    H = _domain(p, h)
+    tasks = apply_task_list_tree(m, n, nb, h)
+
+    def access(t):
+        kind, i, k = t
+        if kind == TASK_LARFB:
+            return set(), {("B", i)}
+        if kind == TASK_SSRFB:
+            return set(), {("B", k + ((i - k) // H) * H), ("B", i)}
+        return set(), {("B", tt_partner(k, H, i)), ("B", i)}
+
+    return tasks, _mechanical_deps(tasks, access)
+
+
 def task_access(kind: int, i: int, j: int, k: int):
     """(reads, writes) of one task as sets of data items, from the kernel
     definitions of Sec. 3.2.1.  The diagonal tile is split into its R part
@@ -246,8 +441,8 @@ def dependencies(m: int, n: int, nb: int):
     return tasks, preds
 
 
-def random_topological_order(m: int, n: int, nb: int, rng: np.random.Generator):
-    tasks, preds = dependencies(m, n, nb)
+def random_topological_order(m: int, n: int, nb: int, rng: np.random.Generator, h: int = 0):
+    tasks, preds = dependencies_tree(m, n, nb, h) if h > 0 else dependencies(m, n, nb)
     succ = {t: [] for t in tasks}
     indeg = {t: len(preds[t]) for t in tasks}
     for t, ps in preds.items():

@@ -49,7 +49,8 @@ static double g_flops = 0.0;
 /* Deliberate-mistake switch used only by the test that checks the pins catch
  * plausible errors.  0 = correct arithmetic.  1 = apply T instead of T^T in
  * the block updates, 2 = flip the sign of beta, 3 = drop the B_l -= W update
- * in DSSRFB, 4 = drop the T off-diagonal recurrence. */
+ * in DSSRFB, 4 = drop the T off-diagonal recurrence, 5 = leave the diagonal
+ * row out of the triangular reflectors of the tree variant (DTTQRT/DTTSSRFB). */
 static int g_mutation = 0;
 
 void oracle_set_mutation(int m) { g_mutation = m; }
@@ -338,6 +339,107 @@ static void tsqrt(int nc, double *Rk, int ldr, int mrA, double *A, int lda, int 
 }
 
 /* ---------------------------------------------------------------------- */
+/* Tree variant: the triangle-on-triangle kernels.  When the tiles of a panel
+ * column are first reduced to triangles independently (DGEQRT on every
+ * domain head), two triangles are merged by the QR of [R1; R2] with R1 and R2
+ * upper triangular.  Reflector j then has nonzeros only in rows 0..j of the
+ * bottom triangle (the rows below are zero and stay zero), so the kernels
+ * below are DTSQRT and DSSRFB with every row loop cut at that length.  This
+ * is the pairwise reduction of the R factors that shortens the DTSQRT chain
+ * of Algorithm 2 (a variant beyond the paper's flat elimination order). */
+
+/* Rows of reflector j in a bottom triangle with mr rows. */
+static int tt_len(int j, int mr)
+{
+    int len = (g_mutation == 5) ? j : j + 1;
+    return len < mr ? len : mr;
+}
+
+/* DTTSSRFB: [B; C] <- Q^T [B; C] for the nrefl triangular reflectors
+ * VB(:, a), a = 0..nrefl-1, whose global column index is j0 + a (so column a
+ * has tt_len(j0 + a, mrV) meaningful rows), T strip Tk, B the nrefl rows of
+ * the top tile row and C the bottom tile row (ncols columns).  Per inner
+ * block l: W = T_l^T (B_l + VB_l^T C); B_l -= W; C -= VB_l W. */
+static void ttssrfb_t(int nrefl, int j0, int mrV, const double *VB, int ldv, const double *Tk, int ldt,
+                      int ib, double *B, int ldb, double *C, int ldc, int ncols, double *work)
+{
+    for (int l0 = 0; l0 < nrefl; l0 += ib) {
+        int sb = imin(ib, nrefl - l0);
+        double *W = work;
+        for (int c = 0; c < ncols; c++)
+            for (int a = 0; a < sb; a++) {
+                int len = tt_len(j0 + l0 + a, mrV);
+                double acc = EL(B, ldb, l0 + a, c);
+                for (int r = 0; r < len; r++)
+                    acc += EL(VB, ldv, r, l0 + a) * EL(C, ldc, r, c);
+                EL(W, sb, a, c) = acc;
+                g_flops += 2.0 * len;
+            }
+        trmm_tt(sb, &EL(Tk, ldt, 0, l0), ldt, ncols, W, sb);
+        for (int c = 0; c < ncols; c++)
+            for (int a = 0; a < sb; a++)
+                EL(B, ldb, l0 + a, c) -= EL(W, sb, a, c);
+        g_flops += (double)sb * ncols;
+        for (int c = 0; c < ncols; c++)
+            for (int a = 0; a < sb; a++) {
+                int len = tt_len(j0 + l0 + a, mrV);
+                for (int r = 0; r < len; r++)
+                    EL(C, ldc, r, c) -= EL(VB, ldv, r, l0 + a) * EL(W, sb, a, c);
+                g_flops += 2.0 * len;
+            }
+    }
+}
+
+/* DTTQRT: QR of [R1; R2] with R1 the nc x nc upper triangle of the top tile
+ * Rk and R2 the upper trapezoid (entries (r, c), r <= c) of the mrB x nc
+ * bottom tile B.  R1 is updated in place; the trapezoid of B is overwritten
+ * by the reflector parts; entries of B below its diagonal are neither read
+ * nor written (they hold the DGEQRT reflectors of that tile).  T strip to
+ * Tk.  Inner blocking as in DTSQRT. */
+static void ttqrt(int nc, double *Rk, int ldr, int mrB, double *B, int ldb, int ib, double *Tk, int ldt,
+                  double *work)
+{
+    for (int l0 = 0; l0 < nc; l0 += ib) {
+        int sb = imin(ib, nc - l0);
+        double *Tl = &EL(Tk, ldt, 0, l0);
+        for (int jj = 0; jj < sb; jj++)
+            for (int ii = 0; ii < ib; ii++)
+                EL(Tl, ldt, ii, jj) = 0.0;
+        for (int jj = 0; jj < sb; jj++) {
+            int j = l0 + jj, len = tt_len(j, mrB);
+            double beta, tau;
+            make_reflector(EL(Rk, ldr, j, j), len, &EL(B, ldb, 0, j), &beta, &tau);
+            EL(Rk, ldr, j, j) = beta;
+            for (int c = j + 1; c < l0 + sb; c++) {
+                double w = EL(Rk, ldr, j, c);
+                for (int r = 0; r < len; r++)
+                    w += EL(B, ldb, r, j) * EL(B, ldb, r, c);
+                EL(Rk, ldr, j, c) -= tau * w;
+                for (int r = 0; r < len; r++)
+                    EL(B, ldb, r, c) -= tau * EL(B, ldb, r, j) * w;
+                g_flops += 4.0 * len + 2.0;
+            }
+            EL(Tl, ldt, jj, jj) = tau;
+        }
+        /* Gram entries: column ii < jj is the shorter one */
+        for (int jj = 0; jj < sb; jj++)
+            for (int ii = 0; ii < jj; ii++) {
+                int len = tt_len(l0 + ii, mrB);
+                double g = 0.0;
+                for (int r = 0; r < len; r++)
+                    g += EL(B, ldb, r, l0 + ii) * EL(B, ldb, r, l0 + jj);
+                EL(Tl, ldt, ii, jj) = g;
+                g_flops += 2.0 * len;
+            }
+        t_recurrence(sb, Tl, ldt);
+        int ntr = nc - (l0 + sb);
+        if (ntr > 0)
+            ttssrfb_t(sb, l0, mrB, &EL(B, ldb, 0, l0), ldb, Tl, ldt, ib, &EL(Rk, ldr, l0, l0 + sb), ldr,
+                      &EL(B, ldb, 0, l0 + sb), ldb, ntr, work);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
 /* Tile geometry helpers. */
 typedef struct {
     int64_t m, n;
@@ -366,30 +468,73 @@ static double *tstrip(const geom *g, double *T, int64_t ldt, int i, int k)
     return &T[(size_t)k * g->nb * (size_t)ldt + (size_t)i * g->ib];
 }
 
-/* Task kinds, in the paper's priority order (Sec. 4). */
-enum { TASK_GEQRT = 0, TASK_TSQRT = 1, TASK_LARFB = 2, TASK_SSRFB = 3 };
+/* Task kinds, in the paper's priority order (Sec. 4), then the two kernels
+ * of the tree variant. */
+enum { TASK_GEQRT = 0, TASK_TSQRT = 1, TASK_LARFB = 2, TASK_SSRFB = 3, TASK_TTQRT = 4, TASK_TTSSRFB = 5 };
 
-static void run_task(const geom *g, double *A, int64_t lda, double *T, int64_t ldt, int kind, int i,
-                     int j, int k, double *work)
+/* Elimination tree.  At step k the tile rows k..p-1 form domains of H
+ * consecutive rows starting at row k (the last one may be shorter); the head
+ * row of each domain is reduced by DGEQRT, the other rows of the domain are
+ * eliminated into it by the DTSQRT chain of Algorithm 2, and the heads are
+ * then merged pairwise by DTTQRT: at level l, head of domain d + 2^l into
+ * head of domain d for d a multiple of 2^(l+1).  H >= p - k is Algorithm 2's
+ * flat order. */
+typedef struct {
+    double *T2;    /* T strips of the DTTQRT reflectors, laid out like T */
+    int64_t ldt2;
+    int H;         /* domain size in tiles */
+} tree_ctx;
+
+static int dom_size(const geom *g, int h) { return (h <= 0 || h > g->p) ? g->p : h; }
+static int head_of(int k, int H, int i) { return k + ((i - k) / H) * H; }
+/* head row that domain head e is merged into (its partner at level ctz(d)) */
+static int tt_partner(int k, int H, int e)
 {
+    int d = (e - k) / H, lev = 0;
+    while (!((d >> lev) & 1))
+        lev++;
+    return k + (d - (1 << lev)) * H;
+}
+
+static void run_task(const geom *g, double *A, int64_t lda, double *T, int64_t ldt, const tree_ctx *tc,
+                     int kind, int i, int j, int k, double *work)
+{
+    int H = tc ? tc->H : g->p;
     switch (kind) {
     case TASK_GEQRT:
-        geqrt(mr_of(g, k), nc_of(g, k), g->ib, tile(g, A, lda, k, k), (int)lda,
-              tstrip(g, T, ldt, k, k), (int)ldt, work);
+        geqrt(mr_of(g, i), nc_of(g, k), g->ib, tile(g, A, lda, i, k), (int)lda,
+              tstrip(g, T, ldt, i, k), (int)ldt, work);
         break;
     case TASK_LARFB:
-        larfb_t(mr_of(g, k), nc_of(g, k), tile(g, A, lda, k, k), (int)lda, tstrip(g, T, ldt, k, k),
-                (int)ldt, g->ib, tile(g, A, lda, k, j), (int)lda, nc_of(g, j), work);
+        larfb_t(mr_of(g, i), nc_of(g, k), tile(g, A, lda, i, k), (int)lda, tstrip(g, T, ldt, i, k),
+                (int)ldt, g->ib, tile(g, A, lda, i, j), (int)lda, nc_of(g, j), work);
         break;
-    case TASK_TSQRT:
-        tsqrt(nc_of(g, k), tile(g, A, lda, k, k), (int)lda, mr_of(g, i), tile(g, A, lda, i, k),
+    case TASK_TSQRT: {
+        int hd = head_of(k, H, i);
+        tsqrt(nc_of(g, k), tile(g, A, lda, hd, k), (int)lda, mr_of(g, i), tile(g, A, lda, i, k),
               (int)lda, g->ib, tstrip(g, T, ldt, i, k), (int)ldt, work);
         break;
-    case TASK_SSRFB:
+    }
+    case TASK_SSRFB: {
+        int hd = head_of(k, H, i);
         ssrfb_t(nc_of(g, k), mr_of(g, i), tile(g, A, lda, i, k), (int)lda, tstrip(g, T, ldt, i, k),
-                (int)ldt, g->ib, tile(g, A, lda, k, j), (int)lda, tile(g, A, lda, i, j), (int)lda,
+                (int)ldt, g->ib, tile(g, A, lda, hd, j), (int)lda, tile(g, A, lda, i, j), (int)lda,
                 nc_of(g, j), work);
         break;
+    }
+    case TASK_TTQRT: {
+        int pt = tt_partner(k, H, i);
+        ttqrt(nc_of(g, k), tile(g, A, lda, pt, k), (int)lda, mr_of(g, i), tile(g, A, lda, i, k), (int)lda,
+              g->ib, tstrip(g, tc->T2, tc->ldt2, i, k), (int)tc->ldt2, work);
+        break;
+    }
+    case TASK_TTSSRFB: {
+        int pt = tt_partner(k, H, i);
+        ttssrfb_t(nc_of(g, k), 0, mr_of(g, i), tile(g, A, lda, i, k), (int)lda,
+                  tstrip(g, tc->T2, tc->ldt2, i, k), (int)tc->ldt2, g->ib, tile(g, A, lda, pt, j), (int)lda,
+                  tile(g, A, lda, i, j), (int)lda, nc_of(g, j), work);
+        break;
+    }
     }
 }
 
@@ -427,13 +572,13 @@ int oracle_tiled_qr(int64_t m, int64_t n, double *A, int64_t lda, int nb, int ib
     double *work = malloc(sizeof(double) * (size_t)ib * nb);
     int kmax = g.p < g.q ? g.p : g.q;
     for (int k = 0; k < kmax; k++) {
-        run_task(&g, A, lda, T, ldt, TASK_GEQRT, k, k, k, work);
+        run_task(&g, A, lda, T, ldt, NULL, TASK_GEQRT, k, k, k, work);
         for (int j = k + 1; j < g.q; j++)
-            run_task(&g, A, lda, T, ldt, TASK_LARFB, k, j, k, work);
+            run_task(&g, A, lda, T, ldt, NULL, TASK_LARFB, k, j, k, work);
         for (int i = k + 1; i < g.p; i++) {
-            run_task(&g, A, lda, T, ldt, TASK_TSQRT, i, k, k, work);
+            run_task(&g, A, lda, T, ldt, NULL, TASK_TSQRT, i, k, k, work);
             for (int j = k + 1; j < g.q; j++)
-                run_task(&g, A, lda, T, ldt, TASK_SSRFB, i, j, k, work);
+                run_task(&g, A, lda, T, ldt, NULL, TASK_SSRFB, i, j, k, work);
         }
     }
     free(work);
@@ -459,7 +604,7 @@ int oracle_tiled_qr_ordered(int64_t m, int64_t n, double *A, int64_t lda, int nb
     double *work = malloc(sizeof(double) * (size_t)ib * nb);
     for (int64_t t = 0; t < ntasks; t++) {
         const int32_t *tk = &tasks[4 * t];
-        run_task(&g, A, lda, T, ldt, tk[0], tk[1], tk[2], tk[3], work);
+        run_task(&g, A, lda, T, ldt, NULL, tk[0], tk[1], tk[2], tk[3], work);
     }
     free(work);
     return 0;
@@ -489,6 +634,128 @@ int oracle_apply_qt(int64_t m, int64_t n, const double *A, int64_t lda, int nb, 
             ssrfb_t(nc_of(&g, k), mr_of(&g, i), tile(&g, Am, lda, i, k), (int)lda,
                     tstrip(&g, Tm, ldt, i, k), (int)ldt, ib, Bk, (int)ldb, &B[(size_t)i * nb],
                     (int)ldb, (int)nrhs, work);
+    }
+    free(work);
+    return 0;
+}
+
+/* The tree variant (domains of h tile rows, pairwise merging of the domain
+ * heads; see tree_ctx) executed sequentially: per step k, every domain's
+ * DGEQRT + DLARFB row, then its DTSQRT chain with the DSSRFB rows, then the
+ * merge levels in order, each DTTQRT followed by its DTTSSRFB row.  T2
+ * (ldt2 >= p*ib rows, n columns, zeroed first) receives the DTTQRT T strips.
+ * h <= 0 or h >= p gives exactly oracle_tiled_qr. */
+int oracle_tiled_qr_tree(int64_t m, int64_t n, double *A, int64_t lda, int nb, int ib, int h, double *T,
+                         int64_t ldt, double *T2, int64_t ldt2)
+{
+    int rc = check_args(m, n, lda, nb, ib, ldt);
+    if (rc)
+        return rc;
+    geom g = make_geom(m, n, nb, ib);
+    if (ldt < (int64_t)g.p * ib)
+        return -9;
+    if (ldt2 < (int64_t)g.p * ib)
+        return -11;
+    for (int64_t c = 0; c < n; c++) {
+        for (int64_t r = 0; r < ldt; r++)
+            T[c * ldt + r] = 0.0;
+        for (int64_t r = 0; r < ldt2; r++)
+            T2[c * ldt2 + r] = 0.0;
+    }
+    tree_ctx tc = {T2, ldt2, dom_size(&g, h)};
+    const int H = tc.H;
+    double *work = malloc(sizeof(double) * (size_t)ib * nb);
+    int kmax = g.p < g.q ? g.p : g.q;
+    for (int k = 0; k < kmax; k++) {
+        int ndom = (g.p - k + H - 1) / H;
+        for (int d = 0; d < ndom; d++) {
+            int hd = k + d * H, last = imin(hd + H, g.p) - 1;
+            run_task(&g, A, lda, T, ldt, &tc, TASK_GEQRT, hd, k, k, work);
+            for (int j = k + 1; j < g.q; j++)
+                run_task(&g, A, lda, T, ldt, &tc, TASK_LARFB, hd, j, k, work);
+            for (int i = hd + 1; i <= last; i++) {
+                run_task(&g, A, lda, T, ldt, &tc, TASK_TSQRT, i, k, k, work);
+                for (int j = k + 1; j < g.q; j++)
+                    run_task(&g, A, lda, T, ldt, &tc, TASK_SSRFB, i, j, k, work);
+            }
+        }
+        for (int lev = 0; (1 << lev) < ndom; lev++)
+            for (int d = 0; d + (1 << lev) < ndom; d += 2 << lev) {
+                int e = k + (d + (1 << lev)) * H;
+                run_task(&g, A, lda, T, ldt, &tc, TASK_TTQRT, e, k, k, work);
+                for (int j = k + 1; j < g.q; j++)
+                    run_task(&g, A, lda, T, ldt, &tc, TASK_TTSSRFB, e, j, k, work);
+            }
+    }
+    free(work);
+    return 0;
+}
+
+/* The tree variant with the tasks run in a caller-given order (rows {kind,
+ * i, j, k}, kinds TASK_*); the order must respect the dependencies. */
+int oracle_tiled_qr_tree_ordered(int64_t m, int64_t n, double *A, int64_t lda, int nb, int ib, int h,
+                                 double *T, int64_t ldt, double *T2, int64_t ldt2, int64_t ntasks,
+                                 const int32_t *tasks)
+{
+    int rc = check_args(m, n, lda, nb, ib, ldt);
+    if (rc)
+        return rc;
+    geom g = make_geom(m, n, nb, ib);
+    if (ldt < (int64_t)g.p * ib)
+        return -9;
+    if (ldt2 < (int64_t)g.p * ib)
+        return -11;
+    for (int64_t c = 0; c < n; c++) {
+        for (int64_t r = 0; r < ldt; r++)
+            T[c * ldt + r] = 0.0;
+        for (int64_t r = 0; r < ldt2; r++)
+            T2[c * ldt2 + r] = 0.0;
+    }
+    tree_ctx tc = {T2, ldt2, dom_size(&g, h)};
+    double *work = malloc(sizeof(double) * (size_t)ib * nb);
+    for (int64_t t = 0; t < ntasks; t++) {
+        const int32_t *tk = &tasks[4 * t];
+        run_task(&g, A, lda, T, ldt, &tc, tk[0], tk[1], tk[2], tk[3], work);
+    }
+    free(work);
+    return 0;
+}
+
+/* B (m x nrhs) <- Q^T B for a factorization by oracle_tiled_qr_tree (same h):
+ * the update kernels replayed on the rows of B in the sequential order of
+ * the tree variant. */
+int oracle_apply_qt_tree(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib, int h,
+                         const double *T, int64_t ldt, const double *T2, int64_t ldt2, int64_t nrhs, double *B,
+                         int64_t ldb)
+{
+    int rc = check_args(m, n, lda, nb, ib, ldt);
+    if (rc)
+        return rc;
+    if (ldb < (m > 1 ? m : 1))
+        return -14;
+    geom g = make_geom(m, n, nb, ib);
+    const int H = dom_size(&g, h);
+    double *work = malloc(sizeof(double) * (size_t)ib * (size_t)(nrhs > 0 ? nrhs : 1));
+    int kmax = g.p < g.q ? g.p : g.q;
+    double *Am = (double *)A, *Tm = (double *)T, *T2m = (double *)T2;
+    for (int k = 0; k < kmax; k++) {
+        int ndom = (g.p - k + H - 1) / H, nck = nc_of(&g, k);
+        for (int d = 0; d < ndom; d++) {
+            int hd = k + d * H, last = imin(hd + H, g.p) - 1;
+            double *Bh = &B[(size_t)hd * nb];
+            larfb_t(mr_of(&g, hd), nck, tile(&g, Am, lda, hd, k), (int)lda, tstrip(&g, Tm, ldt, hd, k),
+                    (int)ldt, ib, Bh, (int)ldb, (int)nrhs, work);
+            for (int i = hd + 1; i <= last; i++)
+                ssrfb_t(nck, mr_of(&g, i), tile(&g, Am, lda, i, k), (int)lda, tstrip(&g, Tm, ldt, i, k),
+                        (int)ldt, ib, Bh, (int)ldb, &B[(size_t)i * nb], (int)ldb, (int)nrhs, work);
+        }
+        for (int lev = 0; (1 << lev) < ndom; lev++)
+            for (int d = 0; d + (1 << lev) < ndom; d += 2 << lev) {
+                int e = k + (d + (1 << lev)) * H, pt = k + d * H;
+                ttssrfb_t(nck, 0, mr_of(&g, e), tile(&g, Am, lda, e, k), (int)lda,
+                          tstrip(&g, T2m, ldt2, e, k), (int)ldt2, ib, &B[(size_t)pt * nb], (int)ldb,
+                          &B[(size_t)e * nb], (int)ldb, (int)nrhs, work);
+            }
     }
     free(work);
     return 0;
