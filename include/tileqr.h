@@ -81,7 +81,13 @@ enum {
  *   storage is required for the V and R tiles").
  * T: one strip of ib*nb doubles per tile, strip (i,k) at offset
  *   ((k*p)+i)*ib*nb, column-major ib x nb: t = nb/ib upper-triangular ib x ib
- *   blocks side by side (the s x s T_i of Sec. 3.2.3), lower parts zero. */
+ *   blocks side by side (the s x s T_i of Sec. 3.2.3), lower parts zero.
+ * Tree form (tileqr_factor_tree, domain < p): at step k the tile rows
+ *   k..p-1 form domains of `domain` rows from row k; tile (i,k) of a domain
+ *   head i holds its DGEQRT reflectors below the diagonal and, for i > k,
+ *   the reflectors of the merge DTTQRT(i,k) on and above it (upper
+ *   triangular); their T strips are in T2, laid out like T.  T2 is NULL for
+ *   the flat form (domain == p: Algorithm 2). */
 typedef struct tileqr_desc {
     int64_t m, n;
     int32_t nb, ib;
@@ -94,6 +100,9 @@ typedef struct tileqr_desc {
     size_t sched_bytes;
     void *workspace;
     size_t workspace_bytes;
+    int32_t domain;       /* domain size of the elimination tree (p: flat) */
+    int32_t reserved;
+    double *T2;           /* DTTQRT T strips (tree form), else NULL */
 } tileqr_desc;
 
 /* Bytes of device workspace tileqr_factor needs for an m x n matrix (the
@@ -117,6 +126,24 @@ int tileqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int precision, s
 int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib,
                   int precision, int schedule, int flags, void *workspace, size_t ws_bytes,
                   tileqr_stream_t stream, tileqr_desc *out);
+
+/* Tree form of the factorization, for tall matrices: the panel column of
+ * step k is eliminated in domains of `domain` tile rows (each a DGEQRT plus
+ * the DTSQRT chain of Algorithm 2 into the domain head), and the domain heads
+ * are merged pairwise (binary tree, log2 depth) by the triangle-on-triangle
+ * kernels DTTQRT / DTTMQR.  This shortens Algorithm 2's serial DTSQRT chain
+ * of p - k tasks per step (the critical path of Sec. 4 for p >> q) to about
+ * domain + log2(p / domain); it is a variant beyond the paper's flat
+ * elimination order.  R is the same matrix up to rounding and row signs;
+ * Q is a different product of reflectors (see tileqr_desc).
+ *   domain  1 <= domain; domain >= p (or 0) gives exactly tileqr_factor
+ *   other arguments as tileqr_factor (task-graph schedule only)
+ * Returns 0, -i, TILEQR_ERR_WORKSPACE, TILEQR_ERR_UNSUPPORTED or
+ * TILEQR_ERR_CUDA. */
+int tileqr_workspace_size_tree(int64_t m, int64_t n, int nb, int ib, int precision, int domain, size_t *bytes);
+int tileqr_factor_tree(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib, int domain,
+                       int precision, int flags, void *workspace, size_t ws_bytes, tileqr_stream_t stream,
+                       tileqr_desc *out);
 
 /* tileqr_factor_noalloc -- the same FP64 factorization (persistent task-graph
  * kernel, same results as tileqr_factor with TILEQR_SCHED_DAG) for callers
@@ -173,8 +200,15 @@ int tileqr_get_R(const tileqr_desc *d, double *R, int64_t ldr, tileqr_stream_t s
 int tileqr_get_factors(const tileqr_desc *d, double *AV, int64_t ldav, double *T, int64_t ldt,
                        tileqr_stream_t stream);
 
+/* Copies the DTTQRT T strips of a tree-form factorization as a (p*ib) x n
+ * column-major device array (ldt >= p*ib), strip (i,k) at rows i*ib..,
+ * columns k*nb.. (zero for rows that are not merged at step k).  Returns
+ * TILEQR_ERR_UNSUPPORTED for a flat factorization. */
+int tileqr_get_tree_T(const tileqr_desc *d, double *T2, int64_t ldt, tileqr_stream_t stream);
+
 /* B <- Q^T B for the Q of a factorization (Sec. 3.2.1: the DLARFB and DSSRFB
- * transformations replayed on the columns of B in the order of Algorithm 2).
+ * transformations replayed on the columns of B in the order of Algorithm 2;
+ * for the tree form also the DTTMQR merges).
  *   B, ldb    device, column-major m x nrhs, ldb >= max(1,m), in place
  *   workspace device scratch of tileqr_apply_workspace_size() bytes
  * Asynchronous. */
@@ -254,8 +288,8 @@ int tileqr_refine_workspace_size(const tileqr_desc *d, size_t *bytes);
  *   b        device, m entries;   x  device, n entries (output)
  *   max_iter refinement steps (outer iterations) at most
  * Synchronous.  Returns 0 (also when not converged: see info), -i,
- * TILEQR_ERR_SINGULAR, TILEQR_ERR_WORKSPACE, TILEQR_ERR_UNSUPPORTED,
- * TILEQR_ERR_CUDA. */
+ * TILEQR_ERR_SINGULAR, TILEQR_ERR_WORKSPACE, TILEQR_ERR_UNSUPPORTED (also for a
+ * tree-form factorization), TILEQR_ERR_CUDA. */
 int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_t lda, const double *b, double *x,
                         int max_iter, double tol, void *workspace, size_t ws_bytes, tileqr_stream_t stream,
                         tileqr_refine_info *info);
@@ -276,12 +310,28 @@ void tileqr_set_profile_events(void *before, void *after);
 /* Task trace (the execution-flow view of Sec. 4, Fig. 6): if `records` is a
  * device buffer of `capacity` records of 4 uint64 each, every later
  * tileqr_factor with TILEQR_SCHED_DAG writes one record per executed task:
- * {task code (k << 42 | i << 21 | j), start ns, end ns (%globaltimer), SM id}.
+ * {task code (tt << 63 | k << 42 | i << 21 | j; tt = 1 for the tree form's
+ * DTTQRT / DTTMQR), start ns, end ns (%globaltimer), SM id}.
  * Records beyond `capacity` are dropped; the number written is readable with
  * tileqr_trace_count after the factorization (synchronises the stream).
  * NULL disables tracing. Host only. */
 void tileqr_set_trace(void *records, uint64_t capacity);
 int tileqr_trace_count(const tileqr_desc *d, tileqr_stream_t stream, uint64_t *count);
+
+/* Task-graph introspection (host only, no CUDA call): the graph that the
+ * persistent kernel executes (Sec. 4's dependency-driven schedule) for an
+ * m x n matrix, tile size nb and domain size `domain` (0: flat).
+ *   what      0 = the factorization; 1 = Q^T applied to one column chunk
+ *             of right-hand sides (tileqr_apply_qt / tileqr_solve_ls)
+ *   tasks     ntasks rows {kind, i, j, k}: kind 0 DGEQRT, 1 DTSQRT, 2 DLARFB,
+ *             3 DSSRFB, 4 DTTQRT, 5 DTTMQR; j = -1 for what = 1
+ *   ndeps     per task, the number of predecessors that release it
+ *   succ_ptr  ntasks + 1 offsets into succ (CSR); succ: successor indices
+ * Call with tasks == NULL to get *ntasks and *nedges, then again with
+ * buffers of that size (4*ntasks, ntasks, ntasks+1, nedges entries).
+ * Returns 0 or -i (-99: a successor outside the graph, an internal error). */
+int tileqr_task_graph(int64_t m, int64_t n, int nb, int domain, int what, int32_t *tasks, int32_t *ndeps,
+                      int64_t *succ_ptr, int64_t *succ, int64_t *ntasks, int64_t *nedges);
 
 #ifdef __cplusplus
 }

@@ -5,8 +5,11 @@
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <vector>
 
 #include "factor.h"
+#include "graph.cuh"
 
 namespace tqr {
 static std::atomic<unsigned long long> g_launches{0};
@@ -22,6 +25,45 @@ static unsigned long long watchdog_ns_default()
     if (ms <= 0)
         ms = 10000;
     return (unsigned long long)ms * 1000000ull;
+}
+}  // namespace tqr
+
+namespace tqr {
+WsLayout make_layout(int64_t m, int64_t n, int nb, int ib, int h)
+{
+    WsLayout L{};
+    L.m = m;
+    L.n = n;
+    L.nb = nb;
+    L.ib = ib;
+    L.p = (int)((m + nb - 1) / nb);
+    L.q = (int)((n + nb - 1) / nb);
+    L.steps = L.p < L.q ? L.p : L.q;
+    const TGraph G = make_graph(L.p, L.q, h);
+    L.H = G.H;
+    const bool tree = G.H < G.p;
+    const size_t tiles = (size_t)L.p * L.q * nb * nb * sizeof(double);
+    const size_t tst = (size_t)L.p * L.q * ib * nb * sizeof(double);
+    L.off_tiles = 0;
+    L.off_T = align256(tiles);
+    L.off_T2 = L.off_T + align256(tst);
+    L.off_ctrl = L.off_T2 + (tree ? align256(tst) : 0);
+    L.off_cnt = L.off_ctrl + 256;
+    size_t off = L.off_cnt + align256(g_ncounters(G) * sizeof(unsigned int));
+    unsigned long long kinds[6], caps[K_NKIND] = {0, 0, 0, 0};
+    g_count(G, kinds);
+    for (int t = 0; t < 6; t++)
+        caps[kind_prio(t)] += kinds[t];
+    unsigned long long tot = 0;
+    for (int t = 0; t < K_NKIND; t++) {
+        L.cap[t] = (unsigned int)caps[t];
+        tot += caps[t];
+        L.off_q[t] = off;
+        off += align256((size_t)(caps[t] ? caps[t] : 1) * sizeof(unsigned long long));
+    }
+    L.total = (unsigned int)tot;
+    L.end = off;
+    return L;
 }
 }  // namespace tqr
 
@@ -56,9 +98,27 @@ extern "C" int tileqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int p
     return 0;
 }
 
-extern "C" int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib,
-                             int precision, int schedule, int flags, void *workspace, size_t ws_bytes,
-                             tileqr_stream_t stream, tileqr_desc *out)
+extern "C" int tileqr_workspace_size_tree(int64_t m, int64_t n, int nb, int ib, int precision, int domain,
+                                          size_t *bytes)
+{
+    int rc = check_geom(m, n, nb, ib);
+    if (rc)
+        return rc;
+    if (precision != TILEQR_FP64 && precision != TILEQR_TF32 && precision != TILEQR_SPLIT_BF16)
+        return -5;
+    if (domain < 0)
+        return -6;
+    if (!bytes)
+        return -7;
+    *bytes = make_layout(m, n, nb, ib, domain).end;
+    return 0;
+}
+
+// The factorization proper; `domain` 0 = Algorithm 2's flat tree.  Argument
+// errors are reported with the positions of tileqr_factor; the caller remaps.
+static int factor_impl(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib, int domain,
+                       int precision, int schedule, int flags, void *workspace, size_t ws_bytes,
+                       tileqr_stream_t stream, tileqr_desc *out)
 {
     if (m < 0)
         return -1;
@@ -87,7 +147,10 @@ extern "C" int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda,
         return TILEQR_ERR_UNSUPPORTED;
     if (precision == TILEQR_TF32 && (schedule != TILEQR_SCHED_DAG || !factor_mixed_supported(nb, ib)))
         return TILEQR_ERR_UNSUPPORTED;
-    const WsLayout L = make_layout(m, n, nb, ib);
+    const WsLayout L = make_layout(m, n, nb, ib, domain);
+    const bool tree = L.H < L.p;
+    if (tree && schedule != TILEQR_SCHED_DAG)
+        return TILEQR_ERR_UNSUPPORTED;
     if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < L.end)
         return TILEQR_ERR_WORKSPACE;
     char *ws = (char *)workspace;
@@ -108,9 +171,14 @@ extern "C" int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda,
     out->sched_bytes = L.end - L.off_ctrl;
     out->workspace = workspace;
     out->workspace_bytes = ws_bytes;
+    out->domain = L.H;
+    out->T2 = tree ? (double *)(ws + L.off_T2) : nullptr;
 
     // reset the scheduler state (control block, counters, queues)
     if (cudaMemsetAsync(ws + L.off_ctrl, 0, L.end - L.off_ctrl, st) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    // T2 strips of rows that are not merged stay zero (documented contents)
+    if (tree && cudaMemsetAsync(ws + L.off_T2, 0, L.off_ctrl - L.off_T2, st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
     if (m == 0 || n == 0)
         return 0;
@@ -133,6 +201,27 @@ extern "C" int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda,
         rc = launch_factor(L, ws, schedule, flags, st, wd, g_trace, tcap);
     if (rc == 0 && g_ev_before && g_ev_after && cudaEventRecord(g_ev_after, st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
+    return rc;
+}
+
+extern "C" int tileqr_factor(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib,
+                             int precision, int schedule, int flags, void *workspace, size_t ws_bytes,
+                             tileqr_stream_t stream, tileqr_desc *out)
+{
+    return factor_impl(m, n, A, lda, nb, ib, 0, precision, schedule, flags, workspace, ws_bytes, stream, out);
+}
+
+extern "C" int tileqr_factor_tree(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib, int domain,
+                                  int precision, int flags, void *workspace, size_t ws_bytes,
+                                  tileqr_stream_t stream, tileqr_desc *out)
+{
+    if (domain < 0)
+        return -7;
+    const int rc = factor_impl(m, n, A, lda, nb, ib, domain, precision, TILEQR_SCHED_DAG, flags, workspace,
+                               ws_bytes, stream, out);
+    // positions of tileqr_factor_tree: precision 8, out 13
+    if (rc == -7)
+        return -8;
     return rc;
 }
 
@@ -166,6 +255,21 @@ extern "C" int tileqr_get_R(const tileqr_desc *d, double *R, int64_t ldr, tileqr
     return launch_tile2cm(d->tiles, d->nb, d->p, d->q, d->m, d->n, R, ldr, 1, k, (cudaStream_t)stream);
 }
 
+extern "C" int tileqr_get_tree_T(const tileqr_desc *d, double *T2, int64_t ldt, tileqr_stream_t stream)
+{
+    if (d == nullptr)
+        return -1;
+    if (d->T2 == nullptr)
+        return TILEQR_ERR_UNSUPPORTED;
+    if (T2 == nullptr && d->n > 0)
+        return -2;
+    if (ldt < (int64_t)d->p * d->ib || ldt < 1)
+        return -3;
+    if (d->m == 0 || d->n == 0)
+        return 0;
+    return launch_strips2cm(d->T2, d->nb, d->ib, d->p, d->q, d->n, T2, ldt, (cudaStream_t)stream);
+}
+
 extern "C" int tileqr_get_factors(const tileqr_desc *d, double *AV, int64_t ldav, double *T, int64_t ldt,
                                   tileqr_stream_t stream)
 {
@@ -195,7 +299,7 @@ extern "C" int tileqr_apply_workspace_size(const tileqr_desc *d, int64_t nrhs, s
         return -2;
     if (bytes == nullptr)
         return -3;
-    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib);
+    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib, d->domain);
     const int64_t ncp = apply_ncp(nrhs);
     *bytes = align256((size_t)L.p * L.nb * ncp * sizeof(double)) + apply_sched_bytes(L, (int)(ncp / APPLY_W)) + 256;
     return 0;
@@ -214,7 +318,7 @@ static int apply_core(const tileqr_desc *d, const WsLayout &L, double *B, int64_
     int rc = launch_cm2rows(B, ldb, d->m, nrhs, Bt, d->nb, d->p, ncp, st);
     if (rc)
         return rc;
-    rc = launch_apply(L, d->tiles, d->T, Bt, ncp, sched, st, watchdog_ns_default());
+    rc = launch_apply(L, d->tiles, d->T, d->T2, Bt, ncp, sched, st, watchdog_ns_default());
     *Bt_out = Bt;
     *ncp_out = ncp;
     *flag_out = flag;
@@ -238,7 +342,7 @@ extern "C" int tileqr_apply_qt(const tileqr_desc *d, double *B, int64_t ldb, int
         return TILEQR_ERR_WORKSPACE;
     if (nrhs == 0 || d->m == 0 || d->n == 0)
         return 0;
-    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib);
+    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib, d->domain);
     cudaStream_t st = (cudaStream_t)stream;
     double *Bt;
     int64_t ncp;
@@ -268,7 +372,7 @@ extern "C" int tileqr_solve_ls(const tileqr_desc *d, double *B, int64_t ldb, int
         return TILEQR_ERR_WORKSPACE;
     if (nrhs == 0 || d->n == 0)
         return 0;
-    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib);
+    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib, d->domain);
     cudaStream_t st = (cudaStream_t)stream;
     double *Bt;
     int64_t ncp;
@@ -346,4 +450,103 @@ extern "C" void tileqr_set_profile_events(void *before, void *after)
 {
     g_ev_before = (cudaEvent_t)before;
     g_ev_after = (cudaEvent_t)after;
+}
+
+// ---------------------------------------------------------------------------
+// Task-graph introspection (host only): enumerate the tasks of the graph the
+// kernels execute and their successors, from the same functions.
+
+extern "C" int tileqr_task_graph(int64_t m, int64_t n, int nb, int domain, int what, int32_t *tasks,
+                                 int32_t *ndeps, int64_t *succ_ptr, int64_t *succ, int64_t *ntasks,
+                                 int64_t *nedges)
+{
+    if (m < 0)
+        return -1;
+    if (n < 0)
+        return -2;
+    if (nb < 1)
+        return -3;
+    if (domain < 0)
+        return -4;
+    if (what != 0 && what != 1)
+        return -5;
+    if (ntasks == nullptr)
+        return -10;
+    if (nedges == nullptr)
+        return -11;
+    const int p = (int)((m + nb - 1) / nb), q = (int)((n + nb - 1) / nb);
+    const TGraph G = make_graph(p, q, domain);
+    // tasks in (tt, k, i, j) order; the key is the counter index
+    std::vector<GTask> list;
+    std::map<size_t, int64_t> index;
+    for (int k = 0; k < G.steps; k++)
+        for (int i = k; i < p; i++) {
+            const bool head = ((i - k) % G.H) == 0;
+            for (int tt = 0; tt < 2; tt++) {
+                if (tt == 1 && !(head && i > k))
+                    continue;
+                if (what == 1) {
+                    index[g_cidx(G, tt, k, i, 0)] = (int64_t)list.size();
+                    list.push_back(GTask{tt, k, i, -1});
+                } else {
+                    for (int j = k; j < q; j++) {
+                        index[g_cidx(G, tt, k, i, j)] = (int64_t)list.size();
+                        list.push_back(GTask{tt, k, i, j});
+                    }
+                }
+            }
+        }
+    std::vector<std::vector<int64_t>> out(list.size());
+    int64_t ne = 0;
+    for (size_t t = 0; t < list.size(); t++) {
+        const GTask a = list[t];
+        GTask sp[2];
+        std::vector<GTask> ss;
+        if (what == 1) {
+            const int kind = ga_kind(G, a.tt, a.k, a.i);
+            const int ns = ga_specific(G, kind, a.k, a.i, sp);
+            for (int s2 = 0; s2 < ns; s2++)
+                ss.push_back(GTask{sp[s2].tt, sp[s2].k, sp[s2].i, 0});
+        } else {
+            const int kind = g_kind(G, a.tt, a.k, a.i, a.j);
+            const int fan = g_fanout(G, kind, a.k);
+            for (int s2 = 0; s2 < fan; s2++)
+                ss.push_back(g_fan_task(kind, a.k, a.i, s2));
+            const int ns = g_specific(G, kind, a.k, a.i, a.j, sp);
+            for (int s2 = 0; s2 < ns; s2++)
+                ss.push_back(sp[s2]);
+        }
+        for (const GTask &b : ss) {
+            auto it = index.find(g_cidx(G, b.tt, b.k, b.i, b.j));
+            if (it == index.end())
+                return -99;   // a successor outside the graph: an internal error
+            out[t].push_back(it->second);
+            ne++;
+        }
+    }
+    *ntasks = (int64_t)list.size();
+    *nedges = ne;
+    if (tasks == nullptr)
+        return 0;
+    if (ndeps == nullptr)
+        return -7;
+    if (succ_ptr == nullptr)
+        return -8;
+    if (succ == nullptr && ne > 0)
+        return -9;
+    int64_t pos = 0;
+    for (size_t t = 0; t < list.size(); t++) {
+        const GTask a = list[t];
+        const int kind = what == 1 ? ga_kind(G, a.tt, a.k, a.i) : g_kind(G, a.tt, a.k, a.i, a.j);
+        tasks[4 * t + 0] = kind;
+        tasks[4 * t + 1] = a.i;
+        tasks[4 * t + 2] = a.j;
+        tasks[4 * t + 3] = a.k;
+        ndeps[t] = what == 1 ? ga_ndeps(kind, a.k) : g_ndeps(kind, a.k);
+        succ_ptr[t] = pos;
+        for (int64_t v : out[t])
+            succ[pos++] = v;
+    }
+    succ_ptr[list.size()] = pos;
+    return 0;
 }

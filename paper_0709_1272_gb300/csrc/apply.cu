@@ -1,14 +1,16 @@
 // apply.cu -- Q^T B and the triangular solve of the least-squares path.
 //
-// Q^T B replays the transformations of Algorithm 2 on the columns of B, split
-// into column chunks of APPLY_W.  For chunk c the tasks are LB(k) (DLARFB
-// with V_kk, T_kk on row block k) and SB(i,k) (DSSRFB with V_ik, T_ik on row
-// blocks k and i).  Their dependencies are those of the factorization
-// restricted to one tile column: LB(k) <- SB(k,k-1); SB(i,k) <- (LB(k) if
-// i = k+1 else SB(i-1,k)) and SB(i,k-1).  They run in one persistent kernel
-// with the same counter / ready-queue scheduler, so consecutive steps k
-// overlap as a wavefront.
+// Q^T B replays the update transformations of the factorization on the
+// columns of B, split into column chunks of APPLY_W.  For chunk c the tasks
+// are the update kinds of the factorization's task graph restricted to one
+// tile column (graph.cuh): LB = DLARFB with a domain head's V and T, SB =
+// DSSRFB of a domain row into its head, TB = DTTMQR merging two heads (tree
+// form).  In Algorithm 2's flat form: LB(k) <- SB(k,k-1); SB(i,k) <- (LB(k)
+// if i = k+1 else SB(i-1,k)) and SB(i,k-1).  They run in one persistent
+// kernel with the same counter / ready-queue scheduler, so consecutive
+// steps k overlap as a wavefront.
 #include "factor.h"
+#include "graph.cuh"
 #include "sched.cuh"
 #include "tile_f64.cuh"
 
@@ -17,9 +19,11 @@ namespace tqr {
 struct ApplyArgs {
     const double *tiles;
     const double *T;
+    const double *T2;
     double *Bt;
     int p, q, steps, nchunk;
     int64_t ncp;
+    TGraph G;
 };
 
 template <int NB, int S>
@@ -28,9 +32,9 @@ __device__ __forceinline__ double *chunk_ptr(const ApplyArgs &A, int i, int cb)
     return A.Bt + ((size_t)i * A.ncp + (size_t)cb * APPLY_W) * NB;
 }
 
-__device__ __forceinline__ size_t apply_cnt_idx(const ApplyArgs &A, int k, int i, int cb)
+__device__ __forceinline__ size_t apply_cnt_idx(const ApplyArgs &A, int tt, int k, int i, int cb)
 {
-    return ((size_t)k * A.p + i) * A.nchunk + cb;
+    return (((size_t)tt * A.steps + k) * A.p + i) * A.nchunk + cb;
 }
 
 template <int NB, int S>
@@ -39,9 +43,10 @@ __global__ void __launch_bounds__(NT, 1) k_apply_dag(ApplyArgs A, Queues Q)
     extern __shared__ double sm[];
     __shared__ unsigned long long s_code;
     __shared__ int s_cmd;
-    if (blockIdx.x == 0)
-        for (int cb = threadIdx.x; cb < A.nchunk; cb += NT)
-            q_push(Q, 0, encode_task(0, 0, cb));
+    const TGraph &G = A.G;
+    if (blockIdx.x == 0)   // step 0's DLARFBs (one per domain head and chunk) have no predecessors
+        for (int u = threadIdx.x; u < A.nchunk * g_ndom(G, 0); u += NT)
+            q_push(Q, 0, encode_task(0, g_head(G, 0, u / A.nchunk), u % A.nchunk));
     for (;;) {
         if (threadIdx.x == 0)
             s_cmd = q_acquire(Q, s_code);
@@ -50,30 +55,25 @@ __global__ void __launch_bounds__(NT, 1) k_apply_dag(ApplyArgs A, Queues Q)
             break;
         int k, i, cb;
         decode_task(s_code, k, i, cb);
+        const int kind = ga_kind(G, decode_tt(s_code), k, i);
         const double *Vt = A.tiles + ((size_t)k * A.p + i) * (size_t)NB * NB;
-        const double *Tt = A.T + ((size_t)k * A.p + i) * (size_t)S * NB;
-        if (i == k)
-            task_larfb<NB, S, APPLY_W>(sm, chunk_ptr<NB, S>(A, k, cb), Vt, Tt, APPLY_W);
+        const size_t strip = ((size_t)k * A.p + i) * (size_t)S * NB;
+        if (kind == K_LARFB)
+            task_larfb<NB, S, APPLY_W>(sm, chunk_ptr<NB, S>(A, i, cb), Vt, A.T + strip, APPLY_W);
+        else if (kind == K_SSRFB)
+            task_ssrfb<NB, S, APPLY_W>(sm, chunk_ptr<NB, S>(A, g_head(G, k, g_dom(G, k, i)), cb),
+                                       chunk_ptr<NB, S>(A, i, cb), Vt, A.T + strip, APPLY_W);
         else
-            task_ssrfb<NB, S, APPLY_W>(sm, chunk_ptr<NB, S>(A, k, cb), chunk_ptr<NB, S>(A, i, cb), Vt, Tt,
-                                       APPLY_W);
+            task_ssrfb<NB, S, APPLY_W, true>(sm, chunk_ptr<NB, S>(A, g_partner(G, k, i), cb),
+                                             chunk_ptr<NB, S>(A, i, cb), Vt, A.T2 + strip, APPLY_W);
         __syncthreads();
         if (threadIdx.x == 0) {
-            // successors
-            if (i == k) {
-                if (k + 1 < A.p)
-                    q_signal(Q, apply_cnt_idx(A, k, k + 1, cb), 1 + (k > 0 ? 1 : 0), 1,
-                             encode_task(k, k + 1, cb));
-            } else {
-                if (i + 1 < A.p)
-                    q_signal(Q, apply_cnt_idx(A, k, i + 1, cb), 1 + (k > 0 ? 1 : 0), 1,
-                             encode_task(k, i + 1, cb));
-                if (k + 1 < A.steps) {
-                    if (i == k + 1)
-                        q_signal(Q, apply_cnt_idx(A, k + 1, i, cb), 1, 0, encode_task(k + 1, i, cb));
-                    else
-                        q_signal(Q, apply_cnt_idx(A, k + 1, i, cb), 2, 1, encode_task(k + 1, i, cb));
-                }
+            GTask sp[2];
+            const int ns = ga_specific(G, kind, k, i, sp);
+            for (int s = 0; s < ns; s++) {
+                const int tk = ga_kind(G, sp[s].tt, sp[s].k, sp[s].i);
+                q_signal(Q, apply_cnt_idx(A, sp[s].tt, sp[s].k, sp[s].i, cb), ga_ndeps(tk, sp[s].k),
+                         tk == K_LARFB ? 0 : 1, encode_task(sp[s].k, sp[s].i, cb, sp[s].tt));
             }
             __threadfence();
             atomicAdd(&Q.ctrl->completed, 1u);
@@ -81,17 +81,34 @@ __global__ void __launch_bounds__(NT, 1) k_apply_dag(ApplyArgs A, Queues Q)
     }
 }
 
+// Scheduler state of the Q^T application: control block, counters (two
+// banks for the tree form), the LB queue and the SB + TB queue.
+struct ApplySched {
+    size_t cnt_bytes, q0_bytes, q1_bytes;
+    unsigned long long n0, n1;
+};
+static ApplySched apply_sched(const WsLayout &L, int nchunk)
+{
+    const TGraph G = make_graph(L.p, L.q, L.H);
+    unsigned long long cnt[2];
+    ga_count(G, cnt);
+    ApplySched a;
+    a.n0 = cnt[0] * (unsigned long long)nchunk;
+    a.n1 = cnt[1] * (unsigned long long)nchunk;
+    a.cnt_bytes = align256((size_t)(G.H < G.p ? 2 : 1) * L.steps * L.p * nchunk * sizeof(unsigned int));
+    a.q0_bytes = align256((a.n0 ? a.n0 : 1) * 8);
+    a.q1_bytes = align256((a.n1 ? a.n1 : 1) * 8);
+    return a;
+}
+
 size_t apply_sched_bytes(const WsLayout &L, int nchunk)
 {
-    size_t cnt = (size_t)L.steps * L.p * nchunk * sizeof(unsigned int);
-    unsigned long long nlb = (unsigned long long)L.steps * nchunk, nsb = 0;
-    for (int k = 0; k < L.steps; k++)
-        nsb += (unsigned long long)(L.p - k - 1) * nchunk;
-    return 256 + align256(cnt) + align256((nlb ? nlb : 1) * 8) + align256((nsb ? nsb : 1) * 8);
+    const ApplySched a = apply_sched(L, nchunk);
+    return 256 + a.cnt_bytes + a.q0_bytes + a.q1_bytes;
 }
 
 template <int NB, int S>
-static int launch_apply_t(const WsLayout &L, const double *tiles, const double *T, double *Bt,
+static int launch_apply_t(const WsLayout &L, const double *tiles, const double *T, const double *T2, double *Bt,
                           int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns)
 {
     constexpr size_t smem = F64Cfg<NB, S, APPLY_W>::SMEM;
@@ -109,26 +126,25 @@ static int launch_apply_t(const WsLayout &L, const double *tiles, const double *
     ApplyArgs A;
     A.tiles = tiles;
     A.T = T;
+    A.T2 = T2;
     A.Bt = Bt;
     A.p = L.p;
     A.q = L.q;
     A.steps = L.steps;
     A.ncp = ncp;
     A.nchunk = (int)(ncp / APPLY_W);
-    const size_t cnt_bytes = align256((size_t)L.steps * L.p * A.nchunk * sizeof(unsigned int));
-    unsigned long long nlb = (unsigned long long)L.steps * A.nchunk, nsb = 0;
-    for (int k = 0; k < L.steps; k++)
-        nsb += (unsigned long long)(L.p - k - 1) * A.nchunk;
+    A.G = make_graph(L.p, L.q, L.H);
+    const ApplySched a = apply_sched(L, A.nchunk);
     Queues Q;
     Q.ctrl = (SchedCtrl *)sched;
     Q.cnt = (unsigned int *)(sched + 256);
-    Q.slot[0] = (unsigned long long *)(sched + 256 + cnt_bytes);
-    Q.slot[1] = (unsigned long long *)(sched + 256 + cnt_bytes + align256((nlb ? nlb : 1) * 8));
+    Q.slot[0] = (unsigned long long *)(sched + 256 + a.cnt_bytes);
+    Q.slot[1] = (unsigned long long *)(sched + 256 + a.cnt_bytes + a.q0_bytes);
     Q.slot[2] = Q.slot[3] = nullptr;
-    Q.cap[0] = (unsigned int)nlb;
-    Q.cap[1] = (unsigned int)nsb;
+    Q.cap[0] = (unsigned int)a.n0;
+    Q.cap[1] = (unsigned int)a.n1;
     Q.cap[2] = Q.cap[3] = 0;
-    Q.total = (unsigned int)(nlb + nsb);
+    Q.total = (unsigned int)(a.n0 + a.n1);
     Q.watchdog_ns = watchdog_ns;
     Q.withheld = ~0ull;
     Q.trace = nullptr;
@@ -145,12 +161,12 @@ static int launch_apply_t(const WsLayout &L, const double *tiles, const double *
     return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
 }
 
-int launch_apply(const WsLayout &L, const double *tiles, const double *T, double *Bt, int64_t ncp,
-                 char *sched, cudaStream_t st, unsigned long long watchdog_ns)
+int launch_apply(const WsLayout &L, const double *tiles, const double *T, const double *T2, double *Bt,
+                 int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns)
 {
 #define TQR_CASE(NB_, S_)                                                                        \
     if (L.nb == NB_ && L.ib == S_)                                                               \
-        return launch_apply_t<NB_, S_>(L, tiles, T, Bt, ncp, sched, st, watchdog_ns);
+        return launch_apply_t<NB_, S_>(L, tiles, T, T2, Bt, ncp, sched, st, watchdog_ns);
     TQR_CASE(64, 16)
     TQR_CASE(64, 32)
     TQR_CASE(128, 16)

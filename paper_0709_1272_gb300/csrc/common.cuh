@@ -21,16 +21,19 @@ __host__ __device__ inline int task_kind(int i, int j, int k)
 {
     return (i == k) ? (j == k ? K_GEQRT : K_LARFB) : (j == k ? K_TSQRT : K_SSRFB);
 }
-__host__ __device__ inline unsigned long long encode_task(int k, int i, int j)
+// Task code: tt (1 bit: the tree kernels) | k (21) | i (21) | j (21).
+__host__ __device__ inline unsigned long long encode_task(int k, int i, int j, int tt = 0)
 {
-    return ((unsigned long long)k << 42) | ((unsigned long long)i << 21) | (unsigned long long)j;
+    return ((unsigned long long)tt << 63) | ((unsigned long long)k << 42) | ((unsigned long long)i << 21) |
+           (unsigned long long)j;
 }
 __host__ __device__ inline void decode_task(unsigned long long c, int &k, int &i, int &j)
 {
-    k = (int)(c >> 42);
+    k = (int)((c >> 42) & 0x1FFFFF);
     i = (int)((c >> 21) & 0x1FFFFF);
     j = (int)(c & 0x1FFFFF);
 }
+__host__ __device__ inline int decode_tt(unsigned long long c) { return (int)(c >> 63); }
 
 // Number of predecessors of a task (Sec. 4; derived from the reads and writes
 // of the four kernels): the previous-step writer of its tile (k > 0) plus
@@ -59,53 +62,20 @@ struct SchedCtrl {
 };
 static_assert(sizeof(SchedCtrl) <= 256, "control block must fit its 256-byte slot");
 
-// Byte layout of the workspace (every piece 256-byte aligned).
+// Byte layout of the workspace (every piece 256-byte aligned).  H is the
+// domain size of the elimination tree (H == p: Algorithm 2's flat tree); a
+// tree layout adds the DTTQRT T strips (T2) and a second counter bank.
 struct WsLayout {
     int64_t m, n;
-    int nb, ib, p, q, steps;
-    size_t off_tiles, off_T, off_ctrl, off_cnt, off_q[K_NKIND], end;
+    int nb, ib, p, q, steps, H;
+    size_t off_tiles, off_T, off_T2, off_ctrl, off_cnt, off_q[K_NKIND], end;
     unsigned int cap[K_NKIND];
     unsigned int total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-inline WsLayout make_layout(int64_t m, int64_t n, int nb, int ib)
-{
-    WsLayout L{};
-    L.m = m;
-    L.n = n;
-    L.nb = nb;
-    L.ib = ib;
-    L.p = (int)((m + nb - 1) / nb);
-    L.q = (int)((n + nb - 1) / nb);
-    L.steps = L.p < L.q ? L.p : L.q;
-    size_t tiles = (size_t)L.p * L.q * nb * nb * sizeof(double);
-    size_t tst = (size_t)L.p * L.q * ib * nb * sizeof(double);
-    L.off_tiles = 0;
-    L.off_T = align256(tiles);
-    L.off_ctrl = L.off_T + align256(tst);
-    L.off_cnt = L.off_ctrl + 256;
-    size_t cnt = (size_t)L.steps * L.p * L.q * sizeof(unsigned int);
-    size_t off = L.off_cnt + align256(cnt);
-    unsigned long long caps[K_NKIND] = {0, 0, 0, 0};
-    for (int k = 0; k < L.steps; k++) {
-        caps[K_GEQRT] += 1;
-        caps[K_LARFB] += (unsigned long long)(L.q - k - 1);
-        caps[K_TSQRT] += (unsigned long long)(L.p - k - 1);
-        caps[K_SSRFB] += (unsigned long long)(L.p - k - 1) * (L.q - k - 1);
-    }
-    unsigned long long tot = 0;
-    for (int t = 0; t < K_NKIND; t++) {
-        L.cap[t] = (unsigned int)caps[t];
-        tot += caps[t];
-        L.off_q[t] = off;
-        off += align256((size_t)(caps[t] ? caps[t] : 1) * sizeof(unsigned long long));
-    }
-    L.total = (unsigned int)tot;
-    L.end = off;
-    return L;
-}
+WsLayout make_layout(int64_t m, int64_t n, int nb, int ib, int h = 0);
 
 // ---------------------------------------------------------------------------
 // Global-memory access that bypasses L1: tiles are written by other SMs

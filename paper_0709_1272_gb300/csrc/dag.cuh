@@ -3,6 +3,7 @@
 // builds.  With MIXED, the DLARFB/DSSRFB tasks run on the tcgen05 tensor
 // cores (tile_mixed.cuh) while DGEQRT/DTSQRT stay in FP64.
 #pragma once
+#include "graph.cuh"
 #include "sched.cuh"
 #include "tile_f64.cuh"
 #include "tile_mixed.cuh"
@@ -12,7 +13,9 @@ namespace tqr {
 struct FactorArgs {
     double *tiles;
     double *T;
+    double *T2;   // DTTQRT T strips (tree form only)
     int p, q, steps;
+    TGraph G;
 };
 
 template <int NB, int S>
@@ -25,63 +28,78 @@ __device__ __forceinline__ double *strip_ptr(const FactorArgs &F, int i, int k)
 {
     return F.T + ((size_t)k * F.p + i) * (size_t)S * NB;
 }
-
-template <int NB, int S, bool MIXED = false>
-__device__ void run_factor_task(double *sm, const FactorArgs &F, int k, int i, int j)
+template <int NB, int S>
+__device__ __forceinline__ double *strip2_ptr(const FactorArgs &F, int i, int k)
 {
-    switch (task_kind(i, j, k)) {
+    return F.T2 + ((size_t)k * F.p + i) * (size_t)S * NB;
+}
+
+// Run the tile kernel of one task.  DTSQRT / DSSRFB eliminate row i into the
+// head of its domain (row k in Algorithm 2); DTTQRT / DTTMQR merge domain
+// head i into its partner head, reading only the upper triangle of tile
+// (i, k).  With MIXED, the three update kinds run on the tensor cores.
+template <int NB, int S, bool MIXED>
+__device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int kind, int k, int i, int j,
+                                         uint32_t tmem, uint64_t *mbar, uint32_t &mphase, int *err)
+{
+    const TGraph &G = F.G;
+    switch (kind) {
     case K_GEQRT:
-        task_geqrt<NB, S, MIXED>(sm, tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k));
-        break;
-    case K_LARFB:
-        task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, k, k),
-                          strip_ptr<NB, S>(F, k, k));
+        task_geqrt<NB, S, MIXED>(sm, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
         break;
     case K_TSQRT:
-        task_tsqrt<NB, S, MIXED>(sm, tile_ptr<NB, S>(F, k, k), tile_ptr<NB, S>(F, i, k),
-                                 strip_ptr<NB, S>(F, i, k));
+        task_tsqrt<NB, S, MIXED, false>(sm, tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), k),
+                                        tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
         break;
-    default:
-        task_ssrfb<NB, S>(sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, i, j),
-                          tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
+    case K_TTQRT:
+        task_tsqrt<NB, S, MIXED, true>(sm, tile_ptr<NB, S>(F, g_partner(G, k, i), k), tile_ptr<NB, S>(F, i, k),
+                                       strip2_ptr<NB, S>(F, i, k));
         break;
+    case K_LARFB:
+        if constexpr (MIXED)
+            task_update_mixed<S, VK_UNIT>((unsigned char *)sm, nullptr, tile_ptr<NB, S>(F, i, j),
+                                          tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), tmem, mbar, mphase,
+                                          err);
+        else
+            task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
+        break;
+    case K_SSRFB: {
+        double *top = tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), j);
+        if constexpr (MIXED)
+            task_update_mixed<S, VK_FULL>((unsigned char *)sm, top, tile_ptr<NB, S>(F, i, j),
+                                          tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), tmem, mbar, mphase,
+                                          err);
+        else
+            task_ssrfb<NB, S>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                              strip_ptr<NB, S>(F, i, k));
+        break;
+    }
+    default: {   // K_TTMQR
+        double *top = tile_ptr<NB, S>(F, g_partner(G, k, i), j);
+        if constexpr (MIXED)
+            task_update_mixed<S, VK_UPPER>((unsigned char *)sm, top, tile_ptr<NB, S>(F, i, j),
+                                           tile_ptr<NB, S>(F, i, k), strip2_ptr<NB, S>(F, i, k), tmem, mbar,
+                                           mphase, err);
+        else
+            task_ssrfb<NB, S, FactorW<NB>::value, true>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                                        strip2_ptr<NB, S>(F, i, k));
+        break;
+    }
     }
 }
 
-// Successors of task (k, i, j) in the graph of Algorithm 2 (the mirror of
-// task_ndeps): signalled cooperatively by all threads of the CTA.
-__device__ static void release_factor(const Queues &Q, const FactorArgs &F, int k, int i, int j)
+// Successors of a finished task in graph G, signalled cooperatively by all
+// threads of the CTA (the mirror of g_ndeps; see graph.cuh).
+__device__ static void release_graph(const Queues &Q, const TGraph &G, int kind, int k, int i, int j)
 {
-    const int p = F.p, q = F.q;
-    const int kind = task_kind(i, j, k);
-    int nsucc = 0;
-    switch (kind) {
-    case K_GEQRT: nsucc = (q - k - 1) + (k + 1 < p ? 1 : 0); break;
-    case K_LARFB: nsucc = (k + 1 < p) ? 1 : 0; break;
-    case K_TSQRT: nsucc = (q - k - 1) + (i + 1 < p ? 1 : 0); break;
-    default: nsucc = (i + 1 < p ? 1 : 0) + 1; break;
-    }
-    for (int s = threadIdx.x; s < nsucc; s += NT) {
-        int ks, is, js;
-        switch (kind) {
-        case K_GEQRT:
-            if (s < q - k - 1) { ks = k; is = k; js = k + 1 + s; }     // LARFB(k, j)
-            else { ks = k; is = k + 1; js = k; }                       // TSQRT(k+1, k)
-            break;
-        case K_LARFB:
-            ks = k; is = k + 1; js = j;                                // SSRFB(k+1, j, k)
-            break;
-        case K_TSQRT:
-            if (s < q - k - 1) { ks = k; is = i; js = k + 1 + s; }     // SSRFB(i, j, k)
-            else { ks = k; is = i + 1; js = k; }                       // TSQRT(i+1, k)
-            break;
-        default:
-            if (s == 0 && i + 1 < p) { ks = k; is = i + 1; js = j; }   // SSRFB(i+1, j, k)
-            else { ks = k + 1; is = i; js = j; }                       // next step on tile (i,j)
-            break;
-        }
-        const size_t idx = ((size_t)ks * p + is) * q + js;
-        q_signal(Q, idx, task_ndeps(is, js, ks), task_kind(is, js, ks), encode_task(ks, is, js));
+    const int fan = g_fanout(G, kind, k);
+    GTask sp[2];
+    const int nsp = g_specific(G, kind, k, i, j, sp);
+    for (int s = threadIdx.x; s < fan + nsp; s += NT) {
+        const GTask t = s < fan ? g_fan_task(kind, k, i, s) : sp[s - fan];
+        const int tk = g_kind(G, t.tt, t.k, t.i, t.j);
+        q_signal(Q, g_cidx(G, t.tt, t.k, t.i, t.j), g_ndeps(tk, t.k), kind_prio(tk),
+                 encode_task(t.k, t.i, t.j, t.tt));
     }
 }
 
@@ -114,11 +132,15 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_fac
         tc::fence_after_sync();
         tmem = s_tmem;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (ld_relaxed_s32(&Q.ctrl->nonfinite) != 0)
-            atomicCAS(&Q.ctrl->error, 0, TILEQR_ERR_NONFINITE);
-        else
-            q_push(Q, K_GEQRT, encode_task(0, 0, 0));
+    if (blockIdx.x == 0) {
+        // the step-0 DGEQRTs (one per domain head) have no predecessors
+        if (ld_relaxed_s32(&Q.ctrl->nonfinite) != 0) {
+            if (threadIdx.x == 0)
+                atomicCAS(&Q.ctrl->error, 0, TILEQR_ERR_NONFINITE);
+        } else {
+            for (int d = threadIdx.x; d < g_ndom(F.G, 0); d += NT)
+                q_push(Q, kind_prio(K_GEQRT), encode_task(0, g_head(F.G, 0, d), 0));
+        }
     }
     for (;;) {
         if (threadIdx.x == 0)
@@ -128,25 +150,15 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_fac
             break;
         int k, i, j;
         decode_task(s_code, k, i, j);
+        const int kind = g_kind(F.G, decode_tt(s_code), k, i, j);
         const unsigned long long t0 = Q.trace ? globaltimer_ns() : 0ull;
-        const int kind = task_kind(i, j, k);
-        if (MIXED && kind == K_SSRFB) {
-            task_update_mixed<S, false>((unsigned char *)sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, i, j),
-                                        tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), tmem, &s_mbar,
-                                        mphase, &Q.ctrl->error);
-        } else if (MIXED && kind == K_LARFB) {
-            task_update_mixed<S, true>((unsigned char *)sm, nullptr, tile_ptr<NB, S>(F, k, j),
-                                       tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k), tmem, &s_mbar, mphase,
-                                       &Q.ctrl->error);
-        } else {
-            run_factor_task<NB, S, MIXED>(sm, F, k, i, j);
-        }
+        run_task<NB, S, MIXED>(sm, F, kind, k, i, j, tmem, &s_mbar, mphase, &Q.ctrl->error);
         __syncthreads();
-        release_factor(Q, F, k, i, j);
+        release_graph(Q, F.G, kind, k, i, j);
         __syncthreads();
         if (threadIdx.x == 0) {
             if (Q.trace)
-                trace_record(Q, encode_task(k, i, j), t0, globaltimer_ns());
+                trace_record(Q, s_code, t0, globaltimer_ns());
             __threadfence();
             atomicAdd(&Q.ctrl->completed, 1u);
         }
@@ -191,7 +203,8 @@ __host__ __device__ inline void decode_btask(unsigned long long c, int &mat, int
     j = (int)(c & 0x7FFF);
 }
 
-// Successors of task (k, i, j) of matrix `mat` (same graph as release_factor).
+// Successors of task (k, i, j) of matrix `mat` in the graph of Algorithm 2
+// (the flat tree: release_graph with one domain per step).
 __device__ static void release_batched(const Queues &Q, const FactorArgs &F, size_t cnt_off, int mat, int k, int i,
                                        int j)
 {
@@ -269,9 +282,11 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
                 const MatInfo &mi = mats[mat];
                 s_F.tiles = mi.tiles;
                 s_F.T = mi.T;
+                s_F.T2 = nullptr;
                 s_F.p = mi.p;
                 s_F.q = mi.q;
                 s_F.steps = mi.steps;
+                s_F.G = make_graph(mi.p, mi.q, 0);
                 s_cnt = mi.cnt_off;
             }
         }
@@ -283,18 +298,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
         const FactorArgs F = s_F;
         const size_t cnt_off = s_cnt;
         const unsigned long long t0 = Q.trace ? globaltimer_ns() : 0ull;
-        const int kind = task_kind(i, j, k);
-        if (MIXED && kind == K_SSRFB) {
-            task_update_mixed<S, false>((unsigned char *)sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, i, j),
-                                        tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), tmem, &s_mbar,
-                                        mphase, &Q.ctrl->error);
-        } else if (MIXED && kind == K_LARFB) {
-            task_update_mixed<S, true>((unsigned char *)sm, nullptr, tile_ptr<NB, S>(F, k, j),
-                                       tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k), tmem, &s_mbar, mphase,
-                                       &Q.ctrl->error);
-        } else {
-            run_factor_task<NB, S, MIXED>(sm, F, k, i, j);
-        }
+        run_task<NB, S, MIXED>(sm, F, task_kind(i, j, k), k, i, j, tmem, &s_mbar, mphase, &Q.ctrl->error);
         __syncthreads();
         release_batched(Q, F, cnt_off, mat, k, i, j);
         __syncthreads();

@@ -78,9 +78,11 @@ static int launch_factor_t(const WsLayout &L, char *ws, int schedule, int flags,
     FactorArgs F;
     F.tiles = (double *)(ws + L.off_tiles);
     F.T = (double *)(ws + L.off_T);
+    F.T2 = (L.H < L.p) ? (double *)(ws + L.off_T2) : nullptr;
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;
+    F.G = make_graph(L.p, L.q, L.H);
     if (schedule == TILEQR_SCHED_DAG) {
         Queues Q;
         Q.ctrl = (SchedCtrl *)(ws + L.off_ctrl);
@@ -166,9 +168,11 @@ static int launch_factor_dag_at_t(const WsLayout &L, double *tiles, double *T, c
     FactorArgs F;
     F.tiles = tiles;
     F.T = T;
+    F.T2 = nullptr;
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;
+    F.G = make_graph(L.p, L.q, 0);
     Queues Q;
     Q.ctrl = (SchedCtrl *)sched;
     Q.cnt = (unsigned int *)(sched + (L.off_cnt - L.off_ctrl));

@@ -27,9 +27,11 @@ static int launch_factor_mixed_t(const WsLayout &L, char *ws, int flags, cudaStr
     FactorArgs F;
     F.tiles = (double *)(ws + L.off_tiles);
     F.T = (double *)(ws + L.off_T);
+    F.T2 = (L.H < L.p) ? (double *)(ws + L.off_T2) : nullptr;
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;
+    F.G = make_graph(L.p, L.q, L.H);
     Queues Q;
     Q.ctrl = (SchedCtrl *)(ws + L.off_ctrl);
     Q.cnt = (unsigned int *)(ws + L.off_cnt);

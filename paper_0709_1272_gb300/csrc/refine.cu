@@ -522,7 +522,8 @@ extern "C" int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_
         return -6;
     if (!(tol > 0.0))
         return -7;
-    if (d->nb != 128)
+    // the FP32 correction solve replays Algorithm 2's flat graph only
+    if (d->nb != 128 || d->T2 != nullptr)
         return TILEQR_ERR_UNSUPPORTED;
     const RefineLayout L = refine_layout(d);
     if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < L.end)

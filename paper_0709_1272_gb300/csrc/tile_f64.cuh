@@ -57,13 +57,13 @@ struct F64Cfg {
 //   Y = B_l + V_l^T C ;  W = T_l^T Y ;  B_l -= W ;  C -= V_l W
 // V_l (NB x S) is staged in shared memory as [r][a] (zero where the
 // reflectors are zero), T_l as S x S column-major, the column chunk of C as
-// [c][r].  Rows r < r0 of V_l are zero and skipped.  B_l (the S rows of the
+// [c][r].  Rows outside [r0, r1) of V_l are zero and skipped.  B_l (the S rows of the
 // top tile, DSSRFB / DTSQRT) is read and written in global memory at
 // Bg[c * NB + a]; Bg == nullptr for DLARFB (the unit block of V_l lies inside
 // C).  Only columns c < nc are meaningful; columns beyond stay untouched in
 // global memory.
 template <int NB, int S, int W_>
-__device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int nc)
+__device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int nc, int r1 = NB)
 {
     using C_ = F64Cfg<NB, S, W_>;
     constexpr int W = C_::W, LDC = C_::LDC, LDV = C_::LDV, AW = C_::AW, CU = C_::CU, RV = C_::RV;
@@ -90,7 +90,7 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
         for (int u = 0; u < CU; u++)
             y[ai][u] = 0.0;
     // column groups u with 32 u >= nc hold no data: skip them (warp-uniform)
-    for (int r = r0; r < NB; r++) {
+    for (int r = r0; r < r1; r++) {
         double v[AW], cc[CU];
 #pragma unroll
         for (int ai = 0; ai < AW; ai++)
@@ -147,7 +147,7 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
 
     // Phase C: C -= V W over rows r >= r0
     const int rbase = warp * RV;
-    if (rbase + RV > r0) {
+    if (rbase + RV > r0 && rbase < r1) {
         double acc[RV][CU];
 #pragma unroll
         for (int v = 0; v < RV; v++)
@@ -179,25 +179,27 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
 }
 
 // Stage columns [c0, c0+nc) of a tile into the chunk area ([c][r], ld LDC);
-// columns nc..W-1 are zero-filled.
-template <int NB, int S, int W_>
+// columns nc..W-1 are zero-filled.  TRI: only the upper triangle of the tile
+// (row <= column) is read, the rest staged as zero.
+template <int NB, int S, int W_, bool TRI = false>
 __device__ __forceinline__ void stage_chunk(double *sm, const double *tile, int c0, int nc)
 {
     using C_ = F64Cfg<NB, S, W_>;
     double *Cs = sm + C_::OFF_C;
     for (int idx = threadIdx.x; idx < C_::W * NB; idx += NT) {
         const int c = idx / NB, r = idx - c * NB;
-        Cs[c * C_::LDC + r] = (c < nc) ? ldcg(tile + (size_t)(c0 + c) * NB + r) : 0.0;
+        Cs[c * C_::LDC + r] = (c < nc && (!TRI || r <= c0 + c)) ? ldcg(tile + (size_t)(c0 + c) * NB + r) : 0.0;
     }
 }
-template <int NB, int S, int W_>
+// Store rows >= r0 of the staged columns (TRI: only their upper-triangle part).
+template <int NB, int S, int W_, bool TRI = false>
 __device__ __forceinline__ void store_chunk(const double *sm, double *tile, int c0, int nc, int r0)
 {
     using C_ = F64Cfg<NB, S, W_>;
     const double *Cs = sm + C_::OFF_C;
     for (int idx = threadIdx.x; idx < nc * NB; idx += NT) {
         const int c = idx / NB, r = idx - c * NB;
-        if (r >= r0)
+        if (r >= r0 && (!TRI || r <= c0 + c))
             stcg(tile + (size_t)(c0 + c) * NB + r, Cs[c * C_::LDC + r]);
     }
 }
@@ -211,6 +213,18 @@ __device__ __forceinline__ void stage_v_full(double *sm, const double *Vt, int l
     for (int idx = threadIdx.x; idx < NB * S; idx += NT) {
         const int a = idx / NB, r = idx - a * NB;
         Vs[r * C_::LDV + a] = ldcg(Vt + (size_t)(l0 + a) * NB + r);
+    }
+}
+// Stage V block l of a DTTQRT tile (the reflectors in the upper triangle,
+// row <= column; the strict lower part holds the tile's DGEQRT reflectors).
+template <int NB, int S, int W_>
+__device__ __forceinline__ void stage_v_upper(double *sm, const double *Vt, int l0)
+{
+    using C_ = F64Cfg<NB, S, W_>;
+    double *Vs = sm + C_::OFF_V;
+    for (int idx = threadIdx.x; idx < NB * S; idx += NT) {
+        const int a = idx / NB, r = idx - a * NB;
+        Vs[r * C_::LDV + a] = (r <= l0 + a) ? ldcg(Vt + (size_t)(l0 + a) * NB + r) : 0.0;
     }
 }
 // Stage V block l of a DGEQRT tile (unit lower, implicit ones) as [r][a].
@@ -239,7 +253,9 @@ __device__ __forceinline__ void stage_t(double *sm, const double *Tt, int l0)
 // DTSQRT reflectors in Vt and the T strip Tt, blocks l = 0..t-1 in order.
 // ncols: columns of Bt/Ct to update (tile ld is NB); the factorization
 // passes NB, the Q^T application the width of its column chunk.
-template <int NB, int S, int W_ = FactorW<NB>::value>
+// TRI (DTTMQR of the tree form): the reflectors are the upper triangle of
+// Vt, so block l reaches only rows < l0 + S of Ct.
+template <int NB, int S, int W_ = FactorW<NB>::value, bool TRI = false>
 __device__ __noinline__ void task_ssrfb(double *sm, double *Bt, double *Ct, const double *Vt, const double *Tt,
                            int ncols = NB)
 {
@@ -248,10 +264,13 @@ __device__ __noinline__ void task_ssrfb(double *sm, double *Bt, double *Ct, cons
         const int nc = min(C_::W, ncols - c0);
         stage_chunk<NB, S, W_>(sm, Ct, c0, nc);
         for (int l0 = 0; l0 < NB; l0 += S) {
-            stage_v_full<NB, S, W_>(sm, Vt, l0);
+            if constexpr (TRI)
+                stage_v_upper<NB, S, W_>(sm, Vt, l0);
+            else
+                stage_v_full<NB, S, W_>(sm, Vt, l0);
             stage_t<NB, S, W_>(sm, Tt, l0);
             __syncthreads();
-            apply_block<NB, S, W_>(sm, Bt + (size_t)c0 * NB + l0, 0, nc);
+            apply_block<NB, S, W_>(sm, Bt + (size_t)c0 * NB + l0, 0, nc, TRI ? l0 + S : NB);
         }
         store_chunk<NB, S, W_>(sm, Ct, c0, nc, 0);
         __syncthreads();
@@ -408,13 +427,13 @@ __device__ __noinline__ void panel_factor(double *sm, double *Pt, double *Ph, in
     __syncthreads();
 }
 
-// Build T_l (S x S upper) from the staged V_l ([r][a], rows >= r0) and the
+// Build T_l (S x S upper) from the staged V_l ([r][a], rows in [r0, r1)) and the
 // taus: forward columnwise compact-WY recurrence T(0:j-1, j) = -tau_j
 // T(0:j-1, 0:j-1) V(:,0:j-1)^T v_j, T(j,j) = tau_j (Schreiber-Van Loan, the
 // accumulation named in Sec. 3.2.1).  Result in Ts; also written to the
 // global strip Tt (block at column l0), lower parts zero.
 template <int NB, int S>
-__device__ __noinline__ void build_t(double *sm, int r0, double *Tt, int l0)
+__device__ __noinline__ void build_t(double *sm, int r0, double *Tt, int l0, int r1 = NB)
 {
     using C_ = F64Cfg<NB, S>;
     constexpr int LDV = C_::LDV;
@@ -434,11 +453,11 @@ __device__ __noinline__ void build_t(double *sm, int r0, double *Tt, int l0)
         const int i = pidx - base;
         double g0 = 0.0, g1 = 0.0;
         int r = r0;
-        for (; r + 1 < NB; r += 2) {
+        for (; r + 1 < r1; r += 2) {
             g0 = fma(Vs[r * LDV + i], Vs[r * LDV + j], g0);
             g1 = fma(Vs[(r + 1) * LDV + i], Vs[(r + 1) * LDV + j], g1);
         }
-        if (r < NB)
+        if (r < r1)
             g0 = fma(Vs[r * LDV + i], Vs[r * LDV + j], g0);
         Ts[i + j * S] = g0 + g1;
     }
@@ -471,16 +490,17 @@ __device__ __noinline__ void build_t(double *sm, int r0, double *Tt, int l0)
 // Apply inner block l (V_l, T_l already staged) to the tile columns right of
 // the block, [l0 + S, NB), chunk by chunk: the trailing update inside DGEQRT
 // (Rt == nullptr, rows >= r0 = l0) and DTSQRT (B rows l0.. of the R tile Rt).
-template <int NB, int S>
+// TRI (DTTQRT): At is an upper triangle and V_l reaches rows < l0 + S only.
+template <int NB, int S, bool TRI = false>
 __device__ __noinline__ void trailing_update(double *sm, double *At, double *Rt, int l0, int r0)
 {
     using C_ = F64Cfg<NB, S>;
     for (int c0 = l0 + S; c0 < NB; c0 += C_::W) {
         const int nc = min(C_::W, NB - c0);
-        stage_chunk<NB, S, C_::W>(sm, At, c0, nc);
+        stage_chunk<NB, S, C_::W, TRI>(sm, At, c0, nc);
         __syncthreads();
-        apply_block<NB, S, C_::W>(sm, Rt ? Rt + (size_t)c0 * NB + l0 : nullptr, r0, nc);
-        store_chunk<NB, S, C_::W>(sm, At, c0, nc, r0);
+        apply_block<NB, S, C_::W>(sm, Rt ? Rt + (size_t)c0 * NB + l0 : nullptr, r0, nc, TRI ? l0 + S : NB);
+        store_chunk<NB, S, C_::W, TRI>(sm, At, c0, nc, r0);
         __syncthreads();
     }
 }
@@ -518,7 +538,7 @@ __device__ __forceinline__ double panel_f32_to_f64(float v)
 // FP32 on the CUDA cores; the FP64 tile then receives C -= delta and
 // B_l -= W with one FP64 subtraction per element.  The reflectors, tau and
 // T_l were formed in FP64 by the panel and are only read here.
-template <int NB, int S>
+template <int NB, int S, bool TRI = false>
 __device__ __noinline__ void trailing_update_mixed(double *sm, double *At, double *Rt, int l0, int r0)
 {
     using C_ = F64Cfg<NB, S>;
@@ -544,7 +564,8 @@ __device__ __noinline__ void trailing_update_mixed(double *sm, double *At, doubl
         __syncthreads();
         for (int idx = tid; idx < W * NB; idx += NT) {
             const int c = idx / NB, r = idx - c * NB;
-            Cf[c * LDF + r] = (c < nc && r >= r0) ? panel_f64_to_f32(ldcg(At + (size_t)(c0 + c) * NB + r)) : 0.0f;
+            const bool in = c < nc && r >= r0 && (!TRI || r <= c0 + c);
+            Cf[c * LDF + r] = in ? panel_f64_to_f32(ldcg(At + (size_t)(c0 + c) * NB + r)) : 0.0f;
         }
         __syncthreads();
         // Y = B_l + V^T C: thread (c, quarter of the block rows)
@@ -559,7 +580,7 @@ __device__ __noinline__ void trailing_update_mixed(double *sm, double *At, doubl
                 bv[i] = (Rt != nullptr && c < nc) ? ldcg(Rt + (size_t)(c0 + c) * NB + l0 + a) : 0.0;
                 y[i] = panel_f64_to_f32(bv[i]);
             }
-            for (int r = r0; r < NB; r++) {
+            for (int r = r0; r < (TRI ? l0 + S : NB); r++) {
                 const float cv = Cf[c * LDF + r];
 #pragma unroll
                 for (int i = 0; i < AQ; i++)
@@ -591,7 +612,7 @@ __device__ __noinline__ void trailing_update_mixed(double *sm, double *At, doubl
         // C -= V W: thread (row r, half of the chunk columns), lanes along rows
         {
             const int r = tid & (NB - 1), half = tid >> 7;
-            if (r >= r0) {
+            if (r >= r0 && (!TRI || r < l0 + S)) {
                 constexpr int CH = W / 2;
                 float d[CH];
 #pragma unroll
@@ -659,7 +680,11 @@ __device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt)
 // the upper triangle of the diagonal tile Rt and A the tile At; R updated in
 // place (upper triangle only: V_kk below the diagonal is left untouched), A
 // overwritten by the reflector tile, T strip to Tt.
-template <int NB, int S, bool MIXED = false>
+// TRI: DTTQRT of the tree form: A is the upper triangle of At (the rest of
+// At, the tile's DGEQRT reflectors, is neither read nor written); reflector
+// j then has nonzeros in rows 0..j only, so inner block l works on rows
+// < l0 + S.
+template <int NB, int S, bool MIXED = false, bool TRI = false>
 __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, double *Tt)
 {
     using C_ = F64Cfg<NB, S>;
@@ -671,18 +696,20 @@ __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, doub
     for (int l0 = 0; l0 < NB; l0 += S) {
         for (int idx = threadIdx.x; idx < S * NB; idx += NT) {
             const int c = idx / NB, r = idx - c * NB;
-            Pt[c * LDC + r] = ldcg(At + (size_t)(l0 + c) * NB + r);
+            Pt[c * LDC + r] = (!TRI || r <= l0 + c) ? ldcg(At + (size_t)(l0 + c) * NB + r) : 0.0;
         }
         for (int idx = threadIdx.x; idx < S * S; idx += NT) {
             const int c = idx / S, a = idx - c * S;
             Ph[c * S + a] = (a <= c) ? ldcg(Rt + (size_t)(l0 + c) * NB + l0 + a) : 0.0;
         }
         __syncthreads();
-        panel_factor<NB, S, true>(sm, Pt, Ph, S, NB);
+        panel_factor<NB, S, true>(sm, Pt, Ph, S, TRI ? l0 + S : NB);
         for (int idx = threadIdx.x; idx < S * NB; idx += NT) {
             const int c = idx / NB, r = idx - c * NB;
-            const double val = Pt[c * LDC + r];
-            stcg(At + (size_t)(l0 + c) * NB + r, val);
+            const bool in = !TRI || r <= l0 + c;
+            const double val = in ? Pt[c * LDC + r] : 0.0;
+            if (in)
+                stcg(At + (size_t)(l0 + c) * NB + r, val);
             Vs[r * LDV + c] = val;
         }
         for (int idx = threadIdx.x; idx < S * S; idx += NT) {
@@ -691,11 +718,11 @@ __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, doub
                 stcg(Rt + (size_t)(l0 + c) * NB + l0 + a, Ph[c * S + a]);
         }
         __syncthreads();
-        build_t<NB, S>(sm, 0, Tt, l0);
+        build_t<NB, S>(sm, 0, Tt, l0, TRI ? l0 + S : NB);
         if constexpr (MIXED)
-            trailing_update_mixed<NB, S>(sm, At, Rt, l0, 0);
+            trailing_update_mixed<NB, S, TRI>(sm, At, Rt, l0, 0);
         else
-            trailing_update<NB, S>(sm, At, Rt, l0, 0);
+            trailing_update<NB, S, TRI>(sm, At, Rt, l0, 0);
     }
 }
 

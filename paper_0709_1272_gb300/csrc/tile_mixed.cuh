@@ -73,18 +73,24 @@ __device__ __forceinline__ double f32_to_f64_bits(float v)
     return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
 }
 
-// Element (trow, tcol) of a reflector tile; UNIT: a DGEQRT tile, whose
-// reflectors are unit lower triangular (zeros above the diagonal, implicit
-// ones on it; R occupies the upper part of the stored tile).
-template <bool UNIT>
+// Which part of a reflector tile holds the reflectors: the whole tile
+// (DTSQRT), the unit lower triangle (DGEQRT: zeros above the diagonal,
+// implicit ones on it, R stored above), or the upper triangle with the
+// diagonal (DTTQRT of the tree form: the DGEQRT reflectors stored below).
+enum { VK_FULL = 0, VK_UNIT = 1, VK_UPPER = 2 };
+
+// Element (trow, tcol) of a reflector tile of kind VK.
+template <int VK>
 __device__ __forceinline__ double mixed_v_elem(const double *Vt, int trow, int tcol)
 {
-    if (UNIT) {
+    if (VK == VK_UNIT) {
         if (trow < tcol)
             return 0.0;
         if (trow == tcol)
             return 1.0;
     }
+    if (VK == VK_UPPER && trow > tcol)
+        return 0.0;
     return ldcg(Vt + (size_t)tcol * 128 + trow);
 }
 
@@ -124,11 +130,12 @@ __device__ __forceinline__ bool mixed_mma_round(uint64_t *mbar, uint32_t &phase,
     return ok;
 }
 
-// Mixed DSSRFB (Bt != nullptr, V = full DTSQRT tile) or DLARFB (Bt ==
-// nullptr, V = unit-lower DGEQRT tile) on FP64 tiles.  Returns false on a
-// tensor-core wait timeout (an error is recorded; the tile contents are then
-// undefined).
-template <int S, bool UNIT>
+// Mixed DSSRFB (Bt != nullptr, V = full DTSQRT tile), DLARFB (Bt ==
+// nullptr, V = unit-lower DGEQRT tile) or DTTMQR (Bt != nullptr, V = upper
+// DTTQRT triangle: V = [I; V_B] as for DSSRFB, so G = V_B^T V_B again) on
+// FP64 tiles.  Returns false on a tensor-core wait timeout (an error is
+// recorded; the tile contents are then undefined).
+template <int S, int VK>
 __device__ __noinline__ bool task_update_mixed(unsigned char *sm, double *Bt, double *Ct, const double *Vt,
                                                const double *Tt, uint32_t tmem, uint64_t *mbar, uint32_t &phase,
                                                int *err)
@@ -150,10 +157,10 @@ __device__ __noinline__ bool task_update_mixed(unsigned char *sm, double *Bt, do
         for (int u = tid; u < NB * (KC / 4); u += NT) {
             const int j = u & 7, m = u >> 3, r = r0 + 4 * j;
             const uint32_t off = tc::kmajor_off(m, 4 * j, KC);
-            store_split4(sm, M::OFF_AHI, M::OFF_ALO, off, f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r, m)),
-                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r + 1, m)),
-                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r + 2, m)),
-                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r + 3, m)));
+            store_split4(sm, M::OFF_AHI, M::OFF_ALO, off, f64_to_f32_bits(mixed_v_elem<VK>(Vt, r, m)),
+                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r + 1, m)),
+                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r + 2, m)),
+                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r + 3, m)));
             const double *cp = Ct + (size_t)m * NB + r;
             store_split4(sm, M::OFF_BHI, M::OFF_BLO, off, f64_to_f32_bits(ldcg(cp)), f64_to_f32_bits(ldcg(cp + 1)),
                          f64_to_f32_bits(ldcg(cp + 2)), f64_to_f32_bits(ldcg(cp + 3)));
@@ -259,10 +266,10 @@ __device__ __noinline__ bool task_update_mixed(unsigned char *sm, double *Bt, do
         for (int u = tid; u < NB * (KC / 4); u += NT) {
             const int r = u & (NB - 1), j = u >> 7, k = k0 + 4 * j;
             const uint32_t off = tc::kmajor_off(r, 4 * j, KC);
-            store_split4(sm, M::OFF_AHI, M::OFF_ALO, off, f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r, k)),
-                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r, k + 1)),
-                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r, k + 2)),
-                         f64_to_f32_bits(mixed_v_elem<UNIT>(Vt, r, k + 3)));
+            store_split4(sm, M::OFF_AHI, M::OFF_ALO, off, f64_to_f32_bits(mixed_v_elem<VK>(Vt, r, k)),
+                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r, k + 1)),
+                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r, k + 2)),
+                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r, k + 3)));
             // B operand (column c = r, reflector k) = W[k][c]
             store_split4(sm, M::OFF_BHI, M::OFF_BLO, off, PW[k * LDF + r], PW[(k + 1) * LDF + r],
                          PW[(k + 2) * LDF + r], PW[(k + 3) * LDF + r]);

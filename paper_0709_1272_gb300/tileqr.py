@@ -34,6 +34,7 @@ EXPORTED = [
     "tileqr_refine_workspace_size", "tileqr_solve_refine",
     "tileqr_batched_workspace_size", "tileqr_batched_prepare", "tileqr_factor_batched",
     "tileqr_batched_status", "tileqr_batched_get",
+    "tileqr_workspace_size_tree", "tileqr_factor_tree", "tileqr_get_tree_T", "tileqr_task_graph",
 ]
 
 
@@ -46,6 +47,7 @@ class tileqr_desc(ctypes.Structure):
         ("tiles", ctypes.c_void_p), ("T", ctypes.c_void_p),
         ("sched", ctypes.c_void_p), ("sched_bytes", ctypes.c_size_t),
         ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+        ("domain", ctypes.c_int32), ("reserved", ctypes.c_int32), ("T2", ctypes.c_void_p),
     ]
 
 
@@ -114,6 +116,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_solve_refine": (i32, [dp, vp, i64, vp, vp, i32, ctypes.c_double, vp, sz, vp,
                                       ctypes.POINTER(tileqr_refine_info)]),
         "tileqr_trace_count": (i32, [dp, vp, ctypes.POINTER(ctypes.c_uint64)]),
+        "tileqr_workspace_size_tree": (i32, [i64, i64, i32, i32, i32, i32, ctypes.POINTER(sz)]),
+        "tileqr_factor_tree": (i32, [i64, i64, vp, i64, i32, i32, i32, i32, i32, vp, sz, vp, dp]),
+        "tileqr_get_tree_T": (i32, [dp, vp, i64, vp]),
+        "tileqr_task_graph": (i32, [i64, i64, i32, i32, i32, vp, vp, vp, vp, ctypes.POINTER(i64),
+                                    ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -197,6 +204,49 @@ def tileqr_factor(A: torch.Tensor, nb: int, ib: int, precision: int = TILEQR_FP6
     return Factorization(d, workspace, A.device)
 
 
+def tileqr_workspace_size_tree(m: int, n: int, nb: int, ib: int, precision: int = TILEQR_FP64,
+                               domain: int = 0) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().tileqr_workspace_size_tree(m, n, nb, ib, precision, domain, ctypes.byref(out)),
+           "tileqr_workspace_size_tree")
+    return out.value
+
+
+def tileqr_factor_tree(A: torch.Tensor, nb: int, ib: int, domain: int, precision: int = TILEQR_FP64,
+                       flags: int = 0, workspace: torch.Tensor | None = None, stream=None) -> "Factorization":
+    """Tree form (domains of `domain` tile rows, heads merged pairwise)."""
+    A = as_colmajor(A)
+    m, n = A.shape
+    need = tileqr_workspace_size_tree(m, n, nb, ib, precision, domain)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=A.device)
+    d = tileqr_desc()
+    rc = load().tileqr_factor_tree(m, n, ctypes.c_void_p(A.data_ptr()), _ld(A), nb, ib, domain, precision, flags,
+                                   ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream_ptr(stream),
+                                   ctypes.byref(d))
+    _check(rc, "tileqr_factor_tree")
+    return Factorization(d, workspace, A.device)
+
+
+def tileqr_task_graph(m: int, n: int, nb: int, domain: int = 0, what: int = 0):
+    """(tasks, ndeps, succ_ptr, succ) of the executed task graph, as numpy
+    arrays (host only; no GPU needed)."""
+    import numpy as np
+    lib = load()
+    nt, ne = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.tileqr_task_graph(m, n, nb, domain, what, None, None, None, None, ctypes.byref(nt),
+                                 ctypes.byref(ne)), "tileqr_task_graph")
+    tasks = np.zeros((nt.value, 4), dtype=np.int32)
+    ndeps = np.zeros(nt.value, dtype=np.int32)
+    ptr = np.zeros(nt.value + 1, dtype=np.int64)
+    succ = np.zeros(max(ne.value, 1), dtype=np.int64)
+    vp = ctypes.c_void_p
+    _check(lib.tileqr_task_graph(m, n, nb, domain, what, vp(tasks.ctypes.data), vp(ndeps.ctypes.data),
+                                 vp(ptr.ctypes.data), vp(succ.ctypes.data), ctypes.byref(nt), ctypes.byref(ne)),
+           "tileqr_task_graph")
+    return tasks, ndeps, ptr, succ[:ne.value]
+
+
 class Factorization:
     """A factorization living in a caller-owned (torch) workspace."""
 
@@ -236,6 +286,14 @@ class Factorization:
                                          ctypes.c_void_p(T.data_ptr()), max(d.p * d.ib, 1),
                                          _stream_ptr(stream)), "tileqr_get_factors")
         return AV, T
+
+    def tree_T(self, stream=None) -> torch.Tensor:
+        """The DTTQRT T strips of a tree-form factorization, (p*ib) x n."""
+        d = self.desc
+        T2 = colmajor_empty(d.p * d.ib, d.n, self.device)
+        _check(load().tileqr_get_tree_T(ctypes.byref(d), ctypes.c_void_p(T2.data_ptr()), max(d.p * d.ib, 1),
+                                        _stream_ptr(stream)), "tileqr_get_tree_T")
+        return T2
 
     def _apply_workspace(self, nrhs: int) -> torch.Tensor:
         out = ctypes.c_size_t(0)

@@ -1,0 +1,129 @@
+"""The task graph the persistent kernels execute (exported by the library's
+host-only tileqr_task_graph, built from the same functions the kernels call)
+against the dependencies the oracle derives mechanically from the tiles each
+task reads and writes, for Algorithm 2 and the tree form.
+
+Checked: the same task set; every task is released by exactly ndeps
+signals; the graph is acyclic and runs to completion; every mechanically
+required ordering is enforced (a path in the library graph); and every
+library edge is a real dependency (implied by the mechanical ones).  A wrong
+edge here would hang or corrupt the GPU run, so this is checked on the CPU
+first.  No GPU is needed."""
+import pytest
+
+import oracle
+
+CASES = [
+    (520, 200, 64, 0),      # Algorithm 2, ragged edges
+    (520, 200, 64, 100),    # domain >= p: flat
+    (520, 200, 64, 1),      # binary tree over every tile row
+    (520, 200, 64, 2),
+    (700, 300, 64, 3),
+    (64 * 23, 64 * 4, 64, 4),
+    (64 * 23, 64 * 4, 64, 5),
+    (200, 450, 64, 2),      # wide: p < q
+    (1100, 64, 64, 2),      # one tile column
+    (64 * 9, 64 * 9, 64, 2),
+]
+
+
+@pytest.fixture(scope="module")
+def tq():
+    from paper_0709_1272_gb300 import build
+    build.build()
+    from paper_0709_1272_gb300 import tileqr
+    tileqr.load()
+    return tileqr
+
+
+def _graph(tq, m, n, nb, h, what):
+    tasks, ndeps, ptr, succ = tq.tileqr_task_graph(m, n, nb, h, what)
+    keys = [tuple(int(x) for x in t) for t in tasks]
+    edges = [(a, int(b)) for a in range(len(keys)) for b in succ[ptr[a]:ptr[a + 1]]]
+    return keys, [int(x) for x in ndeps], edges
+
+
+def _ancestors(n, edges):
+    """Bit set of the ancestors of every node (Kahn order); also checks that
+    the graph is acyclic."""
+    preds = [[] for _ in range(n)]
+    succ = [[] for _ in range(n)]
+    indeg = [0] * n
+    for a, b in edges:
+        preds[b].append(a)
+        succ[a].append(b)
+        indeg[b] += 1
+    order = [v for v in range(n) if indeg[v] == 0]
+    head = 0
+    while head < len(order):
+        v = order[head]
+        head += 1
+        for w in succ[v]:
+            indeg[w] -= 1
+            if indeg[w] == 0:
+                order.append(w)
+    assert len(order) == n, "cycle or unreachable task"
+    anc = [0] * n
+    for v in order:
+        acc = 0
+        for u in preds[v]:
+            acc |= anc[u] | (1 << u)
+        anc[v] = acc
+    return anc
+
+
+def _compare(keys, ndeps, edges, otasks, opreds):
+    n = len(keys)
+    assert sorted(keys) == sorted(otasks)
+    assert len(set(keys)) == n
+    indeg = [0] * n
+    for _, b in edges:
+        indeg[b] += 1
+    assert indeg == ndeps
+    pos = {k: i for i, k in enumerate(keys)}
+    anc_lib = _ancestors(n, edges)
+    oedges = [(pos[p], pos[t]) for t, ps in opreds.items() for p in ps]
+    anc_or = _ancestors(n, oedges)
+    for a, b in oedges:     # every required order is enforced
+        assert (anc_lib[b] >> a) & 1, (keys[a], keys[b])
+    for a, b in edges:      # no edge without a real dependency behind it
+        assert (anc_or[b] >> a) & 1, (keys[a], keys[b])
+
+
+@pytest.mark.parametrize("m,n,nb,h", CASES)
+def test_factorization_graph(tq, m, n, nb, h):
+    keys, ndeps, edges = _graph(tq, m, n, nb, h, 0)
+    if h <= 0:
+        otasks, opreds = oracle.dependencies(m, n, nb)
+    else:
+        otasks, opreds = oracle.dependencies_tree(m, n, nb, h)
+    _compare(keys, ndeps, edges, otasks, opreds)
+
+
+@pytest.mark.parametrize("m,n,nb,h", CASES)
+def test_apply_graph(tq, m, n, nb, h):
+    keys, ndeps, edges = _graph(tq, m, n, nb, h, 1)
+    keys = [(k[0], k[1], k[3]) for k in keys]   # {kind, i, -1, k} -> (kind, i, k)
+    otasks, opreds = oracle.apply_dependencies_tree(m, n, nb, h)
+    _compare(keys, ndeps, edges, otasks, opreds)
+
+
+def test_task_counts_match_the_workspace_queues(tq):
+    # the write-once ready queues are sized from closed-form counts; they must
+    # equal the enumerated graph
+    import numpy as np
+    for (m, n, nb, h) in CASES:
+        tasks, _, _, _ = tq.tileqr_task_graph(m, n, nb, h, 0)
+        kinds = np.bincount(tasks[:, 0], minlength=6)
+        p, q = -(-m // nb), -(-n // nb)
+        H = p if (h <= 0 or h > p) else h
+        exp = [0] * 6
+        for k in range(min(p, q)):
+            P, nd, nq = p - k, -(-(p - k) // H), q - k - 1
+            exp[0] += nd
+            exp[1] += P - nd
+            exp[4] += nd - 1
+            exp[2] += nd * nq
+            exp[3] += (P - nd) * nq
+            exp[5] += (nd - 1) * nq
+        assert list(kinds) == exp
