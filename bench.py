@@ -243,6 +243,60 @@ def run_batched(args, dev, rank, world, barrier, dist):
     return out
 
 
+def run_tall(args, dev, rank, world, barrier, dist):
+    """Tall-skinny workload: 262144 x 512 N(0,1), nb 128, least squares with
+    16 N(0,1) right-hand sides.  Algorithm 2's flat tree (a chain of p - 1
+    DTSQRT per step) against the tree form (domains of 8 tile rows, heads
+    merged pairwise), FP64 and with tensor-core updates."""
+    import torch
+    from paper_0709_1272_gb300 import inputs, replicas, tileqr
+    m, n, nb = args.tall_m, 512, 128
+    ops = lapack_opcount(m, n)
+    A = tileqr.to_device_colmajor(inputs.normal_matrix(m, n, seed=20070709 + 3 + 1000 * rank), dev)
+    B = tileqr.to_device_colmajor(inputs.normal_matrix(m, 16, seed=20070709 + 6 + 1000 * rank), dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        out = None
+        best = float("inf")
+        for _ in range(reps):
+            barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return replicas.max_over_ranks(best, dist, dev), out
+
+    res = {"workload": f"tall-skinny tile QR, {m}x{n} N(0,1), nb={nb}; least squares with 16 N(0,1) "
+                       f"right-hand sides", "unit": UNIT, "timing": "CUDA events, best of the timed runs, "
+                       "max over ranks"}
+    variants = [("fp64_flat", tileqr.TILEQR_FP64, 16, 0, 1), ("fp64_tree", tileqr.TILEQR_FP64, 16, 8, 3),
+                ("tf32_tree", tileqr.TILEQR_TF32, 16, 16, 3)]
+    facs = {}
+    for label, prec, ib, h, reps in variants:
+        ws = torch.empty(tileqr.tileqr_workspace_size_tree(m, n, nb, ib, prec, h), dtype=torch.uint8, device=dev)
+        tileqr.tileqr_factor_tree(A, nb, ib, h, precision=prec, workspace=ws).check()   # warm-up
+        t, f = timed(lambda: tileqr.tileqr_factor_tree(A, nb, ib, h, precision=prec, workspace=ws), reps)
+        f.check()
+        res[label] = {"ms": t * 1e3, "value": world * ops / t / 1e9, "ib": ib,
+                      "domain": h if h > 0 else "flat (Algorithm 2)"}
+        facs[label] = (f, ws)
+    res["tree_speedup_fp64"] = res["fp64_flat"]["ms"] / res["fp64_tree"]["ms"]
+    res["value"] = res["fp64_tree"]["value"]
+    f = facs["fp64_tree"][0]
+    t, X = timed(lambda: f.solve_ls(B.clone()), 3)
+    r = B - A @ X
+    ratio = (torch.linalg.matrix_norm(A.t() @ r) /
+             (torch.linalg.matrix_norm(A) * torch.linalg.matrix_norm(r))).item()
+    res["solve_ls_ms"] = t * 1e3
+    res["ls_optimality"] = ratio   # ||A^T r|| / (||A|| ||r||)
+    del facs, A, B
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -263,6 +317,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched (4096 ragged matrices) measurement")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--no-tall", action="store_true",
+                    help="skip the tall-skinny (262144 x 512, flat vs tree) measurement")
+    ap.add_argument("--tall-m", type=int, default=262144)
     ap.add_argument("--loop-subset", type=int, default=512)
     args = ap.parse_args()
 
@@ -420,6 +477,12 @@ def main():
         torch.cuda.empty_cache()
         batched = run_batched(args, dev, rank, world, barrier, dist)
 
+    # ---- tall-skinny 262144 x 512: flat tree vs tree form
+    tall = None
+    if not args.no_tall:
+        torch.cuda.empty_cache()
+        tall = run_tall(args, dev, rank, world, barrier, dist)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -458,6 +521,8 @@ def main():
         out["mixed_ls"] = mixed
     if batched:
         out["batched"] = batched
+    if tall:
+        out["tall_skinny"] = tall
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(nb, ib)
     print(json.dumps(out), flush=True)
