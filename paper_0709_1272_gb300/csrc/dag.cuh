@@ -119,14 +119,15 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_fac
     __shared__ unsigned long long s_code;
     __shared__ int s_cmd;
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_mbar[2];
     uint32_t tmem = 0, mphase = 0;
     if (MIXED) {
         // one tensor-memory allocation and one mbarrier per persistent CTA
         if ((threadIdx.x >> 5) == 0)
             tc::tmem_alloc(&s_tmem, MixCfg<S>::TMEM_COLS);
         if (threadIdx.x == 0)
-            tc::mbar_init(&s_mbar, 1);
+            for (int b = 0; b < 2; b++)
+                tc::mbar_init(&s_mbar[b], 1);
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_fac
         decode_task(s_code, k, i, j);
         const int kind = g_kind(F.G, decode_tt(s_code), k, i, j);
         const unsigned long long t0 = Q.trace ? globaltimer_ns() : 0ull;
-        run_task<NB, S, MIXED>(sm, F, kind, k, i, j, tmem, &s_mbar, mphase, &Q.ctrl->error);
+        run_task<NB, S, MIXED>(sm, F, kind, k, i, j, tmem, s_mbar, mphase, &Q.ctrl->error);
         __syncthreads();
         release_graph(Q, F.G, kind, k, i, j);
         __syncthreads();
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
     __shared__ unsigned long long s_code;
     __shared__ int s_cmd;
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ FactorArgs s_F;
     __shared__ size_t s_cnt;
     uint32_t tmem = 0, mphase = 0;
@@ -257,7 +258,8 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
         if ((threadIdx.x >> 5) == 0)
             tc::tmem_alloc(&s_tmem, MixCfg<S>::TMEM_COLS);
         if (threadIdx.x == 0)
-            tc::mbar_init(&s_mbar, 1);
+            for (int b = 0; b < 2; b++)
+                tc::mbar_init(&s_mbar[b], 1);
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
         const FactorArgs F = s_F;
         const size_t cnt_off = s_cnt;
         const unsigned long long t0 = Q.trace ? globaltimer_ns() : 0ull;
-        run_task<NB, S, MIXED>(sm, F, task_kind(i, j, k), k, i, j, tmem, &s_mbar, mphase, &Q.ctrl->error);
+        run_task<NB, S, MIXED>(sm, F, task_kind(i, j, k), k, i, j, tmem, s_mbar, mphase, &Q.ctrl->error);
         __syncthreads();
         release_batched(Q, F, cnt_off, mat, k, i, j);
         __syncthreads();

@@ -28,18 +28,25 @@ struct MixCfg {
     static constexpr int NB = 128;
     static constexpr int KC = 32;                    // K extent of a staged operand chunk
     static constexpr int OPB = NB * KC * 4;          // one 128 x 32 tf32 operand: 16 KB
-    static constexpr int LDF = NB + 1;               // ld of the FP32 128 x 128 panels
+    static constexpr int OPSET = 4 * OPB;            // A hi, A lo, B hi, B lo: 64 KB
+    static constexpr int LDF = NB + 1;               // ld of the FP32 P / W panel (conflict-free columns)
+    static constexpr int LDG = NB + 4;               // ld of G (rows 16-byte aligned: float4 reads)
     static constexpr int OFF_AHI = 0;
     static constexpr int OFF_ALO = OPB;
     static constexpr int OFF_BHI = 2 * OPB;
     static constexpr int OFF_BLO = 3 * OPB;
-    static constexpr int OFF_PW = 4 * OPB;                          // P, then W (FP32)
+    static constexpr int OFF_PW = OPSET;                            // P + B, then W (FP32)
     static constexpr int OFF_G = OFF_PW + NB * LDF * 4;             // G (FP32)
-    static constexpr int OFF_T = OFF_G + NB * LDF * 4;              // T strip (FP32, s x 128)
+    static constexpr int OFF_T = OFF_G + NB * LDG * 4;              // T strip (FP32, s x 128)
     static constexpr int SMEM = OFF_T + S * NB * 4;
     static constexpr int TMEM_COLS = 256;                           // P / D at 0, G at 128
     static_assert(S == 16 || S == 32, "ib 16 or 32");
     static_assert(SMEM <= 232448, "shared memory budget");
+    // the second operand set of the double-buffered MMA rounds: the P / W area
+    // while P is still in tensor memory (phase 1), the G area once the block
+    // recurrence is done (phase 3)
+    static_assert(NB * LDF * 4 >= OPSET && NB * LDG * 4 >= OPSET, "second operand set fits");
+    static_assert(OFF_PW % 128 == 0 && OFF_G % 128 == 0, "operand sets 128-byte aligned");
 };
 
 // FP64 -> FP32 with integer operations: exponent rebias, mantissa funnel
@@ -108,11 +115,12 @@ __device__ __forceinline__ void store_split4(unsigned char *sm, int off_hi, int 
     *(float4 *)(sm + off_lo + byte_off) = l;
 }
 
-// One MMA round: make the staged operands visible to the tensor core, issue
-// the products from thread 0, commit, and wait (bounded).  Returns false
-// (and records an error) if the wait gives up.
+// Make the staged operands of one round visible to the tensor core and issue
+// its products from thread 0, committed to mbar (one of two: rounds alternate
+// between two operand sets, so the staging of round r+1 overlaps the MMAs of
+// round r).
 template <typename IssueFn>
-__device__ __forceinline__ bool mixed_mma_round(uint64_t *mbar, uint32_t &phase, int *err, IssueFn issue)
+__device__ __forceinline__ void mixed_issue(uint64_t *mbar, IssueFn issue)
 {
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -122,26 +130,30 @@ __device__ __forceinline__ bool mixed_mma_round(uint64_t *mbar, uint32_t &phase,
         issue();
         tc::commit(mbar);
     }
-    const bool ok = tc::mbar_wait(mbar, phase);
-    phase ^= 1u;
+}
+// Wait (bounded) for the last commit to operand set b; phase holds one parity
+// bit per set.  Returns false if the wait gave up.
+__device__ __forceinline__ bool mixed_wait(uint64_t *mbar, uint32_t &phase, int b)
+{
+    const bool ok = tc::mbar_wait(&mbar[b], (phase >> b) & 1u);
+    phase ^= 1u << b;
     tc::fence_after_sync();
-    if (!ok && threadIdx.x == 0)
-        atomicCAS(err, 0, TILEQR_ERR_TIMEOUT);
     return ok;
 }
 
 // Mixed DSSRFB (Bt != nullptr, V = full DTSQRT tile), DLARFB (Bt ==
 // nullptr, V = unit-lower DGEQRT tile) or DTTMQR (Bt != nullptr, V = upper
 // DTTQRT triangle: V = [I; V_B] as for DSSRFB, so G = V_B^T V_B again) on
-// FP64 tiles.  Returns false on a tensor-core wait timeout (an error is
-// recorded; the tile contents are then undefined).
+// FP64 tiles.  mbar: two mbarriers (one per operand set).  Returns false on a
+// tensor-core wait timeout (an error is recorded; the tile contents are then
+// undefined); the outcome is the same in every thread.
 template <int S, int VK>
 __device__ __noinline__ bool task_update_mixed(unsigned char *sm, double *Bt, double *Ct, const double *Vt,
                                                const double *Tt, uint32_t tmem, uint64_t *mbar, uint32_t &phase,
                                                int *err)
 {
     using M = MixCfg<S>;
-    constexpr int NB = 128, KC = M::KC, LDF = M::LDF, T_ = NB / S;
+    constexpr int NB = 128, KC = M::KC, LDF = M::LDF, LDG = M::LDG, T_ = NB / S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float *PW = (float *)(sm + M::OFF_PW);
     float *GS = (float *)(sm + M::OFF_G);
@@ -149,58 +161,87 @@ __device__ __noinline__ bool task_update_mixed(unsigned char *sm, double *Bt, do
     const uint32_t sbase = tc::smem_addr(sm);
     const uint32_t idesc = tc::idesc_tf32(128, 128);
     const uint32_t SBO = KC * 32, LBO = 128;
+    bool ok = true;
 
-    // ---- phase 1: P = V^T C and G = V^T V, K (tile rows) in chunks of 32
-    for (int r0 = 0; r0 < NB; r0 += KC) {
-        // unit u: operand row m (reflector a for A, tile column c for B), K = tile
-        // rows r0 + 4j .. +3; 8 lanes cover 32 contiguous doubles of one column
-        for (int u = tid; u < NB * (KC / 4); u += NT) {
-            const int j = u & 7, m = u >> 3, r = r0 + 4 * j;
-            const uint32_t off = tc::kmajor_off(m, 4 * j, KC);
-            store_split4(sm, M::OFF_AHI, M::OFF_ALO, off, f64_to_f32_bits(mixed_v_elem<VK>(Vt, r, m)),
-                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r + 1, m)),
-                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r + 2, m)),
-                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r + 3, m)));
-            const double *cp = Ct + (size_t)m * NB + r;
-            store_split4(sm, M::OFF_BHI, M::OFF_BLO, off, f64_to_f32_bits(ldcg(cp)), f64_to_f32_bits(ldcg(cp + 1)),
-                         f64_to_f32_bits(ldcg(cp + 2)), f64_to_f32_bits(ldcg(cp + 3)));
-        }
-        const uint32_t acc0 = r0 > 0 ? 1u : 0u;
-        const bool ok = mixed_mma_round(mbar, phase, err, [&]() {
-            for (int ks = 0; ks < KC / 8; ks++) {
-                const uint32_t o = ks * 256;
-                const uint64_t ah = tc::smem_desc(sbase + M::OFF_AHI + o, LBO, SBO);
-                const uint64_t al = tc::smem_desc(sbase + M::OFF_ALO + o, LBO, SBO);
-                const uint64_t bh = tc::smem_desc(sbase + M::OFF_BHI + o, LBO, SBO);
-                const uint64_t bl = tc::smem_desc(sbase + M::OFF_BLO + o, LBO, SBO);
-                const uint32_t acc = (acc0 | (uint32_t)ks) ? 1u : 0u;
-                tc::mma_tf32(tmem, ah, bh, idesc, acc);          // P
-                tc::mma_tf32(tmem, ah, bl, idesc, 1u);
-                tc::mma_tf32(tmem, al, bh, idesc, 1u);
-                tc::mma_tf32(tmem + 128, ah, ah, idesc, acc);    // G
-                tc::mma_tf32(tmem + 128, ah, al, idesc, 1u);
-                tc::mma_tf32(tmem + 128, al, ah, idesc, 1u);
+    // ---- phase 1: P = V^T C and G = V^T V, K (tile rows) in 4 chunks of 32.
+    // Unit u of a chunk: operand row m (reflector m for A, tile column m for
+    // B), K = tile rows r0 + 4j .. +3; 8 lanes cover 32 contiguous doubles of
+    // one column.  All loads of a thread are issued before any conversion.
+    {
+        const int set_off[2] = {0, M::OFF_PW};
+        for (int rr = 0; rr < NB / KC; rr++) {
+            const int b = rr & 1, r0 = rr * KC;
+            if (rr >= 2)
+                ok &= mixed_wait(mbar, phase, b);   // set b was read by round rr - 2
+            double v[4][4], c[4][4];
+#pragma unroll
+            for (int x = 0; x < 4; x++) {
+                const int u = tid + x * NT, j = u & 7, m = u >> 3, r = r0 + 4 * j;
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    v[x][e] = mixed_v_elem<VK>(Vt, r + e, m);
+                    c[x][e] = ldcg(Ct + (size_t)m * NB + r + e);
+                }
             }
-        });
-        if (!ok)
+#pragma unroll
+            for (int x = 0; x < 4; x++) {
+                const int u = tid + x * NT, j = u & 7, m = u >> 3;
+                const uint32_t off = tc::kmajor_off(m, 4 * j, KC);
+                store_split4(sm, set_off[b] + M::OFF_AHI, set_off[b] + M::OFF_ALO, off, f64_to_f32_bits(v[x][0]),
+                             f64_to_f32_bits(v[x][1]), f64_to_f32_bits(v[x][2]), f64_to_f32_bits(v[x][3]));
+                store_split4(sm, set_off[b] + M::OFF_BHI, set_off[b] + M::OFF_BLO, off, f64_to_f32_bits(c[x][0]),
+                             f64_to_f32_bits(c[x][1]), f64_to_f32_bits(c[x][2]), f64_to_f32_bits(c[x][3]));
+            }
+            const uint32_t base = sbase + set_off[b];
+            mixed_issue(&mbar[b], [&]() {
+                for (int ks = 0; ks < KC / 8; ks++) {
+                    const uint32_t o = ks * 256;
+                    const uint64_t ah = tc::smem_desc(base + M::OFF_AHI + o, LBO, SBO);
+                    const uint64_t al = tc::smem_desc(base + M::OFF_ALO + o, LBO, SBO);
+                    const uint64_t bh = tc::smem_desc(base + M::OFF_BHI + o, LBO, SBO);
+                    const uint64_t bl = tc::smem_desc(base + M::OFF_BLO + o, LBO, SBO);
+                    const uint32_t acc = (rr | ks) ? 1u : 0u;
+                    tc::mma_tf32(tmem, ah, bh, idesc, acc);          // P
+                    tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+                    tc::mma_tf32(tmem, al, bh, idesc, 1u);
+                    tc::mma_tf32(tmem + 128, ah, ah, idesc, acc);    // G
+                    tc::mma_tf32(tmem + 128, ah, al, idesc, 1u);
+                    tc::mma_tf32(tmem + 128, al, ah, idesc, 1u);
+                }
+            });
+        }
+        ok &= mixed_wait(mbar, phase, 0);
+        ok &= mixed_wait(mbar, phase, 1);
+        ok = __syncthreads_and(ok);
+        if (!ok) {
+            if (tid == 0)
+                atomicCAS(err, 0, TILEQR_ERR_TIMEOUT);
             return false;
+        }
     }
 
-    // ---- phase 2: P, G to shared memory; T strip to FP32; W recurrence
+    // ---- phase 2: P + B and G to shared memory (thread = TMEM lane = row),
+    // the T strip to FP32, then the block recurrence for W.  B is read here
+    // once, coalesced (a warp reads 32 consecutive rows of one column).
     {
         const int row = 32 * (warp & 3) + lane;
         const int cbase = (warp >> 2) * 64;
         const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
         for (int h = 0; h < 2; h++) {
+            const int c0 = cbase + 32 * h;
             float v[32];
-            tc::tmem_ld32(tmem + lane_off + cbase + 32 * h, v);
+            double bv[32];
 #pragma unroll
             for (int j = 0; j < 32; j++)
-                PW[row * LDF + cbase + 32 * h + j] = v[j];
-            tc::tmem_ld32(tmem + 128 + lane_off + cbase + 32 * h, v);
+                bv[j] = Bt ? ldcg(Bt + (size_t)(c0 + j) * NB + row) : 0.0;
+            tc::tmem_ld32(tmem + lane_off + c0, v);
 #pragma unroll
             for (int j = 0; j < 32; j++)
-                GS[row * LDF + cbase + 32 * h + j] = v[j];
+                PW[row * LDF + c0 + j] = v[j] + (Bt ? f64_to_f32_bits(bv[j]) : 0.0f);
+            tc::tmem_ld32(tmem + 128 + lane_off + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                GS[row * LDG + c0 + j] = v[j];
         }
     }
     for (int idx = tid; idx < S * NB; idx += NT)
@@ -209,6 +250,8 @@ __device__ __noinline__ bool task_update_mixed(unsigned char *sm, double *Bt, do
     __syncthreads();
 
     {
+        // thread (column c, half of the block's rows); G rows are read as
+        // float4 broadcasts (one address per warp)
         const int c = tid & (NB - 1);
         const int half = tid >> 7;
         constexpr int HR = S / 2;   // rows of a block per thread
@@ -216,25 +259,22 @@ __device__ __noinline__ bool task_update_mixed(unsigned char *sm, double *Bt, do
             const int a0 = l * S + half * HR;
             const int kdone = l * S;   // rows of W already final
             float y[HR];
-            double bv[HR];
 #pragma unroll
-            for (int i = 0; i < HR; i++) {
-                bv[i] = Bt ? ldcg(Bt + (size_t)c * NB + a0 + i) : 0.0;
-                y[i] = PW[(a0 + i) * LDF + c] + (Bt ? f64_to_f32_bits(bv[i]) : 0.0f);
-            }
+            for (int i = 0; i < HR; i++)
+                y[i] = PW[(a0 + i) * LDF + c];
             for (int ap = 0; ap < kdone; ap += 4) {
                 const float w0 = PW[(ap + 0) * LDF + c], w1 = PW[(ap + 1) * LDF + c];
                 const float w2 = PW[(ap + 2) * LDF + c], w3 = PW[(ap + 3) * LDF + c];
 #pragma unroll
                 for (int i = 0; i < HR; i++) {
-                    const float *g = GS + (a0 + i) * LDF + ap;
-                    y[i] = fmaf(-g[0], w0, y[i]);
-                    y[i] = fmaf(-g[1], w1, y[i]);
-                    y[i] = fmaf(-g[2], w2, y[i]);
-                    y[i] = fmaf(-g[3], w3, y[i]);
+                    const float4 g = *(const float4 *)(GS + (a0 + i) * LDG + ap);
+                    y[i] = fmaf(-g.x, w0, y[i]);
+                    y[i] = fmaf(-g.y, w1, y[i]);
+                    y[i] = fmaf(-g.z, w2, y[i]);
+                    y[i] = fmaf(-g.w, w3, y[i]);
                 }
             }
-            // Y_l rows go into PW (P_l is consumed), then W_l = T_l^T Y_l
+            // Y_l rows go into PW (P_l + B_l is consumed), then W_l = T_l^T Y_l
 #pragma unroll
             for (int i = 0; i < HR; i++)
                 PW[(a0 + i) * LDF + c] = y[i];
@@ -250,61 +290,98 @@ __device__ __noinline__ bool task_update_mixed(unsigned char *sm, double *Bt, do
             }
             __syncthreads();
 #pragma unroll
-            for (int i = 0; i < HR; i++) {
+            for (int i = 0; i < HR; i++)
                 PW[(a0 + i) * LDF + c] = w[i];
-                if (Bt)
-                    stcg(Bt + (size_t)c * NB + a0 + i, bv[i] - f32_to_f64_bits(w[i]));
-            }
             __syncthreads();
         }
     }
 
-    // ---- phase 3: D = V W, K (reflectors) in chunks of 32
-    for (int k0 = 0; k0 < NB; k0 += KC) {
-        // unit u: operand row r (tile row for A, tile column c = r for B),
-        // K = reflectors k0 + 4j .. +3; lanes run over consecutive rows
-        for (int u = tid; u < NB * (KC / 4); u += NT) {
-            const int r = u & (NB - 1), j = u >> 7, k = k0 + 4 * j;
-            const uint32_t off = tc::kmajor_off(r, 4 * j, KC);
-            store_split4(sm, M::OFF_AHI, M::OFF_ALO, off, f64_to_f32_bits(mixed_v_elem<VK>(Vt, r, k)),
-                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r, k + 1)),
-                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r, k + 2)),
-                         f64_to_f32_bits(mixed_v_elem<VK>(Vt, r, k + 3)));
-            // B operand (column c = r, reflector k) = W[k][c]
-            store_split4(sm, M::OFF_BHI, M::OFF_BLO, off, PW[k * LDF + r], PW[(k + 1) * LDF + r],
-                         PW[(k + 2) * LDF + r], PW[(k + 3) * LDF + r]);
+    // B -= W (FP64), coalesced: thread = row, 64 columns
+    if (Bt) {
+        const int row = 32 * (warp & 3) + lane;
+        const int cbase = (warp >> 2) * 64;
+        for (int h = 0; h < 2; h++) {
+            const int c0 = cbase + 32 * h;
+            double bv[32];
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                bv[j] = ldcg(Bt + (size_t)(c0 + j) * NB + row);
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                stcg(Bt + (size_t)(c0 + j) * NB + row, bv[j] - f32_to_f64_bits(PW[row * LDF + c0 + j]));
         }
-        const uint32_t acc0 = k0 > 0 ? 1u : 0u;
-        const bool ok = mixed_mma_round(mbar, phase, err, [&]() {
-            for (int ks = 0; ks < KC / 8; ks++) {
-                const uint32_t o = ks * 256;
-                const uint64_t ah = tc::smem_desc(sbase + M::OFF_AHI + o, LBO, SBO);
-                const uint64_t al = tc::smem_desc(sbase + M::OFF_ALO + o, LBO, SBO);
-                const uint64_t bh = tc::smem_desc(sbase + M::OFF_BHI + o, LBO, SBO);
-                const uint64_t bl = tc::smem_desc(sbase + M::OFF_BLO + o, LBO, SBO);
-                const uint32_t acc = (acc0 | (uint32_t)ks) ? 1u : 0u;
-                tc::mma_tf32(tmem, ah, bh, idesc, acc);
-                tc::mma_tf32(tmem, ah, bl, idesc, 1u);
-                tc::mma_tf32(tmem, al, bh, idesc, 1u);
-            }
-        });
-        if (!ok)
-            return false;
     }
 
-    // ---- phase 4: C -= D (FP64), row r = TMEM lane
+    // ---- phase 3: D = V W, K (reflectors) in 4 chunks of 32, operand sets
+    // alternating between the set at 0 and the G area (G is no longer needed).
+    // Unit u: operand row r (tile row for A, tile column c = r for B), K =
+    // reflectors k0 + 4j .. +3; lanes run over consecutive rows.
+    {
+        const int set_off[2] = {0, M::OFF_G};
+        for (int kk = 0; kk < NB / KC; kk++) {
+            const int b = kk & 1, k0 = kk * KC;
+            if (kk >= 2)
+                ok &= mixed_wait(mbar, phase, b);
+            double v[4][4];
+#pragma unroll
+            for (int x = 0; x < 4; x++) {
+                const int u = tid + x * NT, r = u & (NB - 1), j = u >> 7, k = k0 + 4 * j;
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    v[x][e] = mixed_v_elem<VK>(Vt, r, k + e);
+            }
+#pragma unroll
+            for (int x = 0; x < 4; x++) {
+                const int u = tid + x * NT, r = u & (NB - 1), j = u >> 7, k = k0 + 4 * j;
+                const uint32_t off = tc::kmajor_off(r, 4 * j, KC);
+                store_split4(sm, set_off[b] + M::OFF_AHI, set_off[b] + M::OFF_ALO, off, f64_to_f32_bits(v[x][0]),
+                             f64_to_f32_bits(v[x][1]), f64_to_f32_bits(v[x][2]), f64_to_f32_bits(v[x][3]));
+                // B operand (column c = r, reflector k) = W[k][c]
+                store_split4(sm, set_off[b] + M::OFF_BHI, set_off[b] + M::OFF_BLO, off, PW[k * LDF + r],
+                             PW[(k + 1) * LDF + r], PW[(k + 2) * LDF + r], PW[(k + 3) * LDF + r]);
+            }
+            const uint32_t base = sbase + set_off[b];
+            mixed_issue(&mbar[b], [&]() {
+                for (int ks = 0; ks < KC / 8; ks++) {
+                    const uint32_t o = ks * 256;
+                    const uint64_t ah = tc::smem_desc(base + M::OFF_AHI + o, LBO, SBO);
+                    const uint64_t al = tc::smem_desc(base + M::OFF_ALO + o, LBO, SBO);
+                    const uint64_t bh = tc::smem_desc(base + M::OFF_BHI + o, LBO, SBO);
+                    const uint64_t bl = tc::smem_desc(base + M::OFF_BLO + o, LBO, SBO);
+                    const uint32_t acc = (kk | ks) ? 1u : 0u;
+                    tc::mma_tf32(tmem, ah, bh, idesc, acc);
+                    tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+                    tc::mma_tf32(tmem, al, bh, idesc, 1u);
+                }
+            });
+        }
+        ok &= mixed_wait(mbar, phase, 0);
+        ok &= mixed_wait(mbar, phase, 1);
+        ok = __syncthreads_and(ok);
+        if (!ok) {
+            if (tid == 0)
+                atomicCAS(err, 0, TILEQR_ERR_TIMEOUT);
+            return false;
+        }
+    }
+
+    // ---- phase 4: C -= D (FP64), row r = TMEM lane; the 32 old values of a
+    // group are loaded before any store
     {
         const int r = 32 * (warp & 3) + lane;
         const int cbase = (warp >> 2) * 64;
         const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
         for (int h = 0; h < 2; h++) {
+            const int c0 = cbase + 32 * h;
             float v[32];
-            tc::tmem_ld32(tmem + lane_off + cbase + 32 * h, v);
+            double old[32];
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
-                double *p = Ct + (size_t)(cbase + 32 * h + j) * NB + r;
-                stcg(p, ldcg(p) - f32_to_f64_bits(v[j]));
-            }
+            for (int j = 0; j < 32; j++)
+                old[j] = ldcg(Ct + (size_t)(c0 + j) * NB + r);
+            tc::tmem_ld32(tmem + lane_off + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                stcg(Ct + (size_t)(c0 + j) * NB + r, old[j] - f32_to_f64_bits(v[j]));
         }
     }
     tc::fence_before_sync();
