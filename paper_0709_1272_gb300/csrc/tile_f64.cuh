@@ -299,15 +299,6 @@ __device__ __noinline__ void task_larfb(double *sm, double *Ct, const double *Vt
 }
 
 // ---------------------------------------------------------------------------
-// Householder panel factorization of S columns, one column at a time.
-// Column jj of the panel has its pivot alpha in the "head" array at
-// Ph[jj * ldh + jj], the rest of the head row at Ph[c * ldh + jj] (c > jj),
-// and its tail (the entries to annihilate) at Pt[jj * LDC + r] for r in
-// [t0(jj), rows).  For DGEQRT head and tail are the same array (t0 = jj + 1);
-// for DTSQRT the head is the R block and the tail the whole A column.
-// Reflector (our reading of the Householder step, Sec. 3.2.1): sigma =
-// ||tail||; sigma == 0 -> tau = 0, no reflection; else beta = -sign(alpha)
-// hypot(alpha, sigma), tau = (beta - alpha) / beta, v = tail / (alpha - beta).
 // Sum of squares of x[t0:rows) for extreme magnitudes (rare path, one
 // thread): returns s2 and scl with ||x|| = scl * sqrt(s2), scl = max |x|.
 __device__ __noinline__ static void rescaled_sumsq(const double *x, int t0, int rows, double *s2,
@@ -324,77 +315,100 @@ __device__ __noinline__ static void rescaled_sumsq(const double *x, int t0, int 
     *scl = mx;
 }
 
+// Reflector scalars of one panel column, formed by one warp: sigma^2 =
+// ||x[t0:rows)||^2 (warp reduction), then lane 0 computes beta, tau and the
+// tail scale 1 / (alpha - beta) and stores them to out[0..2].  FP64 sqrt and
+// division are long dependent sequences on GB300's FP64 pipe, so they run
+// once, in one lane.
+__device__ __forceinline__ void column_scalars(const double *x, int t0, int rows, double alpha, double *out,
+                                               int lane)
+{
+    double part0 = 0.0, part1 = 0.0;
+    int r = t0 + lane;
+    for (; r + 32 < rows; r += 64) {
+        part0 = fma(x[r], x[r], part0);
+        part1 = fma(x[r + 32], x[r + 32], part1);
+    }
+    if (r < rows)
+        part0 = fma(x[r], x[r], part0);
+    double s2 = warp_allsum(part0 + part1);
+    if (lane == 0) {
+        double beta = alpha, tau = 0.0, scale = 0.0;
+        if (s2 != 0.0) {
+            if (s2 > 1e-280 && s2 < 1e280 && fabs(alpha) < 1e140) {
+                // common case: alpha^2 + sigma^2 (and beta * d below) stay in
+                // range, so one sqrt and one reciprocal suffice:
+                // tau = (beta - alpha) / beta = -d^2 / (beta d), scale = 1/d = beta / (beta d)
+                const double h = sqrt(fma(alpha, alpha, s2));
+                beta = (alpha >= 0.0) ? -h : h;
+                const double d = alpha - beta;
+                const double inv = 1.0 / (beta * d);
+                tau = -d * d * inv;
+                scale = beta * inv;
+            } else {
+                // extreme magnitudes (rare): rescaled norm, hypot, two divisions
+                double scl = 1.0;
+                if (!(s2 > 1e-280 && s2 < 1e280))
+                    rescaled_sumsq(x, t0, rows, &s2, &scl);
+                const double h = hypot(alpha, scl * sqrt(s2));
+                beta = (alpha >= 0.0) ? -h : h;
+                tau = (beta - alpha) / beta;
+                scale = 1.0 / (alpha - beta);
+            }
+        }
+        out[0] = beta;
+        out[1] = tau;
+        out[2] = scale;
+    }
+    __syncwarp();
+}
+
+// Householder panel factorization of S columns, one column at a time.
+// Column jj of the panel has its pivot alpha in the "head" array at
+// Ph[jj * ldh + jj], the rest of the head row at Ph[c * ldh + jj] (c > jj),
+// and its tail (the entries to annihilate) at Pt[jj * LDC + r] for r in
+// [t0(jj), rows).  For DGEQRT head and tail are the same array (t0 = jj + 1);
+// for DTSQRT the head is the R block and the tail the whole A column.
+// Reflector (our reading of the Householder step, Sec. 3.2.1): sigma =
+// ||tail||; sigma == 0 -> tau = 0, no reflection; else beta = -sign(alpha)
+// hypot(alpha, sigma), tau = (beta - alpha) / beta, v = tail / (alpha - beta).
+//
+// Critical path: column jj+1 needs H_jj applied before its norm exists.
+// Warp 0 applies H_jj to column jj+1 and at once forms column jj+1's
+// scalars, while warps 1.. apply H_jj to the remaining columns; one block
+// barrier per column.  Scalars are double-buffered in shared memory.
 template <int NB, int S, bool TS>
 __device__ __noinline__ void panel_factor(double *sm, double *Pt, double *Ph, int ldh, int rows)
 {
     using C_ = F64Cfg<NB, S>;
     constexpr int LDC = C_::LDC;
-    double *red = sm + C_::OFF_RED;
+    double *red = sm + C_::OFF_RED;   // scalars of column jj at red[4 * (jj & 1)]
     double *taus = sm + C_::OFF_TAU;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int RPL = (NB + 31) / 32;   // tail rows per lane
+    if (warp == 0)
+        column_scalars(Pt, TS ? 0 : 1, rows, Ph[0], red, lane);
+    __syncthreads();
 #pragma unroll 1
     for (int jj = 0; jj < S; jj++) {
         const int t0 = TS ? 0 : jj + 1;
         double *x = Pt + jj * LDC;
-        double part = 0.0;
-        for (int r = t0 + tid; r < rows; r += NT)
-            part = fma(x[r], x[r], part);
-        part = warp_allsum(part);
-        if (lane == 0)
-            red[warp] = part;
-        __syncthreads();
-        // one thread forms the reflector scalars (FP64 sqrt, hypot and
-        // divisions are long sequences on the FP64 pipe: computing them once
-        // instead of in every warp keeps the pipe free)
-        if (tid == 0) {
-            // tree sum of the warp partials (3 dependent adds instead of 8)
-            const double s01 = red[0] + red[1], s23 = red[2] + red[3];
-            const double s45 = red[4] + red[5], s67 = red[6] + red[7];
-            double s2 = (s01 + s23) + (s45 + s67);
-            static_assert(NWARP == 8, "partial-sum tree assumes 8 warps");
-            const double alpha = Ph[jj * ldh + jj];
-            double beta = alpha, tau = 0.0, scale = 0.0;
-            if (s2 != 0.0) {
-                if (s2 > 1e-280 && s2 < 1e280 && fabs(alpha) < 1e140) {
-                    // common case: alpha^2 + sigma^2 (and beta * d below) stay in
-                    // range, so one sqrt and one reciprocal suffice:
-                    // tau = (beta - alpha) / beta = -d^2 / (beta d), scale = 1/d = beta / (beta d)
-                    const double h = sqrt(fma(alpha, alpha, s2));
-                    beta = (alpha >= 0.0) ? -h : h;
-                    const double d = alpha - beta;
-                    const double inv = 1.0 / (beta * d);
-                    tau = -d * d * inv;
-                    scale = beta * inv;
-                } else {
-                    // extreme magnitudes (rare): rescaled norm, hypot, two divisions
-                    double scl = 1.0;
-                    if (!(s2 > 1e-280 && s2 < 1e280))
-                        rescaled_sumsq(x, t0, rows, &s2, &scl);
-                    const double h = hypot(alpha, scl * sqrt(s2));
-                    beta = (alpha >= 0.0) ? -h : h;
-                    tau = (beta - alpha) / beta;
-                    scale = 1.0 / (alpha - beta);
-                }
-            }
-            red[2 * NWARP - 3] = beta;
-            red[2 * NWARP - 2] = tau;
-            red[2 * NWARP - 1] = scale;
-        }
-        __syncthreads();
-        const double beta = red[2 * NWARP - 3], tau = red[2 * NWARP - 2], scale = red[2 * NWARP - 1];
-        // apply H_jj to the remaining panel columns, one warp per column.  Each
-        // lane scales its slice of the tail once (v = x / (alpha - beta)), so
-        // the dot products see O(1) reflector entries and neither under- nor
-        // overflow for extreme column magnitudes.
-        if (tau != 0.0 && jj + 1 + warp < S) {
-            constexpr int RPL = (NB + 31) / 32;   // tail rows per lane
+        const double *sc = red + 4 * (jj & 1);
+        const double beta = sc[0], tau = sc[1], scale = sc[2];
+        // apply H_jj to columns jj+1..S-1 (warp 0: column jj+1; warps 1..:
+        // the rest, strided).  Each lane scales its slice of the tail once
+        // (v = x / (alpha - beta)), so the dot products see O(1) reflector
+        // entries and neither under- nor overflow for extreme magnitudes.
+        if (tau != 0.0 && jj + 1 < S) {
             double vs[RPL];
 #pragma unroll
             for (int k = 0; k < RPL; k++) {
                 const int r = t0 + lane + 32 * k;
                 vs[k] = (r < rows) ? x[r] * scale : 0.0;
             }
-            for (int c = jj + 1 + warp; c < S; c += NWARP) {
+            const int cfirst = (warp == 0) ? jj + 1 : jj + 1 + warp;
+            const int cstep = (warp == 0) ? S : NWARP - 1;
+            for (int c = cfirst; c < S; c += cstep) {
                 double *y = Pt + c * LDC;
                 double d = 0.0;
 #pragma unroll
@@ -414,7 +428,13 @@ __device__ __noinline__ void panel_factor(double *sm, double *Pt, double *Ph, in
                     if (r < rows)
                         y[r] = fma(-tw, vs[k], y[r]);
                 }
+                __syncwarp();
             }
+        }
+        // scalars of the next column (its update by H_jj, if any, was warp 0's)
+        if (warp == 0 && jj + 1 < S) {
+            const int c = jj + 1;
+            column_scalars(Pt + c * LDC, TS ? 0 : c + 1, rows, Ph[c * ldh + c], red + 4 * (c & 1), lane);
         }
         __syncthreads();
         for (int r = t0 + tid; r < rows; r += NT)
@@ -427,11 +447,19 @@ __device__ __noinline__ void panel_factor(double *sm, double *Pt, double *Ph, in
     __syncthreads();
 }
 
-// Build T_l (S x S upper) from the staged V_l ([r][a], rows in [r0, r1)) and the
-// taus: forward columnwise compact-WY recurrence T(0:j-1, j) = -tau_j
-// T(0:j-1, 0:j-1) V(:,0:j-1)^T v_j, T(j,j) = tau_j (Schreiber-Van Loan, the
-// accumulation named in Sec. 3.2.1).  Result in Ts; also written to the
-// global strip Tt (block at column l0), lower parts zero.
+// Build T_l (S x S upper) from the staged V_l ([r][a], rows in [r0, r1)) and
+// the taus, written to Ts and to the global strip Tt (block at column l0,
+// lower parts zero).  T_l is the compact-WY factor of Schreiber and Van Loan
+// (the accumulation named in Sec. 3.2.1), H_0..H_{S-1} = I - V T V^T.  It is
+// formed here through the identity T^{-1} = diag(1/tau) + striu(V^T V) (the
+// "UT transform" of Joffrain, Low, Quintana-Orti, van de Geijn and Van Zee,
+// 2006), solved column by column by back substitution: column j is
+// independent of the others, so all S columns run in parallel (one
+// half-warp each) and the dependent chain per column is j steps instead of
+// the forward recurrence's sum over all columns:
+//   T(j,j) = tau_j,  T(i,j) = -tau_i sum_{b=i+1..j} G(i,b) T(b,j), i < j.
+// (A zero tau_i gives a zero row i, as it must.)  The Gram entries are
+// summed by two threads per pair with four partial sums each.
 template <int NB, int S>
 __device__ __noinline__ void build_t(double *sm, int r0, double *Tt, int l0, int r1 = NB)
 {
@@ -441,46 +469,68 @@ __device__ __noinline__ void build_t(double *sm, int r0, double *Tt, int l0, int
     double *Ts = sm + C_::OFF_T;
     const double *taus = sm + C_::OFF_TAU;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // Gram entries G(i,j), i < j, into the strict upper part of Ts
+    // Gram entries G(i,j), i < j, into the strict upper part of Ts: thread
+    // pair (2 pidx, 2 pidx + 1) splits the rows of one pair (i, j)
     constexpr int NPAIR = S * (S - 1) / 2;
-    for (int pidx = tid; pidx < NPAIR; pidx += NT) {
-        // unrank pidx -> (i, j) with i < j, column-major over the strict upper triangle
-        int j = 1, base = 0;
-        while (base + j <= pidx) {
-            base += j;
-            j++;
+    constexpr int NU = (2 * NPAIR + 31) / 32 * 32;   // whole warps (the pair shuffle)
+    for (int u = tid; u < NU; u += NT) {
+        const int pidx = u >> 1, side = u & 1;
+        double g = 0.0;
+        int i = 0, j = 1;
+        if (pidx < NPAIR) {
+            // unrank pidx -> (i, j) with i < j, column-major over the strict upper triangle
+            int base = 0;
+            while (base + j <= pidx) {
+                base += j;
+                j++;
+            }
+            i = pidx - base;
+            const int mid = r0 + (r1 - r0) / 2;
+            const int ra = side ? mid : r0, rb = side ? r1 : mid;
+            double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
+            int r = ra;
+            for (; r + 3 < rb; r += 4) {
+                g0 = fma(Vs[r * LDV + i], Vs[r * LDV + j], g0);
+                g1 = fma(Vs[(r + 1) * LDV + i], Vs[(r + 1) * LDV + j], g1);
+                g2 = fma(Vs[(r + 2) * LDV + i], Vs[(r + 2) * LDV + j], g2);
+                g3 = fma(Vs[(r + 3) * LDV + i], Vs[(r + 3) * LDV + j], g3);
+            }
+            for (; r < rb; r++)
+                g0 = fma(Vs[r * LDV + i], Vs[r * LDV + j], g0);
+            g = (g0 + g1) + (g2 + g3);
         }
-        const int i = pidx - base;
-        double g0 = 0.0, g1 = 0.0;
-        int r = r0;
-        for (; r + 1 < r1; r += 2) {
-            g0 = fma(Vs[r * LDV + i], Vs[r * LDV + j], g0);
-            g1 = fma(Vs[(r + 1) * LDV + i], Vs[(r + 1) * LDV + j], g1);
-        }
-        if (r < r1)
-            g0 = fma(Vs[r * LDV + i], Vs[r * LDV + j], g0);
-        Ts[i + j * S] = g0 + g1;
-    }
-    for (int idx = tid; idx < S * S; idx += NT) {
-        const int i = idx % S, j = idx / S;
-        if (i == j)
-            Ts[idx] = taus[j];
-        else if (i > j)
-            Ts[idx] = 0.0;
+        g += __shfl_xor_sync(0xffffffffu, g, 1);
+        if (pidx < NPAIR && side == 0)
+            Ts[i + j * S] = g;
     }
     __syncthreads();
-    if (warp == 0) {
-        for (int j = 1; j < S; j++) {
-            const double tj = Ts[j + j * S];
-            double acc = 0.0;
-            if (lane < j)
-                for (int b = lane; b < j; b++)
-                    acc = fma(Ts[lane + b * S], Ts[b + j * S], acc);
-            __syncwarp();
-            if (lane < j)
-                Ts[lane + j * S] = -tj * acc;
-            __syncwarp();
+    // back substitution: column j by a group of S lanes (lane i = row i);
+    // results stay in registers until every column has read the Gram entries
+    constexpr int GW = S;                         // lanes per column
+    constexpr int CPW = 32 / GW;                  // columns per warp
+    constexpr int NROUND = S / (NWARP * CPW);     // ib 16: 1 round, ib 32: 4
+    static_assert(NROUND >= 1 && NROUND * NWARP * CPW == S, "column rounds");
+    const int i = lane % GW;
+    const unsigned gmask = (GW == 32) ? 0xffffffffu : (0xFFFFu << (lane & 16));
+    double tv[NROUND];
+#pragma unroll
+    for (int rd = 0; rd < NROUND; rd++) {
+        const int j = (rd * NWARP + warp) * CPW + lane / GW;
+        double acc = 0.0, tij = (i == j) ? taus[j] : 0.0;
+        for (int b = j; b >= 1; b--) {
+            const double tb = __shfl_sync(gmask, tij, b, GW);   // T(b,j), final
+            if (i < b)
+                acc = fma(Ts[i + b * S], tb, acc);              // G(i,b) T(b,j)
+            if (i == b - 1)
+                tij = -taus[i] * acc;
         }
+        tv[rd] = (i <= j) ? tij : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rd = 0; rd < NROUND; rd++) {
+        const int j = (rd * NWARP + warp) * CPW + lane / GW;
+        Ts[i + j * S] = tv[rd];
     }
     __syncthreads();
     for (int idx = tid; idx < S * S; idx += NT)
