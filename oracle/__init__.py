@@ -62,11 +62,12 @@ def _load():
                                                      i64, ctypes.POINTER(ctypes.c_int32)]
         lib.oracle_apply_qt_tree.argtypes = [i64, i64, dp, i64, i32, i32, i32, dp, i64, dp, i64, i64, dp,
                                              i64]
+        lib.oracle_apply_q_tree.argtypes = [i64, i64, dp, i64, i32, i32, i32, dp, i64, dp, i64, i64, dp, i64]
         lib.oracle_flops.restype = ctypes.c_double
         lib.oracle_set_mutation.argtypes = [i32]
         for f in (lib.oracle_tiled_qr, lib.oracle_tiled_qr_ordered, lib.oracle_apply_qt,
                   lib.oracle_solve_ls, lib.oracle_unblocked_qr, lib.oracle_tiled_qr_tree,
-                  lib.oracle_tiled_qr_tree_ordered, lib.oracle_apply_qt_tree):
+                  lib.oracle_tiled_qr_tree_ordered, lib.oracle_apply_qt_tree, lib.oracle_apply_q_tree):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -199,6 +200,31 @@ def apply_qt(f: Factored, B) -> np.ndarray:
     if rc:
         raise ValueError(f"oracle_apply_qt: illegal argument {rc}")
     return B
+
+
+def apply_q(f: Factored, B) -> np.ndarray:
+    """Q B (Q itself, not Q^T) for the Q held in a Factored result: the
+    update transformations replayed in reverse order, each with its inner
+    blocks reversed and T_l instead of T_l^T."""
+    lib = _load()
+    B = _fortran(B)
+    if B.ndim == 1:
+        B = B.reshape(-1, 1, order="F")
+    T2 = f.T2 if f.T2 is not None else np.zeros((1, 1), order="F")
+    rc = lib.oracle_apply_q_tree(f.m, f.n, _dp(f.A), max(f.m, 1), f.nb, f.ib, int(f.h), _dp(f.T), f.T.shape[0],
+                                 _dp(T2), T2.shape[0], B.shape[1], _dp(B), max(f.m, 1))
+    if rc:
+        raise ValueError(f"oracle_apply_q_tree: illegal argument {rc}")
+    return B
+
+
+def form_q(f: Factored, ncols: int | None = None) -> np.ndarray:
+    """The first ncols (default min(m, n)) columns of Q, m x ncols: Q applied
+    to the leading columns of the identity."""
+    k = min(f.m, f.n) if ncols is None else ncols
+    E = np.zeros((f.m, k), order="F")
+    E[np.arange(min(f.m, k)), np.arange(min(f.m, k))] = 1.0
+    return apply_q(f, E)
 
 
 def solve_ls(f: Factored, B) -> np.ndarray:

@@ -50,7 +50,9 @@ static double g_flops = 0.0;
  * plausible errors.  0 = correct arithmetic.  1 = apply T instead of T^T in
  * the block updates, 2 = flip the sign of beta, 3 = drop the B_l -= W update
  * in DSSRFB, 4 = drop the T off-diagonal recurrence, 5 = leave the diagonal
- * row out of the triangular reflectors of the tree variant (DTTQRT/DTTSSRFB). */
+ * row out of the triangular reflectors of the tree variant (DTTQRT/DTTSSRFB),
+ * 6 = apply the inner blocks of Q (not Q^T) in forward instead of reverse
+ * order. */
 static int g_mutation = 0;
 
 void oracle_set_mutation(int m) { g_mutation = m; }
@@ -139,6 +141,30 @@ static void trmm_tt(int sb, const double *Tl, int ldt, int ncC, double *W, int l
     g_flops += (double)ncC * sb * (sb + 1);
 }
 
+/* W (sb x ncC) = T_l W (the non-transposed product, for applying Q itself):
+ * (T W)(a) = sum_{b >= a} T(a,b) W(b); ascending a leaves the rows still
+ * needed unread. */
+static void trmm_tn(int sb, const double *Tl, int ldt, int ncC, double *W, int ldw)
+{
+    for (int c = 0; c < ncC; c++)
+        for (int a = 0; a < sb; a++) {
+            double acc = 0.0;
+            for (int b = a; b < sb; b++)
+                acc += EL(Tl, ldt, a, b) * EL(W, ldw, b, c);
+            EL(W, ldw, a, c) = acc;
+        }
+    g_flops += (double)ncC * sb * (sb + 1);
+}
+
+/* First inner block of a sweep over nrefl reflectors: the first (Q^T,
+ * blocks in order) or the last (Q, blocks in reverse order). */
+static int block_first(int nrefl, int ib, int notrans)
+{
+    return (notrans && g_mutation != 6) ? ((nrefl - 1) / ib) * ib : 0;
+}
+static int block_more(int l0, int nrefl, int notrans) { return (notrans && g_mutation != 6) ? l0 >= 0 : l0 < nrefl; }
+static int block_next(int l0, int ib, int notrans) { return (notrans && g_mutation != 6) ? l0 - ib : l0 + ib; }
+
 /* ---------------------------------------------------------------------- */
 /* DLARFB: C (mrC x ncC, rows of the diagonal tile row) <- Q^T C where Q is
  * the product of the nrefl reflectors stored DGEQRT-style in V (mr x nrefl)
@@ -146,13 +172,13 @@ static void trmm_tt(int sb, const double *Tl, int ldt, int ncC, double *W, int l
  * touching rows l*ib .. mr-1 (Sec. 3.2.1, DLARFB; inner blocking Sec. 3.2.3).
  * col0/ncols restrict the update to a column range of C (DGEQRT reuses this
  * for its own trailing columns). */
-static void larfb_t(int mr, int nrefl, const double *V, int ldv, const double *Tk, int ldt,
-                    int ib, double *C, int ldc, int ncols, double *work)
+static void larfb_x(int mr, int nrefl, const double *V, int ldv, const double *Tk, int ldt,
+                    int ib, double *C, int ldc, int ncols, double *work, int notrans)
 {
-    for (int l0 = 0; l0 < nrefl; l0 += ib) {
+    for (int l0 = block_first(nrefl, ib, notrans); block_more(l0, nrefl, notrans); l0 = block_next(l0, ib, notrans)) {
         int sb = imin(ib, nrefl - l0);
         if (l0 >= mr)
-            break;
+            continue;   /* no reflector of this block exists in a short tile */
         double *W = work; /* sb x ncols, ld sb */
         for (int c = 0; c < ncols; c++)
             for (int a = 0; a < sb; a++) {
@@ -162,7 +188,10 @@ static void larfb_t(int mr, int nrefl, const double *V, int ldv, const double *T
                 EL(W, sb, a, c) = acc;
             }
         g_flops += 2.0 * sb * ncols * (mr - l0);
-        trmm_tt(sb, &EL(Tk, ldt, 0, l0), ldt, ncols, W, sb);
+        if (notrans)
+            trmm_tn(sb, &EL(Tk, ldt, 0, l0), ldt, ncols, W, sb);
+        else
+            trmm_tt(sb, &EL(Tk, ldt, 0, l0), ldt, ncols, W, sb);
         for (int c = 0; c < ncols; c++)
             for (int r = l0; r < mr; r++) {
                 double acc = 0.0;
@@ -173,16 +202,21 @@ static void larfb_t(int mr, int nrefl, const double *V, int ldv, const double *T
         g_flops += 2.0 * sb * ncols * (mr - l0);
     }
 }
+static void larfb_t(int mr, int nrefl, const double *V, int ldv, const double *Tk, int ldt, int ib, double *C,
+                    int ldc, int ncols, double *work)
+{
+    larfb_x(mr, nrefl, V, ldv, Tk, ldt, ib, C, ldc, ncols, work, 0);
+}
 
 /* DSSRFB: [B; C] <- Q^T [B; C] where Q is the product of the nrefl reflectors
  * of a DTSQRT, V = [I; VA] with VA (mrC x nrefl), T strip Tk.  B has nrefl
  * meaningful rows (rows of the diagonal tile row), C is mrC x ncols.  For each
  * inner block l: W = T_l^T (B_l + VA_l^T C); B_l -= W; C -= VA_l W
  * (Sec. 3.2.1, DSSRFB; Sec. 3.2.3 and Fig. 4). */
-static void ssrfb_t(int nrefl, int mrC, const double *VA, int ldv, const double *Tk, int ldt,
-                    int ib, double *B, int ldb, double *C, int ldc, int ncols, double *work)
+static void ssrfb_x(int nrefl, int mrC, const double *VA, int ldv, const double *Tk, int ldt,
+                    int ib, double *B, int ldb, double *C, int ldc, int ncols, double *work, int notrans)
 {
-    for (int l0 = 0; l0 < nrefl; l0 += ib) {
+    for (int l0 = block_first(nrefl, ib, notrans); block_more(l0, nrefl, notrans); l0 = block_next(l0, ib, notrans)) {
         int sb = imin(ib, nrefl - l0);
         double *W = work;
         for (int c = 0; c < ncols; c++)
@@ -193,7 +227,10 @@ static void ssrfb_t(int nrefl, int mrC, const double *VA, int ldv, const double 
                 EL(W, sb, a, c) = acc;
             }
         g_flops += 2.0 * sb * ncols * mrC;
-        trmm_tt(sb, &EL(Tk, ldt, 0, l0), ldt, ncols, W, sb);
+        if (notrans)
+            trmm_tn(sb, &EL(Tk, ldt, 0, l0), ldt, ncols, W, sb);
+        else
+            trmm_tt(sb, &EL(Tk, ldt, 0, l0), ldt, ncols, W, sb);
         if (g_mutation != 3) {
             for (int c = 0; c < ncols; c++)
                 for (int a = 0; a < sb; a++)
@@ -209,6 +246,11 @@ static void ssrfb_t(int nrefl, int mrC, const double *VA, int ldv, const double 
             }
         g_flops += 2.0 * sb * ncols * mrC;
     }
+}
+static void ssrfb_t(int nrefl, int mrC, const double *VA, int ldv, const double *Tk, int ldt, int ib, double *B,
+                    int ldb, double *C, int ldc, int ncols, double *work)
+{
+    ssrfb_x(nrefl, mrC, VA, ldv, Tk, ldt, ib, B, ldb, C, ldc, ncols, work, 0);
 }
 
 /* Forward columnwise compact-WY recurrence for one inner block: with
@@ -360,10 +402,10 @@ static int tt_len(int j, int mr)
  * has tt_len(j0 + a, mrV) meaningful rows), T strip Tk, B the nrefl rows of
  * the top tile row and C the bottom tile row (ncols columns).  Per inner
  * block l: W = T_l^T (B_l + VB_l^T C); B_l -= W; C -= VB_l W. */
-static void ttssrfb_t(int nrefl, int j0, int mrV, const double *VB, int ldv, const double *Tk, int ldt,
-                      int ib, double *B, int ldb, double *C, int ldc, int ncols, double *work)
+static void ttssrfb_x(int nrefl, int j0, int mrV, const double *VB, int ldv, const double *Tk, int ldt,
+                      int ib, double *B, int ldb, double *C, int ldc, int ncols, double *work, int notrans)
 {
-    for (int l0 = 0; l0 < nrefl; l0 += ib) {
+    for (int l0 = block_first(nrefl, ib, notrans); block_more(l0, nrefl, notrans); l0 = block_next(l0, ib, notrans)) {
         int sb = imin(ib, nrefl - l0);
         double *W = work;
         for (int c = 0; c < ncols; c++)
@@ -375,7 +417,10 @@ static void ttssrfb_t(int nrefl, int j0, int mrV, const double *VB, int ldv, con
                 EL(W, sb, a, c) = acc;
                 g_flops += 2.0 * len;
             }
-        trmm_tt(sb, &EL(Tk, ldt, 0, l0), ldt, ncols, W, sb);
+        if (notrans)
+            trmm_tn(sb, &EL(Tk, ldt, 0, l0), ldt, ncols, W, sb);
+        else
+            trmm_tt(sb, &EL(Tk, ldt, 0, l0), ldt, ncols, W, sb);
         for (int c = 0; c < ncols; c++)
             for (int a = 0; a < sb; a++)
                 EL(B, ldb, l0 + a, c) -= EL(W, sb, a, c);
@@ -388,6 +433,11 @@ static void ttssrfb_t(int nrefl, int j0, int mrV, const double *VB, int ldv, con
                 g_flops += 2.0 * len;
             }
     }
+}
+static void ttssrfb_t(int nrefl, int j0, int mrV, const double *VB, int ldv, const double *Tk, int ldt, int ib,
+                      double *B, int ldb, double *C, int ldc, int ncols, double *work)
+{
+    ttssrfb_x(nrefl, j0, mrV, VB, ldv, Tk, ldt, ib, B, ldb, C, ldc, ncols, work, 0);
 }
 
 /* DTTQRT: QR of [R1; R2] with R1 the nc x nc upper triangle of the top tile
@@ -756,6 +806,57 @@ int oracle_apply_qt_tree(int64_t m, int64_t n, const double *A, int64_t lda, int
                           tstrip(&g, T2m, ldt2, e, k), (int)ldt2, ib, &B[(size_t)pt * nb], (int)ldb,
                           &B[(size_t)e * nb], (int)ldb, (int)nrhs, work);
             }
+    }
+    free(work);
+    return 0;
+}
+
+/* B (m x nrhs) <- Q B for a factorization by oracle_tiled_qr_tree (same h;
+ * h <= 0 or h >= p: Algorithm 2, T2 unused and may be NULL).  Q is the
+ * product of the tasks' transformations in the order they ran, so Q B
+ * applies the update kernels in the reverse sequential order, each with its
+ * inner blocks reversed and T_l instead of T_l^T. */
+int oracle_apply_q_tree(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib, int h,
+                        const double *T, int64_t ldt, const double *T2, int64_t ldt2, int64_t nrhs, double *B,
+                        int64_t ldb)
+{
+    int rc = check_args(m, n, lda, nb, ib, ldt);
+    if (rc)
+        return rc;
+    if (ldb < (m > 1 ? m : 1))
+        return -14;
+    geom g = make_geom(m, n, nb, ib);
+    const int H = dom_size(&g, h);
+    if (H < g.p && (T2 == NULL || ldt2 < (int64_t)g.p * ib))
+        return -10;
+    double *work = malloc(sizeof(double) * (size_t)ib * (size_t)(nrhs > 0 ? nrhs : 1));
+    int kmax = g.p < g.q ? g.p : g.q;
+    double *Am = (double *)A, *Tm = (double *)T, *T2m = (double *)T2;
+    for (int k = kmax - 1; k >= 0; k--) {
+        int ndom = (g.p - k + H - 1) / H, nck = nc_of(&g, k);
+        int top = 0;
+        while ((1 << (top + 1)) < ndom)
+            top++;
+        for (int lev = ((1 << top) < ndom) ? top : -1; lev >= 0; lev--) {
+            int dmax = ((ndom - (1 << lev) - 1) / (2 << lev)) * (2 << lev);
+            for (int d = dmax; d >= 0; d -= 2 << lev) {
+                if (d + (1 << lev) >= ndom)
+                    continue;
+                int e = k + (d + (1 << lev)) * H, pt = k + d * H;
+                ttssrfb_x(nck, 0, mr_of(&g, e), tile(&g, Am, lda, e, k), (int)lda, tstrip(&g, T2m, ldt2, e, k),
+                          (int)ldt2, ib, &B[(size_t)pt * nb], (int)ldb, &B[(size_t)e * nb], (int)ldb, (int)nrhs,
+                          work, 1);
+            }
+        }
+        for (int d = ndom - 1; d >= 0; d--) {
+            int hd = k + d * H, last = imin(hd + H, g.p) - 1;
+            double *Bh = &B[(size_t)hd * nb];
+            for (int i = last; i > hd; i--)
+                ssrfb_x(nck, mr_of(&g, i), tile(&g, Am, lda, i, k), (int)lda, tstrip(&g, Tm, ldt, i, k), (int)ldt,
+                        ib, Bh, (int)ldb, &B[(size_t)i * nb], (int)ldb, (int)nrhs, work, 1);
+            larfb_x(mr_of(&g, hd), nck, tile(&g, Am, lda, hd, k), (int)lda, tstrip(&g, Tm, ldt, hd, k), (int)ldt,
+                    ib, Bh, (int)ldb, (int)nrhs, work, 1);
+        }
     }
     free(work);
     return 0;

@@ -152,3 +152,47 @@ def test_planted_tree_mistake_is_caught():
     finally:
         oracle.set_mutation(0)
     assert err > 1e-3
+
+
+# ---------------------------------------------------------------------------
+# Q itself (not Q^T): the reverse replay, pinned by orthogonality identities
+@pytest.mark.parametrize("m,n,nb,ib,h", [(700, 300, 64, 16, 0), (700, 300, 64, 16, 2), (512, 256, 64, 32, 1),
+                                         (200, 450, 64, 16, 0), (1100, 64, 64, 16, 3)])
+def test_apply_q_inverts_apply_qt(m, n, nb, ib, h):
+    A = inputs.normal_matrix(m, n, 51 + h)
+    f = oracle.tiled_qr_tree(A, nb, ib, h) if h else oracle.tiled_qr(A, nb, ib)
+    B = inputs.normal_matrix(m, 9, 52)
+    # Q (Q^T B) = B and Q^T (Q B) = B, to rounding
+    assert np.abs(oracle.apply_q(f, oracle.apply_qt(f, B)) - B).max() <= 50 * m * EPS
+    assert np.abs(oracle.apply_qt(f, oracle.apply_q(f, B)) - B).max() <= 50 * m * EPS
+    # Q [R; 0] = A: the factorization is reproduced
+    k = min(m, n)
+    RZ = np.zeros((m, n), order="F")
+    RZ[:k, :] = f.R()
+    assert np.abs(oracle.apply_q(f, RZ) - A).max() <= 50 * m * EPS * np.abs(A).max()
+
+
+@pytest.mark.parametrize("h", [0, 2])
+def test_form_q_is_thin_orthonormal_factor(h):
+    m, n = 600, 250
+    A = inputs.uniform_matrix(m, n, 61)
+    f = oracle.tiled_qr_tree(A, 64, 16, h) if h else oracle.tiled_qr(A, 64, 16)
+    Q = oracle.form_q(f)
+    assert Q.shape == (m, n)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 20 * m * EPS
+    assert np.linalg.norm(A - Q @ f.R()) / np.linalg.norm(A) <= 20 * m * EPS
+    # Q^T applied to the identity is the transpose of the full Q
+    Qfull = oracle.apply_q(f, np.eye(m))
+    assert np.abs(Qfull - oracle.explicit_qt(f).T).max() <= 50 * m * EPS
+
+
+def test_planted_block_order_mistake_in_apply_q_is_caught():
+    A = inputs.normal_matrix(300, 200, 71)
+    f = oracle.tiled_qr(A, 64, 16)
+    B = inputs.normal_matrix(300, 3, 72)
+    try:
+        oracle.set_mutation(6)   # Q's inner blocks applied in forward order
+        err = np.abs(oracle.apply_q(f, oracle.apply_qt(f, B)) - B).max()
+    finally:
+        oracle.set_mutation(0)
+    assert err > 1e-6
