@@ -216,6 +216,20 @@ int tileqr_apply_workspace_size(const tileqr_desc *d, int64_t nrhs, size_t *byte
 int tileqr_apply_qt(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
                     size_t ws_bytes, tileqr_stream_t stream);
 
+/* B <- Q B (Q itself): the same transformations in the reverse order, each
+ * with its inner blocks reversed and T_l in place of T_l^T.  Arguments,
+ * workspace and returns as tileqr_apply_qt. */
+int tileqr_apply_q(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace, size_t ws_bytes,
+                   tileqr_stream_t stream);
+
+/* The leading ncols columns of Q (0 <= ncols <= m; ncols = min(m,n) gives
+ * the thin factor with A = Q R), written to Q (device, column-major m x
+ * ncols, ldq >= max(1,m)): Q applied to the identity's first columns.
+ *   workspace  tileqr_apply_workspace_size(d, ncols) bytes
+ * Asynchronous.  Returns 0, -i, TILEQR_ERR_WORKSPACE, TILEQR_ERR_CUDA. */
+int tileqr_form_q(const tileqr_desc *d, double *Q, int64_t ldq, int64_t ncols, void *workspace, size_t ws_bytes,
+                  tileqr_stream_t stream);
+
 /* Least-squares solve min ||A X - B||_F for m >= n with the factorization d
  * of A: B <- Q^T B, then R X = (Q^T B)(0:n-1, :) by tiled back substitution.
  *   B, ldb    device m x nrhs, in place; on return X is in B(0:n-1, :)
@@ -322,11 +336,13 @@ int tileqr_trace_count(const tileqr_desc *d, tileqr_stream_t stream, uint64_t *c
  * persistent kernel executes (Sec. 4's dependency-driven schedule) for an
  * m x n matrix, tile size nb and domain size `domain` (0: flat).
  *   what      0 = the factorization; 1 = Q^T applied to one column chunk
- *             of right-hand sides (tileqr_apply_qt / tileqr_solve_ls)
+ *             of right-hand sides (tileqr_apply_qt / tileqr_solve_ls);
+ *             2 = Q applied to one chunk (tileqr_apply_q / tileqr_form_q)
  *   tasks     ntasks rows {kind, i, j, k}: kind 0 DGEQRT, 1 DTSQRT, 2 DLARFB,
  *             3 DSSRFB, 4 DTTQRT, 5 DTTMQR; j = -1 for what = 1
  *   ndeps     per task, the number of predecessors that release it
  *   succ_ptr  ntasks + 1 offsets into succ (CSR); succ: successor indices
+ *             (kinds for what >= 1: 2 DLARFB, 3 DSSRFB, 5 DTTMQR)
  * Call with tasks == NULL to get *ntasks and *nedges, then again with
  * buffers of that size (4*ntasks, ntasks, ntasks+1, nedges entries).
  * Returns 0 or -i (-99: a successor outside the graph, an internal error). */

@@ -24,6 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tileqr_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "cholesky_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 TASK_GEQRT, TASK_TSQRT, TASK_LARFB, TASK_SSRFB = 0, 1, 2, 3
@@ -32,11 +33,11 @@ TASK_GEQRT, TASK_TSQRT, TASK_LARFB, TASK_SSRFB = 0, 1, 2, 3
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain -O2, no FMA contraction, no -march)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(x) for x in _SRCS)):
         return _LIB
     tmp = _LIB + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp, _SRC, "-lm"]
+           "-shared", "-o", tmp] + _SRCS + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -63,6 +64,12 @@ def _load():
         lib.oracle_apply_qt_tree.argtypes = [i64, i64, dp, i64, i32, i32, i32, dp, i64, dp, i64, i64, dp,
                                              i64]
         lib.oracle_apply_q_tree.argtypes = [i64, i64, dp, i64, i32, i32, i32, dp, i64, dp, i64, i64, dp, i64]
+        lib.oracle_tiled_cholesky.argtypes = [i64, dp, i64, i32]
+        lib.oracle_tiled_cholesky_ordered.argtypes = [i64, dp, i64, i32, i64, ctypes.POINTER(ctypes.c_int32)]
+        lib.oracle_tiled_cholesky.restype = ctypes.c_int
+        lib.oracle_tiled_cholesky_ordered.restype = ctypes.c_int
+        lib.chol_set_mutation.argtypes = [i32]
+        lib.chol_flops.restype = ctypes.c_double
         lib.oracle_flops.restype = ctypes.c_double
         lib.oracle_set_mutation.argtypes = [i32]
         for f in (lib.oracle_tiled_qr, lib.oracle_tiled_qr_ordered, lib.oracle_apply_qt,
@@ -407,12 +414,15 @@ def apply_task_list_tree(m: int, n: int, nb: int, h: int):
     return out
 
 
-def apply_dependencies_tree(m: int, n: int, nb: int, h: int):
-    """Predecessor sets of the Q^T application on one block column, from the
-    row blocks of B each task reads and writes."""
+def apply_dependencies_tree(m: int, n: int, nb: int, h: int, reverse: bool = False):
+    """Predecessor sets of the Q^T application on one block column (reverse:
+    of the Q application, which runs the same tasks in reverse order), from
+    the row blocks of B each task reads and writes."""
     p, _, _, _ = geometry(m, n, nb)
     H = _domain(p, h)
     tasks = apply_task_list_tree(m, n, nb, h)
+    if reverse:
+        tasks = tasks[::-1]
 
     def access(t):
         kind, i, k = t
@@ -523,6 +533,99 @@ def lapack_opcount(m: int, n: int) -> float:
 def tiled_flop_model(m: int, n: int, nb: int, ib: int) -> float:
     """Sec. 3.2.3: 2 n^2 (m - n/3) (1 + s/(4b)) for the DSSRFB-dominated cost."""
     return lapack_opcount(m, n) * (1.0 + ib / (4.0 * nb))
+
+
+# ---------------------------------------------------------------------------
+# Tiled Cholesky (Sec. 3.1, Algorithm 1): DPOTF2, DTRSM, DGSMM.
+TASK_POTF2, TASK_TRSM, TASK_GSMM = 0, 1, 2
+
+
+def tiled_cholesky(A, nb: int):
+    """(L, info): Algorithm 1 on a copy of the SPD matrix A; L is the lower
+    Cholesky factor (strict upper part zero).  info = 0, or the 1-based
+    global column of the first non-positive pivot (L then partial)."""
+    lib = _load()
+    A = _fortran(A)
+    n = A.shape[0]
+    info = lib.oracle_tiled_cholesky(n, _dp(A), max(n, 1), nb)
+    if info < 0:
+        raise ValueError(f"oracle_tiled_cholesky: illegal argument {info}")
+    return np.tril(A), info
+
+
+def tiled_cholesky_ordered(A, nb: int, tasks):
+    lib = _load()
+    A = _fortran(A)
+    n = A.shape[0]
+    tk = np.ascontiguousarray(np.asarray(tasks, dtype=np.int32).reshape(-1, 4))
+    info = lib.oracle_tiled_cholesky_ordered(n, _dp(A), max(n, 1), nb, tk.shape[0],
+                                             tk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if info < 0:
+        raise ValueError(f"oracle_tiled_cholesky_ordered: illegal argument {info}")
+    return np.tril(A), info
+
+
+def cholesky_flops() -> float:
+    return _load().chol_flops()
+
+
+def cholesky_reset_flops() -> None:
+    _load().chol_reset_flops()
+
+
+def cholesky_set_mutation(code: int) -> None:
+    _load().chol_set_mutation(int(code))
+
+
+def cholesky_task_list(n: int, nb: int):
+    """Tasks {kind, i, j, k} of Algorithm 1 in its printed loop order."""
+    p = -(-n // nb)
+    out = []
+    for k in range(p):
+        out.append((TASK_POTF2, k, k, k))
+        for i in range(k + 1, p):
+            out.append((TASK_TRSM, i, k, k))
+        for i in range(k + 1, p):
+            for j in range(k + 1, i + 1):
+                out.append((TASK_GSMM, i, j, k))
+    return out
+
+
+def cholesky_dependencies(n: int, nb: int):
+    """Predecessor sets of Algorithm 1 from the tiles each kernel reads and
+    writes (Sec. 3.1): DPOTF2 rewrites A_kk, DTRSM reads L_kk and rewrites
+    A_ik, DGSMM reads L_ik and L_jk and rewrites A_ij."""
+
+    def access(t):
+        kind, i, j, k = t
+        if kind == TASK_POTF2:
+            return set(), {("A", k, k)}
+        if kind == TASK_TRSM:
+            return {("A", k, k)}, {("A", i, k)}
+        return {("A", i, k), ("A", j, k)}, {("A", i, j)}
+
+    tasks = cholesky_task_list(n, nb)
+    return tasks, _mechanical_deps(tasks, access)
+
+
+def cholesky_random_order(n: int, nb: int, rng: np.random.Generator):
+    tasks, preds = cholesky_dependencies(n, nb)
+    succ = {t: [] for t in tasks}
+    indeg = {t: len(preds[t]) for t in tasks}
+    for t, ps in preds.items():
+        for x in ps:
+            succ[x].append(t)
+    ready = [t for t in tasks if indeg[t] == 0]
+    order = []
+    while ready:
+        t = ready.pop(int(rng.integers(len(ready))))
+        order.append(t)
+        for x in succ[t]:
+            indeg[x] -= 1
+            if indeg[x] == 0:
+                ready.append(x)
+    assert len(order) == len(tasks)
+    return order
 
 
 if __name__ == "__main__":

@@ -307,7 +307,8 @@ extern "C" int tileqr_apply_workspace_size(const tileqr_desc *d, int64_t nrhs, s
 
 // Q^T applied to Bt (tile-row layout) inside the apply workspace.
 static int apply_core(const tileqr_desc *d, const WsLayout &L, double *B, int64_t ldb, int64_t nrhs,
-                      char *aws, cudaStream_t st, double **Bt_out, int64_t *ncp_out, int **flag_out)
+                      char *aws, cudaStream_t st, double **Bt_out, int64_t *ncp_out, int **flag_out,
+                      bool notrans = false)
 {
     const int64_t ncp = apply_ncp(nrhs);
     double *Bt = (double *)aws;
@@ -318,15 +319,15 @@ static int apply_core(const tileqr_desc *d, const WsLayout &L, double *B, int64_
     int rc = launch_cm2rows(B, ldb, d->m, nrhs, Bt, d->nb, d->p, ncp, st);
     if (rc)
         return rc;
-    rc = launch_apply(L, d->tiles, d->T, d->T2, Bt, ncp, sched, st, watchdog_ns_default());
+    rc = launch_apply(L, d->tiles, d->T, d->T2, Bt, ncp, sched, st, watchdog_ns_default(), notrans);
     *Bt_out = Bt;
     *ncp_out = ncp;
     *flag_out = flag;
     return rc;
 }
 
-extern "C" int tileqr_apply_qt(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
-                               size_t ws_bytes, tileqr_stream_t stream)
+static int apply_impl(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
+                      size_t ws_bytes, tileqr_stream_t stream, bool notrans)
 {
     if (d == nullptr)
         return -1;
@@ -347,10 +348,45 @@ extern "C" int tileqr_apply_qt(const tileqr_desc *d, double *B, int64_t ldb, int
     double *Bt;
     int64_t ncp;
     int *flag;
-    int rc = apply_core(d, L, B, ldb, nrhs, (char *)workspace, st, &Bt, &ncp, &flag);
+    int rc = apply_core(d, L, B, ldb, nrhs, (char *)workspace, st, &Bt, &ncp, &flag, notrans);
     if (rc)
         return rc;
     return launch_rows2cm(Bt, d->nb, d->p, ncp, d->m, nrhs, B, ldb, st);
+}
+
+extern "C" int tileqr_apply_qt(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
+                               size_t ws_bytes, tileqr_stream_t stream)
+{
+    return apply_impl(d, B, ldb, nrhs, workspace, ws_bytes, stream, false);
+}
+
+extern "C" int tileqr_apply_q(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
+                              size_t ws_bytes, tileqr_stream_t stream)
+{
+    return apply_impl(d, B, ldb, nrhs, workspace, ws_bytes, stream, true);
+}
+
+extern "C" int tileqr_form_q(const tileqr_desc *d, double *Q, int64_t ldq, int64_t ncols, void *workspace,
+                             size_t ws_bytes, tileqr_stream_t stream)
+{
+    if (d == nullptr)
+        return -1;
+    if (Q == nullptr && ncols > 0 && d->m > 0)
+        return -2;
+    if (ldq < (d->m > 1 ? d->m : 1))
+        return -3;
+    if (ncols < 0 || ncols > d->m)
+        return -4;
+    size_t need = 0;
+    tileqr_apply_workspace_size(d, ncols, &need);
+    if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < need)
+        return TILEQR_ERR_WORKSPACE;
+    int rc = launch_eye(Q, ldq, d->m, ncols, (cudaStream_t)stream);
+    if (rc)
+        return rc;
+    if (d->n == 0)
+        return 0;
+    return apply_impl(d, Q, ldq, ncols, workspace, ws_bytes, stream, true);
 }
 
 extern "C" int tileqr_solve_ls(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace,
@@ -468,7 +504,7 @@ extern "C" int tileqr_task_graph(int64_t m, int64_t n, int nb, int domain, int w
         return -3;
     if (domain < 0)
         return -4;
-    if (what != 0 && what != 1)
+    if (what < 0 || what > 2)
         return -5;
     if (ntasks == nullptr)
         return -10;
@@ -485,7 +521,7 @@ extern "C" int tileqr_task_graph(int64_t m, int64_t n, int nb, int domain, int w
             for (int tt = 0; tt < 2; tt++) {
                 if (tt == 1 && !(head && i > k))
                     continue;
-                if (what == 1) {
+                if (what >= 1) {
                     index[g_cidx(G, tt, k, i, 0)] = (int64_t)list.size();
                     list.push_back(GTask{tt, k, i, -1});
                 } else {
@@ -502,9 +538,9 @@ extern "C" int tileqr_task_graph(int64_t m, int64_t n, int nb, int domain, int w
         const GTask a = list[t];
         GTask sp[2];
         std::vector<GTask> ss;
-        if (what == 1) {
+        if (what >= 1) {
             const int kind = ga_kind(G, a.tt, a.k, a.i);
-            const int ns = ga_specific(G, kind, a.k, a.i, sp);
+            const int ns = what == 1 ? ga_specific(G, kind, a.k, a.i, sp) : ga_predecessors(G, kind, a.k, a.i, sp);
             for (int s2 = 0; s2 < ns; s2++)
                 ss.push_back(GTask{sp[s2].tt, sp[s2].k, sp[s2].i, 0});
         } else {
@@ -537,12 +573,14 @@ extern "C" int tileqr_task_graph(int64_t m, int64_t n, int nb, int domain, int w
     int64_t pos = 0;
     for (size_t t = 0; t < list.size(); t++) {
         const GTask a = list[t];
-        const int kind = what == 1 ? ga_kind(G, a.tt, a.k, a.i) : g_kind(G, a.tt, a.k, a.i, a.j);
+        const int kind = what >= 1 ? ga_kind(G, a.tt, a.k, a.i) : g_kind(G, a.tt, a.k, a.i, a.j);
         tasks[4 * t + 0] = kind;
         tasks[4 * t + 1] = a.i;
         tasks[4 * t + 2] = a.j;
         tasks[4 * t + 3] = a.k;
-        ndeps[t] = what == 1 ? ga_ndeps(kind, a.k) : g_ndeps(kind, a.k);
+        GTask tmp[2];
+        ndeps[t] = what == 1 ? ga_ndeps(kind, a.k)
+                             : (what == 2 ? ga_specific(G, kind, a.k, a.i, tmp) : g_ndeps(kind, a.k));
         succ_ptr[t] = pos;
         for (int64_t v : out[t])
             succ[pos++] = v;

@@ -8,7 +8,9 @@
 // form).  In Algorithm 2's flat form: LB(k) <- SB(k,k-1); SB(i,k) <- (LB(k)
 // if i = k+1 else SB(i-1,k)) and SB(i,k-1).  They run in one persistent
 // kernel with the same counter / ready-queue scheduler, so consecutive
-// steps k overlap as a wavefront.
+// steps k overlap as a wavefront.  Q B (NOTRANS) runs the same tasks in the
+// reverse graph (graph.cuh: ga_predecessors), each with its inner blocks
+// reversed and T_l in place of T_l^T.
 #include "factor.h"
 #include "graph.cuh"
 #include "sched.cuh"
@@ -37,16 +39,32 @@ __device__ __forceinline__ size_t apply_cnt_idx(const ApplyArgs &A, int tt, int 
     return (((size_t)tt * A.steps + k) * A.p + i) * A.nchunk + cb;
 }
 
-template <int NB, int S>
+template <int NB, int S, bool NOTRANS>
 __global__ void __launch_bounds__(NT, 1) k_apply_dag(ApplyArgs A, Queues Q)
 {
     extern __shared__ double sm[];
     __shared__ unsigned long long s_code;
     __shared__ int s_cmd;
     const TGraph &G = A.G;
-    if (blockIdx.x == 0)   // step 0's DLARFBs (one per domain head and chunk) have no predecessors
-        for (int u = threadIdx.x; u < A.nchunk * g_ndom(G, 0); u += NT)
-            q_push(Q, 0, encode_task(0, g_head(G, 0, u / A.nchunk), u % A.nchunk));
+    if (blockIdx.x == 0) {
+        if (!NOTRANS) {
+            // step 0's DLARFBs (one per domain head and chunk) have no predecessors
+            for (int u = threadIdx.x; u < A.nchunk * g_ndom(G, 0); u += NT)
+                q_push(Q, 0, encode_task(0, g_head(G, 0, u / A.nchunk), u % A.nchunk));
+        } else {
+            // the reverse graph starts from the forward graph's sinks
+            for (int u = threadIdx.x; u < 2 * A.steps * A.p; u += NT) {
+                const int tt = u & 1, k = (u >> 1) / A.p, i = (u >> 1) % A.p;
+                if (i < k || (tt == 1 && (((i - k) % G.H) != 0 || i == k)))
+                    continue;
+                GTask sp[2];
+                const int kind = ga_kind(G, tt, k, i);
+                if (ga_specific(G, kind, k, i, sp) == 0)
+                    for (int cb = 0; cb < A.nchunk; cb++)
+                        q_push(Q, kind == K_LARFB ? 0 : 1, encode_task(k, i, cb, tt));
+            }
+        }
+    }
     for (;;) {
         if (threadIdx.x == 0)
             s_cmd = q_acquire(Q, s_code);
@@ -59,21 +77,24 @@ __global__ void __launch_bounds__(NT, 1) k_apply_dag(ApplyArgs A, Queues Q)
         const double *Vt = A.tiles + ((size_t)k * A.p + i) * (size_t)NB * NB;
         const size_t strip = ((size_t)k * A.p + i) * (size_t)S * NB;
         if (kind == K_LARFB)
-            task_larfb<NB, S, APPLY_W>(sm, chunk_ptr<NB, S>(A, i, cb), Vt, A.T + strip, APPLY_W);
+            task_larfb<NB, S, APPLY_W, NOTRANS>(sm, chunk_ptr<NB, S>(A, i, cb), Vt, A.T + strip, APPLY_W);
         else if (kind == K_SSRFB)
-            task_ssrfb<NB, S, APPLY_W>(sm, chunk_ptr<NB, S>(A, g_head(G, k, g_dom(G, k, i)), cb),
-                                       chunk_ptr<NB, S>(A, i, cb), Vt, A.T + strip, APPLY_W);
+            task_ssrfb<NB, S, APPLY_W, false, NOTRANS>(sm, chunk_ptr<NB, S>(A, g_head(G, k, g_dom(G, k, i)), cb),
+                                                       chunk_ptr<NB, S>(A, i, cb), Vt, A.T + strip, APPLY_W);
         else
-            task_ssrfb<NB, S, APPLY_W, true>(sm, chunk_ptr<NB, S>(A, g_partner(G, k, i), cb),
-                                             chunk_ptr<NB, S>(A, i, cb), Vt, A.T2 + strip, APPLY_W);
+            task_ssrfb<NB, S, APPLY_W, true, NOTRANS>(sm, chunk_ptr<NB, S>(A, g_partner(G, k, i), cb),
+                                                      chunk_ptr<NB, S>(A, i, cb), Vt, A.T2 + strip, APPLY_W);
         __syncthreads();
         if (threadIdx.x == 0) {
-            GTask sp[2];
-            const int ns = ga_specific(G, kind, k, i, sp);
+            // successors: forward ones for Q^T; forward predecessors for Q, each
+            // released by its own forward successors
+            GTask sp[2], tmp[2];
+            const int ns = NOTRANS ? ga_predecessors(G, kind, k, i, sp) : ga_specific(G, kind, k, i, sp);
             for (int s = 0; s < ns; s++) {
                 const int tk = ga_kind(G, sp[s].tt, sp[s].k, sp[s].i);
-                q_signal(Q, apply_cnt_idx(A, sp[s].tt, sp[s].k, sp[s].i, cb), ga_ndeps(tk, sp[s].k),
-                         tk == K_LARFB ? 0 : 1, encode_task(sp[s].k, sp[s].i, cb, sp[s].tt));
+                const int nd = NOTRANS ? ga_specific(G, tk, sp[s].k, sp[s].i, tmp) : ga_ndeps(tk, sp[s].k);
+                q_signal(Q, apply_cnt_idx(A, sp[s].tt, sp[s].k, sp[s].i, cb), nd, tk == K_LARFB ? 0 : 1,
+                         encode_task(sp[s].k, sp[s].i, cb, sp[s].tt));
             }
             __threadfence();
             atomicAdd(&Q.ctrl->completed, 1u);
@@ -107,18 +128,18 @@ size_t apply_sched_bytes(const WsLayout &L, int nchunk)
     return 256 + a.cnt_bytes + a.q0_bytes + a.q1_bytes;
 }
 
-template <int NB, int S>
+template <int NB, int S, bool NOTRANS>
 static int launch_apply_t(const WsLayout &L, const double *tiles, const double *T, const double *T2, double *Bt,
                           int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns)
 {
     constexpr size_t smem = F64Cfg<NB, S, APPLY_W>::SMEM;
     static int grid_max = 0;
     if (grid_max == 0) {
-        cudaFuncSetAttribute(k_apply_dag<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_apply_dag<NB, S, NOTRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int dev = 0, nsm = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_dag<NB, S>, NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_dag<NB, S, NOTRANS>, NT, smem);
         if (per_sm < 1)
             return TILEQR_ERR_CUDA;
         grid_max = nsm * per_sm;
@@ -156,17 +177,18 @@ static int launch_apply_t(const WsLayout &L, const double *tiles, const double *
     int grid = grid_max;
     if ((unsigned)grid > Q.total)
         grid = (int)Q.total;
-    k_apply_dag<NB, S><<<grid, NT, smem, st>>>(A, Q);
+    k_apply_dag<NB, S, NOTRANS><<<grid, NT, smem, st>>>(A, Q);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
 }
 
 int launch_apply(const WsLayout &L, const double *tiles, const double *T, const double *T2, double *Bt,
-                 int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns)
+                 int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns, bool notrans)
 {
 #define TQR_CASE(NB_, S_)                                                                        \
     if (L.nb == NB_ && L.ib == S_)                                                               \
-        return launch_apply_t<NB_, S_>(L, tiles, T, T2, Bt, ncp, sched, st, watchdog_ns);
+        return notrans ? launch_apply_t<NB_, S_, true>(L, tiles, T, T2, Bt, ncp, sched, st, watchdog_ns)       \
+                       : launch_apply_t<NB_, S_, false>(L, tiles, T, T2, Bt, ncp, sched, st, watchdog_ns);
     TQR_CASE(64, 16)
     TQR_CASE(64, 32)
     TQR_CASE(128, 16)

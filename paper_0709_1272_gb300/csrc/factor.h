@@ -36,8 +36,11 @@ int launch_rows2cm(const double *Bt, int nb, int p, int64_t ncp, int64_t m, int6
 // Q^T applied to the tile-row right-hand sides, as a task graph.
 constexpr int APPLY_W = 32;
 size_t apply_sched_bytes(const WsLayout &L, int nchunk);
+// notrans: Q B instead of Q^T B.
 int launch_apply(const WsLayout &L, const double *tiles, const double *T, const double *T2, double *Bt,
-                 int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns);
+                 int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns, bool notrans = false);
+// B (m x ncols, column-major) <- the leading ncols columns of the m x m identity.
+int launch_eye(double *B, int64_t ldb, int64_t m, int64_t ncols, cudaStream_t st);
 // Back substitution R X = Y on the first q row blocks of Bt; sets *flag to
 // j+1 (device int) for an exact zero R(j,j).
 int launch_trsm(const WsLayout &L, const double *tiles, double *Bt, int64_t ncp, int *flag, cudaStream_t st);

@@ -240,6 +240,43 @@ __host__ __device__ inline int ga_specific(const TGraph &G, int kind, int k, int
         out[s] = t[s];
     return n;
 }
+// Q itself (tileqr_apply_q) runs the same tasks in the reverse graph: a task
+// is released by its forward successors (count: ga_specific) and on
+// completion signals its forward predecessors, listed here:
+//   LB(h,k)  <- last writer of row h at step k-1 (k > 0)
+//   SB(r,k)  <- LB(head) or SB(r-1,k) (the domain chain); last writer of row r at k-1
+//   TB(e,k)  <- last writer of head e's row before its merge (the level L(e)-1
+//               merge into e, else e's chain end); the same for the partner d
+//               before the level-l merge (level l-1 merge into d, else d's end)
+// The last writer of row r at step k' is SB(r,k') if r is not a domain head
+// there, else TB(r,k') (r > k').
+__host__ __device__ inline GTask ga_last_writer(const TGraph &G, int k, int r)
+{
+    return ((r - k) % G.H) == 0 ? GTask{1, k, r, 0} : GTask{0, k, r, 0};
+}
+__host__ __device__ inline GTask ga_chain_end(const TGraph &G, int k, int d)
+{
+    return GTask{0, k, g_last(G, k, d), 0};   // SB(last) or, for a one-row domain, LB(head)
+}
+__host__ __device__ inline int ga_predecessors(const TGraph &G, int kind, int k, int i, GTask out[2])
+{
+    int n = 0;
+    if (kind == K_LARFB) {
+        if (k > 0)
+            out[n++] = ga_last_writer(G, k - 1, i);
+    } else if (kind == K_SSRFB) {
+        out[n++] = GTask{0, k, i - 1, 0};
+        if (k > 0)
+            out[n++] = ga_last_writer(G, k - 1, i);
+    } else {
+        const int e = g_dom(G, k, i), lev = g_ctz(e), d = e - (1 << lev);
+        const int le = g_nmerge(G, k, e);
+        out[n++] = le > 0 ? GTask{1, k, g_head(G, k, e + (1 << (le - 1))), 0} : ga_chain_end(G, k, e);
+        out[n++] = lev > 0 ? GTask{1, k, g_head(G, k, d + (1 << (lev - 1))), 0} : ga_chain_end(G, k, d);
+    }
+    return n;
+}
+
 __host__ inline void ga_count(const TGraph &G, unsigned long long cnt[2])
 {
     cnt[0] = cnt[1] = 0;   // [0]: LB, [1]: SB + TB

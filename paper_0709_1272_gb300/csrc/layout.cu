@@ -189,4 +189,24 @@ int launch_rows2cm(const double *Bt, int nb, int p, int64_t ncp, int64_t m, int6
     return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
 }
 
+// B (m x ncols, ld ldb) <- the leading ncols columns of the identity; one
+// warp per column, grid-stride.
+__global__ void __launch_bounds__(256) k_eye(double *B, int64_t ldb, int64_t m, int64_t ncols)
+{
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    const int lane = threadIdx.x & 31;
+    for (int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); c < ncols; c += warps)
+        for (int64_t r = lane; r < m; r += 32)
+            B[c * ldb + r] = (r == c) ? 1.0 : 0.0;
+}
+
+int launch_eye(double *B, int64_t ldb, int64_t m, int64_t ncols, cudaStream_t st)
+{
+    if (m == 0 || ncols == 0)
+        return 0;
+    k_eye<<<grid_for((size_t)ncols), 256, 0, st>>>(B, ldb, m, ncols);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
+}
+
 }  // namespace tqr

@@ -61,8 +61,8 @@ struct F64Cfg {
 // top tile, DSSRFB / DTSQRT) is read and written in global memory at
 // Bg[c * NB + a]; Bg == nullptr for DLARFB (the unit block of V_l lies inside
 // C).  Only columns c < nc are meaningful; columns beyond stay untouched in
-// global memory.
-template <int NB, int S, int W_>
+// global memory.  NOTRANS: W = T_l Y instead of T_l^T Y (applying Q itself).
+template <int NB, int S, int W_, bool NOTRANS = false>
 __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int nc, int r1 = NB)
 {
     using C_ = F64Cfg<NB, S, W_>;
@@ -117,7 +117,8 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
         }
     __syncthreads();
 
-    // Phase B: W = T^T Y (T upper triangular: W(a) = sum_{b<=a} T(b,a) Y(b))
+    // Phase B: W = T^T Y (T upper triangular: W(a) = sum_{b<=a} T(b,a) Y(b)),
+    // or W = T Y (W(a) = sum_{b>=a} T(a,b) Y(b)) for NOTRANS
     double w[AW][CU];
 #pragma unroll
     for (int ai = 0; ai < AW; ai++) {
@@ -125,8 +126,9 @@ __device__ __forceinline__ void apply_block(double *sm, double *Bg, int r0, int 
 #pragma unroll
         for (int u = 0; u < CU; u++)
             w[ai][u] = 0.0;
-        for (int bb = 0; bb <= a; bb++) {
-            const double t = Ts[bb + a * S];
+        const int blo = NOTRANS ? a : 0, bhi = NOTRANS ? S - 1 : a;
+        for (int bb = blo; bb <= bhi; bb++) {
+            const double t = NOTRANS ? Ts[a + bb * S] : Ts[bb + a * S];
 #pragma unroll
             for (int u = 0; u < CU; u++)
                 if (32 * u < nc)
@@ -255,7 +257,8 @@ __device__ __forceinline__ void stage_t(double *sm, const double *Tt, int l0)
 // passes NB, the Q^T application the width of its column chunk.
 // TRI (DTTMQR of the tree form): the reflectors are the upper triangle of
 // Vt, so block l reaches only rows < l0 + S of Ct.
-template <int NB, int S, int W_ = FactorW<NB>::value, bool TRI = false>
+// NOTRANS: apply Q itself (the inner blocks in reverse order, each with T_l).
+template <int NB, int S, int W_ = FactorW<NB>::value, bool TRI = false, bool NOTRANS = false>
 __device__ __noinline__ void task_ssrfb(double *sm, double *Bt, double *Ct, const double *Vt, const double *Tt,
                            int ncols = NB)
 {
@@ -263,14 +266,15 @@ __device__ __noinline__ void task_ssrfb(double *sm, double *Bt, double *Ct, cons
     for (int c0 = 0; c0 < ncols; c0 += C_::W) {
         const int nc = min(C_::W, ncols - c0);
         stage_chunk<NB, S, W_>(sm, Ct, c0, nc);
-        for (int l0 = 0; l0 < NB; l0 += S) {
+        for (int lb = 0; lb < NB; lb += S) {
+            const int l0 = NOTRANS ? NB - S - lb : lb;
             if constexpr (TRI)
                 stage_v_upper<NB, S, W_>(sm, Vt, l0);
             else
                 stage_v_full<NB, S, W_>(sm, Vt, l0);
             stage_t<NB, S, W_>(sm, Tt, l0);
             __syncthreads();
-            apply_block<NB, S, W_>(sm, Bt + (size_t)c0 * NB + l0, 0, nc, TRI ? l0 + S : NB);
+            apply_block<NB, S, W_, NOTRANS>(sm, Bt + (size_t)c0 * NB + l0, 0, nc, TRI ? l0 + S : NB);
         }
         store_chunk<NB, S, W_>(sm, Ct, c0, nc, 0);
         __syncthreads();
@@ -279,7 +283,7 @@ __device__ __noinline__ void task_ssrfb(double *sm, double *Bt, double *Ct, cons
 
 // DLARFB (Sec. 3.2.1): Ct <- Q^T Ct with the DGEQRT reflectors of the
 // diagonal tile Vt (unit lower) and its T strip.
-template <int NB, int S, int W_ = FactorW<NB>::value>
+template <int NB, int S, int W_ = FactorW<NB>::value, bool NOTRANS = false>
 __device__ __noinline__ void task_larfb(double *sm, double *Ct, const double *Vt, const double *Tt,
                            int ncols = NB)
 {
@@ -287,11 +291,12 @@ __device__ __noinline__ void task_larfb(double *sm, double *Ct, const double *Vt
     for (int c0 = 0; c0 < ncols; c0 += C_::W) {
         const int nc = min(C_::W, ncols - c0);
         stage_chunk<NB, S, W_>(sm, Ct, c0, nc);
-        for (int l0 = 0; l0 < NB; l0 += S) {
+        for (int lb = 0; lb < NB; lb += S) {
+            const int l0 = NOTRANS ? NB - S - lb : lb;
             stage_v_unit<NB, S, W_>(sm, Vt, l0);
             stage_t<NB, S, W_>(sm, Tt, l0);
             __syncthreads();
-            apply_block<NB, S, W_>(sm, nullptr, l0, nc);
+            apply_block<NB, S, W_, NOTRANS>(sm, nullptr, l0, nc);
         }
         store_chunk<NB, S, W_>(sm, Ct, c0, nc, 0);
         __syncthreads();

@@ -53,6 +53,17 @@ def kappa_matrix(n: int, kappa: float, seed: int):
     return A, s, u, v
 
 
+def spd_matrix(n: int, seed: int) -> np.ndarray:
+    """Symmetric positive definite n x n: (G + G^T)/2 + n I with G uniform[-1,1)
+    (column-major).  Each row's off-diagonal absolute sum is about n/2 < n, so
+    the matrix is strictly diagonally dominant with a positive diagonal
+    (Gershgorin: SPD, condition number at most about 3)."""
+    G = _rng(seed).uniform(-1.0, 1.0, size=(n, n))
+    A = 0.5 * (G + G.T)
+    A[np.arange(n), np.arange(n)] += n
+    return np.asfortranarray(A)
+
+
 def batch_shapes(count: int, seed: int, m_lo: int = 64, m_hi: int = 2048, n_lo: int = 32):
     """Ragged batch: m uniform in [m_lo, m_hi], n uniform in [n_lo, m]."""
     g = _rng(seed)

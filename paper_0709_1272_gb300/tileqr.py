@@ -35,6 +35,7 @@ EXPORTED = [
     "tileqr_batched_workspace_size", "tileqr_batched_prepare", "tileqr_factor_batched",
     "tileqr_batched_status", "tileqr_batched_get",
     "tileqr_workspace_size_tree", "tileqr_factor_tree", "tileqr_get_tree_T", "tileqr_task_graph",
+    "tileqr_apply_q", "tileqr_form_q",
 ]
 
 
@@ -119,6 +120,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_workspace_size_tree": (i32, [i64, i64, i32, i32, i32, i32, ctypes.POINTER(sz)]),
         "tileqr_factor_tree": (i32, [i64, i64, vp, i64, i32, i32, i32, i32, i32, vp, sz, vp, dp]),
         "tileqr_get_tree_T": (i32, [dp, vp, i64, vp]),
+        "tileqr_apply_q": (i32, [dp, vp, i64, i64, vp, sz, vp]),
+        "tileqr_form_q": (i32, [dp, vp, i64, i64, vp, sz, vp]),
         "tileqr_task_graph": (i32, [i64, i64, i32, i32, i32, vp, vp, vp, vp, ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)]),
     }
@@ -311,6 +314,25 @@ class Factorization:
                                       B.shape[1], ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                       _stream_ptr(stream)), "tileqr_apply_qt")
         return B
+
+    def apply_q(self, B: torch.Tensor, stream=None) -> torch.Tensor:
+        """Q B in place (Q itself); returns B."""
+        B = as_colmajor(B)
+        ws = self._apply_workspace(B.shape[1])
+        _check(load().tileqr_apply_q(ctypes.byref(self.desc), ctypes.c_void_p(B.data_ptr()), _ld(B), B.shape[1],
+                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)),
+               "tileqr_apply_q")
+        return B
+
+    def form_q(self, ncols: int | None = None, stream=None) -> torch.Tensor:
+        """The leading ncols (default min(m, n)) columns of Q, m x ncols."""
+        k = min(self.m, self.n) if ncols is None else ncols
+        Q = colmajor_empty(self.m, k, self.device)
+        ws = self._apply_workspace(k)
+        _check(load().tileqr_form_q(ctypes.byref(self.desc), ctypes.c_void_p(Q.data_ptr()), max(self.m, 1), k,
+                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)),
+               "tileqr_form_q")
+        return Q
 
     def solve_refine(self, A: torch.Tensor, b: torch.Tensor, max_iter: int = 30, tol: float = 1e-12,
                      stream=None):

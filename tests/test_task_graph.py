@@ -108,6 +108,15 @@ def test_apply_graph(tq, m, n, nb, h):
     _compare(keys, ndeps, edges, otasks, opreds)
 
 
+@pytest.mark.parametrize("m,n,nb,h", CASES)
+def test_apply_q_graph(tq, m, n, nb, h):
+    # Q (not Q^T): the same tasks in the reverse graph
+    keys, ndeps, edges = _graph(tq, m, n, nb, h, 2)
+    keys = [(k[0], k[1], k[3]) for k in keys]
+    otasks, opreds = oracle.apply_dependencies_tree(m, n, nb, h, reverse=True)
+    _compare(keys, ndeps, edges, otasks, opreds)
+
+
 def test_task_counts_match_the_workspace_queues(tq):
     # the write-once ready queues are sized from closed-form counts; they must
     # equal the enumerated graph
