@@ -297,6 +297,38 @@ def run_tall(args, dev, rank, world, barrier, dist):
     return res
 
 
+def run_cholesky(args, dev, rank, world, barrier, dist):
+    """Tiled Cholesky (Sec. 3.1, Algorithm 1): n x n SPD, (G + G^T)/2 + n I
+    with G uniform[-1, 1), nb 128, FP64 task graph; rate with the n^3/3
+    operation count."""
+    import torch
+    from paper_0709_1272_gb300 import inputs, replicas, tileqr
+    n, nb = args.n, 128
+    A = tileqr.to_device_colmajor(inputs.spd_matrix(n, seed=20070709 + 7 + 1000 * rank), dev)
+    ws = torch.empty(tileqr.tileqr_cholesky_workspace_size(n, nb), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    tileqr.tileqr_cholesky(A, nb, workspace=ws).check()   # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(2, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        f = tileqr.tileqr_cholesky(A, nb, workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    f.check()
+    t = replicas.max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps, dist, dev)
+    ops = n ** 3 / 3.0
+    peaks = measured_peaks()
+    fp64_peak = NSM * FP64_FLOP_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
+    del A, ws
+    return {"workload": f"tiled Cholesky (Algorithm 1), {n}x{n} SPD (G+G^T)/2 + nI, G uniform[-1,1), nb={nb}, "
+                        f"FP64 task graph", "value": world * ops / t / 1e9, "unit": UNIT, "ms_per_step": t * 1e3,
+            "steps": reps, "pct_fp64_peak": 100.0 * (ops / t / 1e9) / fp64_peak,
+            "timing": "CUDA events around the factorizations (layout conversion included), max over ranks"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,6 +349,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched (4096 ragged matrices) measurement")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--no-cholesky", action="store_true",
+                    help="skip the tiled Cholesky (Algorithm 1) measurement")
     ap.add_argument("--no-tall", action="store_true",
                     help="skip the tall-skinny (262144 x 512, flat vs tree) measurement")
     ap.add_argument("--tall-m", type=int, default=262144)
@@ -477,6 +511,12 @@ def main():
         torch.cuda.empty_cache()
         batched = run_batched(args, dev, rank, world, barrier, dist)
 
+    # ---- tiled Cholesky (Algorithm 1) on an SPD matrix of the same order
+    chol = None
+    if not args.no_cholesky and m == n:
+        torch.cuda.empty_cache()
+        chol = run_cholesky(args, dev, rank, world, barrier, dist)
+
     # ---- tall-skinny 262144 x 512: flat tree vs tree form
     tall = None
     if not args.no_tall:
@@ -523,6 +563,8 @@ def main():
         out["batched"] = batched
     if tall:
         out["tall_skinny"] = tall
+    if chol:
+        out["cholesky"] = chol
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(nb, ib)
     print(json.dumps(out), flush=True)

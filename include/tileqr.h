@@ -67,7 +67,8 @@ enum {
     TILEQR_ERR_WORKSPACE = 1004, /* workspace too small or misaligned (256 B) */
     TILEQR_ERR_SINGULAR = 1005,  /* R has an exact zero on its diagonal (solve) */
     TILEQR_ERR_UNSUPPORTED = 1006, /* (nb, ib, precision) combination not built */
-    TILEQR_ERR_SCRATCH_LIMIT = 1007 /* problem too large for tileqr_factor_noalloc's fixed scratch */
+    TILEQR_ERR_SCRATCH_LIMIT = 1007, /* problem too large for tileqr_factor_noalloc's fixed scratch */
+    TILEQR_ERR_NOT_SPD = 1008       /* tileqr_cholesky: the matrix is not positive definite */
 };
 
 /* Factorization descriptor, filled in by tileqr_factor.  Plain data; the
@@ -308,6 +309,30 @@ int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_t lda, cons
                         int max_iter, double tol, void *workspace, size_t ws_bytes, tileqr_stream_t stream,
                         tileqr_refine_info *info);
 
+/* Tiled Cholesky factorization A = L L^T of a symmetric positive definite
+ * matrix (Sec. 3.1, Algorithm 1): the tasks DPOTF2 (Cholesky of a diagonal
+ * tile), DTRSM (L_ik = A_ik L_kk^{-T}) and DGSMM (A_ij -= L_ik L_jk^T, lower
+ * triangle only on diagonal tiles) run as a task graph in one persistent
+ * kernel (FP64).
+ *   n, A, lda  device, column-major; only the lower triangle is read
+ *   nb         tile size: 64 or 128 (others: TILEQR_ERR_UNSUPPORTED)
+ *   flags      reserved (0)
+ *   workspace  device, 256-byte aligned, >= tileqr_cholesky_workspace_size()
+ *   out        host descriptor (m = n; tiles hold L in the lower tiles)
+ * Asynchronous.  Returns 0, -i, TILEQR_ERR_WORKSPACE, TILEQR_ERR_UNSUPPORTED,
+ * TILEQR_ERR_CUDA.  tileqr_status() then reports 0, TILEQR_ERR_NOT_SPD (the
+ * factorization stopped at a pivot that was not positive; see
+ * tileqr_cholesky_info), TILEQR_ERR_NONFINITE or TILEQR_ERR_TIMEOUT. */
+int tileqr_cholesky_workspace_size(int64_t n, int nb, size_t *bytes);
+int tileqr_cholesky(int64_t n, const double *A, int64_t lda, int nb, int flags, void *workspace, size_t ws_bytes,
+                    tileqr_stream_t stream, tileqr_desc *out);
+/* L (n x n lower triangular, zeros above the diagonal) to the device array
+ * L (column-major, ldl >= max(1,n)).  Asynchronous. */
+int tileqr_cholesky_get_L(const tileqr_desc *d, double *L, int64_t ldl, tileqr_stream_t stream);
+/* *info = 0, or the 1-based column of the first pivot that was not positive
+ * (synchronises the stream). */
+int tileqr_cholesky_info(const tileqr_desc *d, tileqr_stream_t stream, int64_t *info);
+
 /* Human-readable text for a return code (static storage). */
 const char *tileqr_strerror(int code);
 
@@ -337,7 +362,9 @@ int tileqr_trace_count(const tileqr_desc *d, tileqr_stream_t stream, uint64_t *c
  * m x n matrix, tile size nb and domain size `domain` (0: flat).
  *   what      0 = the factorization; 1 = Q^T applied to one column chunk
  *             of right-hand sides (tileqr_apply_qt / tileqr_solve_ls);
- *             2 = Q applied to one chunk (tileqr_apply_q / tileqr_form_q)
+ *             2 = Q applied to one chunk (tileqr_apply_q / tileqr_form_q);
+ *             3 = the tiled Cholesky of an m x m matrix (tileqr_cholesky;
+ *             n and domain ignored; kinds 0 DPOTF2, 1 DTRSM, 2 DGSMM)
  *   tasks     ntasks rows {kind, i, j, k}: kind 0 DGEQRT, 1 DTSQRT, 2 DLARFB,
  *             3 DSSRFB, 4 DTTQRT, 5 DTTMQR; j = -1 for what = 1
  *   ndeps     per task, the number of predecessors that release it

@@ -17,6 +17,11 @@ static cudaEvent_t g_ev_before = nullptr, g_ev_after = nullptr;
 static unsigned long long *g_trace = nullptr;
 static unsigned long long g_trace_cap = 0;
 void count_launch(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void trace_target(unsigned long long **records, unsigned int *capacity)
+{
+    *records = g_trace;
+    *capacity = (unsigned int)(g_trace_cap > 0xffffffffull ? 0xffffffffull : g_trace_cap);
+}
 
 static unsigned long long watchdog_ns_default()
 {
@@ -452,6 +457,7 @@ extern "C" const char *tileqr_strerror(int code)
     case TILEQR_ERR_SINGULAR: return "R has an exact zero on its diagonal";
     case TILEQR_ERR_UNSUPPORTED: return "unsupported (nb, ib, precision)";
     case TILEQR_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed scratch of tileqr_factor_noalloc";
+    case TILEQR_ERR_NOT_SPD: return "matrix is not positive definite";
     default: return "unknown error";
     }
 }
@@ -504,12 +510,63 @@ extern "C" int tileqr_task_graph(int64_t m, int64_t n, int nb, int domain, int w
         return -3;
     if (domain < 0)
         return -4;
-    if (what < 0 || what > 2)
+    if (what < 0 || what > 3)
         return -5;
     if (ntasks == nullptr)
         return -10;
     if (nedges == nullptr)
         return -11;
+    if (what == 3) {
+        // tiled Cholesky graph of an m x m matrix
+        const int p = (int)((m + nb - 1) / nb);
+        std::vector<GTask> list;
+        std::map<size_t, int64_t> index;
+        // every (k, i, j) with k <= j <= i is one task
+        for (int k = 0; k < p; k++)
+            for (int i = k; i < p; i++)
+                for (int j = k; j <= i; j++) {
+                    index[cg_cidx(p, k, i, j)] = (int64_t)list.size();
+                    list.push_back(GTask{0, k, i, j});
+                }
+        std::vector<std::vector<int64_t>> out(list.size());
+        int64_t ne = 0;
+        for (size_t t = 0; t < list.size(); t++) {
+            const GTask a = list[t];
+            const int ns = cg_nsucc(p, a.k, a.i, a.j);
+            for (int s2 = 0; s2 < ns; s2++) {
+                const GTask b = cg_succ(p, a.k, a.i, a.j, s2);
+                auto it = index.find(cg_cidx(p, b.k, b.i, b.j));
+                if (it == index.end())
+                    return -99;
+                out[t].push_back(it->second);
+                ne++;
+            }
+        }
+        *ntasks = (int64_t)list.size();
+        *nedges = ne;
+        if (tasks == nullptr)
+            return 0;
+        if (ndeps == nullptr)
+            return -7;
+        if (succ_ptr == nullptr)
+            return -8;
+        if (succ == nullptr && ne > 0)
+            return -9;
+        int64_t pos = 0;
+        for (size_t t = 0; t < list.size(); t++) {
+            const GTask a = list[t];
+            tasks[4 * t + 0] = cg_kind(a.k, a.i, a.j);
+            tasks[4 * t + 1] = a.i;
+            tasks[4 * t + 2] = a.j;
+            tasks[4 * t + 3] = a.k;
+            ndeps[t] = cg_ndeps(a.k, a.i, a.j);
+            succ_ptr[t] = pos;
+            for (int64_t v : out[t])
+                succ[pos++] = v;
+        }
+        succ_ptr[list.size()] = pos;
+        return 0;
+    }
     const int p = (int)((m + nb - 1) / nb), q = (int)((n + nb - 1) / nb);
     const TGraph G = make_graph(p, q, domain);
     // tasks in (tt, k, i, j) order; the key is the counter index

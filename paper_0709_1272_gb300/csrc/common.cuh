@@ -58,7 +58,8 @@ struct SchedCtrl {
     int error;                    // TILEQR_ERR_* or 0
     int nonfinite;                // set by the layout kernel
     unsigned int trace_cursor;    // next free trace record
-    unsigned long long pad[11];
+    unsigned long long info;      // Cholesky: first non-positive pivot column + 1
+    unsigned long long pad[10];
 };
 static_assert(sizeof(SchedCtrl) <= 256, "control block must fit its 256-byte slot");
 

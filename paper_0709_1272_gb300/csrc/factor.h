@@ -7,6 +7,8 @@
 namespace tqr {
 
 bool factor_supported(int nb, int ib);
+// The task-trace buffer set by tileqr_set_trace (nullptr: tracing off).
+void trace_target(unsigned long long **records, unsigned int *capacity);
 bool factor_mixed_supported(int nb, int ib);
 
 // Mixed-precision (TILEQR_TF32) factorization of the tiles in the workspace:

@@ -286,4 +286,71 @@ __host__ inline void ga_count(const TGraph &G, unsigned long long cnt[2])
     }
 }
 
+// ---------------------------------------------------------------------------
+// The tiled Cholesky factorization (Sec. 3.1, Algorithm 1) on p x p tiles:
+// tasks (k, i, j) with k <= j <= i: DPOTF2 (k,k,k), DTRSM (i,k,k), DGSMM
+// (i,j,k), j > k.  Dependencies (from the tiles each kernel reads/writes):
+//   DPOTF2(k)    <- DGSMM(k,k,k-1)
+//   DTRSM(i,k)   <- DPOTF2(k); DGSMM(i,k,k-1)
+//   DGSMM(i,j,k) <- DTRSM(i,k); DTRSM(j,k) (j < i); DGSMM(i,j,k-1)
+// The DGSMMs of column k+1 feed the next step's panel and get the higher of
+// the two update priority levels.
+enum { KC_POTF2 = 0, KC_TRSM = 1, KC_GSMM = 2 };
+
+__host__ __device__ inline int cg_kind(int k, int i, int j)
+{
+    return (j == k) ? (i == k ? KC_POTF2 : KC_TRSM) : KC_GSMM;
+}
+__host__ __device__ inline int cg_prio(int kind, int k, int j)
+{
+    return kind == KC_POTF2 ? 0 : (kind == KC_TRSM ? 1 : (j == k + 1 ? 2 : 3));
+}
+__host__ __device__ inline int cg_ndeps(int k, int i, int j)
+{
+    const int prev = k > 0 ? 1 : 0;
+    switch (cg_kind(k, i, j)) {
+    case KC_POTF2: return prev;
+    case KC_TRSM: return 1 + prev;
+    default: return (i == j ? 1 : 2) + prev;
+    }
+}
+__host__ __device__ inline size_t cg_cidx(int p, int k, int i, int j)
+{
+    return ((size_t)k * p + i) * p + j;
+}
+// successors: DPOTF2(k) -> DTRSM(i,k), i > k;  DTRSM(i,k) -> DGSMM(i,j,k),
+// k < j <= i, and DGSMM(i',i,k), i' > i;  DGSMM(i,j,k) -> the step-(k+1)
+// task on tile (i,j)
+__host__ __device__ inline int cg_nsucc(int p, int k, int i, int j)
+{
+    switch (cg_kind(k, i, j)) {
+    case KC_POTF2: return p - k - 1;
+    case KC_TRSM: return p - k - 1;
+    default: return 1;
+    }
+}
+__host__ __device__ inline GTask cg_succ(int p, int k, int i, int j, int s)
+{
+    switch (cg_kind(k, i, j)) {
+    case KC_POTF2: return GTask{0, k, k + 1 + s, k};
+    case KC_TRSM:
+        if (s < i - k)
+            return GTask{0, k, i, k + 1 + s};                  // row i: DGSMM(i, j, k)
+        return GTask{0, k, i + 1 + (s - (i - k)), i};          // column i: DGSMM(i', i, k)
+    default: return GTask{0, k + 1, i, j};
+    }
+}
+__host__ inline void cg_count(int p, unsigned long long cnt[4])
+{
+    for (int t = 0; t < 4; t++)
+        cnt[t] = 0;
+    for (int k = 0; k < p; k++) {
+        const unsigned long long r = p - k - 1;
+        cnt[0] += 1;
+        cnt[1] += r;
+        cnt[2] += r;                          // DGSMM on column k+1
+        cnt[3] += r * (r + 1) / 2 - r;        // the other DGSMMs
+    }
+}
+
 }  // namespace tqr

@@ -25,6 +25,7 @@ TILEQR_ERR_WORKSPACE = 1004
 TILEQR_ERR_SINGULAR = 1005
 TILEQR_ERR_UNSUPPORTED = 1006
 TILEQR_ERR_SCRATCH_LIMIT = 1007
+TILEQR_ERR_NOT_SPD = 1008
 
 EXPORTED = [
     "tileqr_workspace_size", "tileqr_factor", "tileqr_status", "tileqr_get_R",
@@ -36,6 +37,7 @@ EXPORTED = [
     "tileqr_batched_status", "tileqr_batched_get",
     "tileqr_workspace_size_tree", "tileqr_factor_tree", "tileqr_get_tree_T", "tileqr_task_graph",
     "tileqr_apply_q", "tileqr_form_q",
+    "tileqr_cholesky_workspace_size", "tileqr_cholesky", "tileqr_cholesky_get_L", "tileqr_cholesky_info",
 ]
 
 
@@ -122,6 +124,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_get_tree_T": (i32, [dp, vp, i64, vp]),
         "tileqr_apply_q": (i32, [dp, vp, i64, i64, vp, sz, vp]),
         "tileqr_form_q": (i32, [dp, vp, i64, i64, vp, sz, vp]),
+        "tileqr_cholesky_workspace_size": (i32, [i64, i32, ctypes.POINTER(sz)]),
+        "tileqr_cholesky": (i32, [i64, vp, i64, i32, i32, vp, sz, vp, dp]),
+        "tileqr_cholesky_get_L": (i32, [dp, vp, i64, vp]),
+        "tileqr_cholesky_info": (i32, [dp, vp, ctypes.POINTER(i64)]),
         "tileqr_task_graph": (i32, [i64, i64, i32, i32, i32, vp, vp, vp, vp, ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)]),
     }
@@ -248,6 +254,57 @@ def tileqr_task_graph(m: int, n: int, nb: int, domain: int = 0, what: int = 0):
                                  vp(ptr.ctypes.data), vp(succ.ctypes.data), ctypes.byref(nt), ctypes.byref(ne)),
            "tileqr_task_graph")
     return tasks, ndeps, ptr, succ[:ne.value]
+
+
+def tileqr_cholesky_workspace_size(n: int, nb: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().tileqr_cholesky_workspace_size(n, nb, ctypes.byref(out)), "tileqr_cholesky_workspace_size")
+    return out.value
+
+
+def tileqr_cholesky(A: torch.Tensor, nb: int = 128, workspace: torch.Tensor | None = None,
+                    stream=None) -> "CholeskyFactorization":
+    """Tiled Cholesky A = L L^T of an SPD matrix (only its lower triangle is read)."""
+    A = as_colmajor(A)
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("tileqr_cholesky needs a square matrix")
+    need = tileqr_cholesky_workspace_size(n, nb)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=A.device)
+    d = tileqr_desc()
+    rc = load().tileqr_cholesky(n, ctypes.c_void_p(A.data_ptr()), _ld(A), nb, 0,
+                                ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream_ptr(stream),
+                                ctypes.byref(d))
+    _check(rc, "tileqr_cholesky")
+    return CholeskyFactorization(d, workspace, A.device)
+
+
+class CholeskyFactorization:
+    """A tiled Cholesky factorization in a caller-owned (torch) workspace."""
+
+    def __init__(self, desc: tileqr_desc, workspace: torch.Tensor, device):
+        self.desc, self.workspace, self.device = desc, workspace, device
+
+    def status(self, stream=None) -> int:
+        return load().tileqr_status(ctypes.byref(self.desc), _stream_ptr(stream))
+
+    def check(self, stream=None):
+        _check(self.status(stream), "tileqr_cholesky")
+        return self
+
+    def info(self, stream=None) -> int:
+        out = ctypes.c_int64(0)
+        _check(load().tileqr_cholesky_info(ctypes.byref(self.desc), _stream_ptr(stream), ctypes.byref(out)),
+               "tileqr_cholesky_info")
+        return int(out.value)
+
+    def L(self, stream=None) -> torch.Tensor:
+        n = self.desc.n
+        L = colmajor_empty(n, n, self.device)
+        _check(load().tileqr_cholesky_get_L(ctypes.byref(self.desc), ctypes.c_void_p(L.data_ptr()), max(n, 1),
+                                            _stream_ptr(stream)), "tileqr_cholesky_get_L")
+        return L
 
 
 class Factorization:

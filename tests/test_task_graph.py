@@ -117,6 +117,13 @@ def test_apply_q_graph(tq, m, n, nb, h):
     _compare(keys, ndeps, edges, otasks, opreds)
 
 
+@pytest.mark.parametrize("n,nb", [(520, 64), (64 * 9, 64), (100, 64), (64, 64), (1000, 128)])
+def test_cholesky_graph(tq, n, nb):
+    keys, ndeps, edges = _graph(tq, n, n, nb, 0, 3)
+    otasks, opreds = oracle.cholesky_dependencies(n, nb)
+    _compare(keys, ndeps, edges, otasks, opreds)
+
+
 def test_task_counts_match_the_workspace_queues(tq):
     # the write-once ready queues are sized from closed-form counts; they must
     # equal the enumerated graph
