@@ -24,7 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tileqr_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "cholesky_oracle.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "cholesky_oracle.c"), os.path.join(_HERE, "lu_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 TASK_GEQRT, TASK_TSQRT, TASK_LARFB, TASK_SSRFB = 0, 1, 2, 3
@@ -69,6 +69,16 @@ def _load():
         lib.oracle_tiled_cholesky.restype = ctypes.c_int
         lib.oracle_tiled_cholesky_ordered.restype = ctypes.c_int
         lib.chol_set_mutation.argtypes = [i32]
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.oracle_tiled_lu.argtypes = [i64, dp, i64, i32, i32, dp, i64, ip]
+        lib.oracle_tiled_lu_ordered.argtypes = [i64, dp, i64, i32, i32, dp, i64, ip, i64,
+                                                ctypes.POINTER(ctypes.c_int32)]
+        lib.oracle_lu_apply.argtypes = [i64, dp, i64, i32, i32, dp, i64, ip, i64, dp, i64, i32]
+        lib.oracle_lu_unapply.argtypes = [i64, dp, i64, i32, i32, dp, i64, ip, i64, dp, i64]
+        for f in (lib.oracle_tiled_lu, lib.oracle_tiled_lu_ordered, lib.oracle_lu_apply, lib.oracle_lu_unapply):
+            f.restype = ctypes.c_int
+        lib.lu_set_mutation.argtypes = [i32]
+        lib.lu_flops.restype = ctypes.c_double
         lib.chol_flops.restype = ctypes.c_double
         lib.oracle_flops.restype = ctypes.c_double
         lib.oracle_set_mutation.argtypes = [i32]
@@ -626,6 +636,171 @@ def cholesky_random_order(n: int, nb: int, rng: np.random.Generator):
                 ready.append(x)
     assert len(order) == len(tasks)
     return order
+
+
+# ---------------------------------------------------------------------------
+# Tiled LU with tiled pairwise pivoting (Sec. 3.2.2, Algorithm 3; GETWP).
+TASK_GETRF, TASK_GESSM, TASK_TSTRF, TASK_SSSSM = 0, 1, 2, 3
+
+
+class LUFactored:
+    """A (n x n, U and multipliers in place), Lx ((p*ib) x n: the L1 blocks of
+    each DTSTRF), piv (p x n ints: the pivots), info (first zero-pivot
+    column + 1, or 0)."""
+
+    def __init__(self, A, Lx, piv, n, nb, ib, info):
+        self.A, self.Lx, self.piv, self.n, self.nb, self.ib, self.info = A, Lx, piv, n, nb, ib, info
+
+    def U(self) -> np.ndarray:
+        return np.triu(self.A)
+
+    def _ip(self):
+        return self.piv.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+    def apply(self, Y, solve: bool = False) -> np.ndarray:
+        """The factorization's transformations applied to Y (Algorithm 3's
+        order); with solve, followed by the back substitution with U: A^{-1} Y."""
+        lib = _load()
+        Y = _fortran(Y)
+        if Y.ndim == 1:
+            Y = Y.reshape(-1, 1, order="F")
+        rc = lib.oracle_lu_apply(self.n, _dp(self.A), max(self.n, 1), self.nb, self.ib, _dp(self.Lx),
+                                 self.Lx.shape[0], self._ip(), Y.shape[1], _dp(Y), max(self.n, 1), int(solve))
+        if rc:
+            raise ValueError(f"oracle_lu_apply: {rc}")
+        return Y
+
+    def solve(self, Y) -> np.ndarray:
+        return self.apply(Y, solve=True)
+
+    def N_times(self, X) -> np.ndarray:
+        """N X, with N the inverse of the factorization's transformations
+        (Sec. 3.2.4): N U reconstructs A."""
+        lib = _load()
+        X = _fortran(X)
+        rc = lib.oracle_lu_unapply(self.n, _dp(self.A), max(self.n, 1), self.nb, self.ib, _dp(self.Lx),
+                                   self.Lx.shape[0], self._ip(), X.shape[1], _dp(X), max(self.n, 1))
+        if rc:
+            raise ValueError(f"oracle_lu_unapply: {rc}")
+        return X
+
+
+def _lu_arrays(n, nb, ib):
+    p = n // nb
+    Lx = np.zeros((max(p * ib, 1), max(n, 1)), order="F")
+    piv = np.zeros((max(p, 1), max(n, 1)), dtype=np.int32, order="F")
+    return Lx, piv
+
+
+def tiled_lu(A, nb: int, ib: int) -> LUFactored:
+    """Algorithm 3 on a copy of A (n x n, n a multiple of nb)."""
+    lib = _load()
+    A = _fortran(A)
+    n = A.shape[0]
+    Lx, piv = _lu_arrays(n, nb, ib)
+    info = lib.oracle_tiled_lu(n, _dp(A), max(n, 1), nb, ib, _dp(Lx), Lx.shape[0],
+                               piv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if info < 0:
+        raise ValueError(f"oracle_tiled_lu: illegal argument {info}")
+    return LUFactored(A, Lx, piv, n, nb, ib, info)
+
+
+def tiled_lu_ordered(A, nb: int, ib: int, tasks) -> LUFactored:
+    lib = _load()
+    A = _fortran(A)
+    n = A.shape[0]
+    Lx, piv = _lu_arrays(n, nb, ib)
+    tk = np.ascontiguousarray(np.asarray(tasks, dtype=np.int32).reshape(-1, 4))
+    info = lib.oracle_tiled_lu_ordered(n, _dp(A), max(n, 1), nb, ib, _dp(Lx), Lx.shape[0],
+                                       piv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), tk.shape[0],
+                                       tk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if info < 0:
+        raise ValueError(f"oracle_tiled_lu_ordered: illegal argument {info}")
+    return LUFactored(A, Lx, piv, n, nb, ib, info)
+
+
+def lu_set_mutation(code: int) -> None:
+    _load().lu_set_mutation(int(code))
+
+
+def lu_flops() -> float:
+    return _load().lu_flops()
+
+
+def lu_reset_flops() -> None:
+    _load().lu_reset_flops()
+
+
+def lu_task_list(n: int, nb: int):
+    """Tasks {kind, i, j, k} of Algorithm 3 in its printed loop order."""
+    p = n // nb
+    out = []
+    for k in range(p):
+        out.append((TASK_GETRF, k, k, k))
+        for j in range(k + 1, p):
+            out.append((TASK_GESSM, k, j, k))
+        for i in range(k + 1, p):
+            out.append((TASK_TSTRF, i, k, k))
+            for j in range(k + 1, p):
+                out.append((TASK_SSSSM, i, j, k))
+    return out
+
+
+def lu_dependencies(n: int, nb: int):
+    """Predecessor sets of Algorithm 3 from the tiles each kernel reads and
+    writes (Sec. 3.2.2): the diagonal tile is split into its U part ('U')
+    and its DGETRF multipliers ('L'); ('X', i, k) are the DTSTRF pivots and
+    L1 blocks."""
+
+    def access(t):
+        kind, i, j, k = t
+        if kind == TASK_GETRF:
+            return {("A", k, k)}, {("U", k, k), ("L", k, k)}
+        if kind == TASK_GESSM:
+            return {("L", k, k)}, {("A", k, j)}
+        if kind == TASK_TSTRF:
+            return set(), {("U", k, k), ("A", i, k), ("X", i, k)}
+        return {("A", i, k), ("X", i, k)}, {("A", k, j), ("A", i, j)}
+
+    tasks = lu_task_list(n, nb)
+    return tasks, _mechanical_deps(tasks, access)
+
+
+def lu_random_order(n: int, nb: int, rng: np.random.Generator):
+    tasks, preds = lu_dependencies(n, nb)
+    succ = {t: [] for t in tasks}
+    indeg = {t: len(preds[t]) for t in tasks}
+    for t, ps in preds.items():
+        for x in ps:
+            succ[x].append(t)
+    ready = [t for t in tasks if indeg[t] == 0]
+    order = []
+    while ready:
+        t = ready.pop(int(rng.integers(len(ready))))
+        order.append(t)
+        for x in succ[t]:
+            indeg[x] -= 1
+            if indeg[x] == 0:
+                ready.append(x)
+    assert len(order) == len(tasks)
+    return order
+
+
+def lu_stability(A0: np.ndarray, f: "LUFactored", y=None) -> dict:
+    """The measures of Sec. 3.2.4 (infinity norms): backward error of the
+    factorization ||A - N U|| / ||A||, of the solution ||y - A x|| / (||A||
+    ||x||) for a right-hand side y, ||N||, ||U|| and || |N| |U| ||."""
+    n = f.n
+    U = f.U()
+    N = f.N_times(np.eye(n))
+    inf = lambda M: float(np.abs(M).sum(axis=1).max()) if M.size else 0.0
+    nA = inf(A0)
+    out = {"fact_backward": inf(A0 - N @ U) / nA, "norm_N": inf(N), "norm_U": inf(U),
+           "norm_absN_absU": inf(np.abs(N) @ np.abs(U))}
+    if y is not None:
+        x = f.solve(y)
+        out["solve_backward"] = inf(y - A0 @ x) / (nA * inf(x))
+    return out
 
 
 if __name__ == "__main__":
