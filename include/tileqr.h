@@ -333,6 +333,58 @@ int tileqr_cholesky_get_L(const tileqr_desc *d, double *L, int64_t ldl, tileqr_s
  * (synchronises the stream). */
 int tileqr_cholesky_info(const tileqr_desc *d, tileqr_stream_t stream, int64_t *info);
 
+/* Tiled LU factorization with tiled pairwise pivoting (Sec. 3.2.2,
+ * Algorithm 3; inner blocking of Sec. 3.2.3): the tasks DGETRF (LU with
+ * partial pivoting of a diagonal tile), DGESSM (its interchanges and L^{-1}
+ * applied to a tile of its row), DTSTRF (LU with pairwise pivoting of the
+ * stacked [U_kk; A_ik]) and DSSSSM (its transformations applied to the
+ * stacked pair [U_kj; A_ij]) run as a task graph in one persistent kernel
+ * (FP64).  The graph is that of Algorithm 2's flat tree, kernel for kernel.
+ * The result is N U = A (Sec. 3.2.4), N the inverse of the recorded
+ * transformations: not the P A = L U of partial pivoting.
+ *   n, A, lda  device, column-major, FP64; A is not modified
+ *   nb, ib     tile size 64 or 128, inner block 16 or 32 (else
+ *              TILEQR_ERR_UNSUPPORTED).  n need not be a multiple of nb:
+ *              the padding is the identity and stays the identity.
+ *   flags      0, or TILEQR_FLAG_TEST_WITHHOLD_LAST_TASK (watchdog test)
+ *   workspace  device, 256-byte aligned, >= tileqr_lu_workspace_size()
+ *   out        host descriptor (m = n, T = the L1 strips)
+ * Pivots are the first entry of largest magnitude among the candidates.  An
+ * exactly zero pivot does not stop the factorization (U then has a zero on
+ * its diagonal); tileqr_lu_info reports the smallest such column.
+ * Asynchronous.  Returns 0, -i, TILEQR_ERR_WORKSPACE, TILEQR_ERR_UNSUPPORTED,
+ * TILEQR_ERR_CUDA; tileqr_status() then reports 0, TILEQR_ERR_NONFINITE
+ * (nothing factored) or TILEQR_ERR_TIMEOUT. */
+int tileqr_lu_workspace_size(int64_t n, int nb, int ib, size_t *bytes);
+int tileqr_lu(int64_t n, const double *A, int64_t lda, int nb, int ib, int flags, void *workspace,
+              size_t ws_bytes, tileqr_stream_t stream, tileqr_desc *out);
+/* *info = 0, or the smallest 1-based column at which an exactly zero pivot
+ * was met (synchronises the stream). */
+int tileqr_lu_info(const tileqr_desc *d, tileqr_stream_t stream, int64_t *info);
+/* The factors, to device arrays (asynchronous; NULL skips Lx / piv):
+ *   F    n x n (ldf >= n): U on and above the diagonal; below it the
+ *        multipliers: DGETRF's in the diagonal tiles, DTSTRF's L2 blocks in
+ *        the tiles below (tile (i, k), column block l = ib columns)
+ *   Lx   (p*ib) x n (ldlx >= p*ib): the unit lower ib x ib blocks L1 of the
+ *        DTSTRF of tile (i, k) at rows i*ib.., columns k*nb + l*ib..
+ *        (unit diagonal stored; zero for i <= k)
+ *   piv  p x n int (ldpiv >= p): entry (i, k*nb + c) = pivot c of DGETRF
+ *        (i == k: the tile row swapped with row c, >= c, LAPACK's
+ *        convention) or DTSTRF (i > k: < nb a row of U_kk, else row
+ *        piv - nb of tile (i, k)); 0 for i < k.
+ * Returns 0, -i, TILEQR_ERR_CUDA. */
+int tileqr_lu_get_factors(const tileqr_desc *d, double *F, int64_t ldf, double *Lx, int64_t ldlx, int *piv,
+                          int64_t ldpiv, tileqr_stream_t stream);
+/* Solve A X = B in place (B: device, n x nrhs, ldb >= n): the recorded
+ * transformations applied to B in Algorithm 3's order as a task graph
+ * (DGESSM / DSSSSM on column chunks of B), then the tiled back substitution
+ * with U.  Synchronous.  Returns 0, -i, TILEQR_ERR_WORKSPACE,
+ * TILEQR_ERR_SINGULAR (U has an exact zero on its diagonal),
+ * TILEQR_ERR_TIMEOUT, TILEQR_ERR_CUDA. */
+int tileqr_lu_solve_workspace_size(const tileqr_desc *d, int64_t nrhs, size_t *bytes);
+int tileqr_lu_solve(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace, size_t ws_bytes,
+                    tileqr_stream_t stream);
+
 /* Human-readable text for a return code (static storage). */
 const char *tileqr_strerror(int code);
 
@@ -365,6 +417,8 @@ int tileqr_trace_count(const tileqr_desc *d, tileqr_stream_t stream, uint64_t *c
  *             2 = Q applied to one chunk (tileqr_apply_q / tileqr_form_q);
  *             3 = the tiled Cholesky of an m x m matrix (tileqr_cholesky;
  *             n and domain ignored; kinds 0 DPOTF2, 1 DTRSM, 2 DGSMM)
+ *             4 = the tiled LU of an m x m matrix (tileqr_lu; n and domain
+ *             ignored; kinds 0 DGETRF, 1 DGESSM, 2 DTSTRF, 3 DSSSSM)
  *   tasks     ntasks rows {kind, i, j, k}: kind 0 DGEQRT, 1 DTSQRT, 2 DLARFB,
  *             3 DSSRFB, 4 DTTQRT, 5 DTTMQR; j = -1 for what = 1
  *   ndeps     per task, the number of predecessors that release it

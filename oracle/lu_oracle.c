@@ -32,8 +32,9 @@
  *    right then receive the swaps, U rows <- L1^{-1} U rows and A -= L2 U rows.
  *    DSSSSM applies exactly this, block by block, to another tile column.
  *  - An exactly zero pivot leaves its column's multipliers at zero and the
- *    factorization continues (U then has a zero on its diagonal); the first
- *    such column is reported.
+ *    factorization continues (U then has a zero on its diagonal); the
+ *    smallest such column is reported (a definition that does not depend
+ *    on the order the tasks ran in).
  */
 #include <math.h>
 #include <stdint.h>
@@ -305,7 +306,8 @@ static int run_lutask(int64_t n, double *A, int64_t lda, int nb, int ib, double 
 
 /* Algorithm 3 in its printed loop order.  Lx: (p*ib) x n (ldlx >= p*ib),
  * zeroed first; piv: p x n ints.  Returns 0, a negative argument index, or
- * the first zero-pivot column + 1 (the factorization is still completed). */
+ * the smallest column + 1 at which some task met an exactly zero pivot (the
+ * factorization is still completed). */
 int oracle_tiled_lu(int64_t n, double *A, int64_t lda, int nb, int ib, double *Lx, int64_t ldlx, int *piv)
 {
     int rc = check(n, lda, nb, ib);
@@ -319,16 +321,16 @@ int oracle_tiled_lu(int64_t n, double *A, int64_t lda, int nb, int ib, double *L
     for (int64_t c = 0; c < n; c++)
         for (int64_t r = 0; r < ldlx; r++)
             Lx[c * ldlx + r] = 0.0;
-    int first = 0;
+    int first = 0;   /* the smallest column with a zero pivot, over all tasks */
     for (int k = 0; k < p; k++) {
         int z = run_lutask(n, A, lda, nb, ib, Lx, ldlx, piv, TASK_GETRF, k, k, k);
-        if (z && !first)
+        if (z && (!first || z < first))
             first = z;
         for (int j = k + 1; j < p; j++)
             run_lutask(n, A, lda, nb, ib, Lx, ldlx, piv, TASK_GESSM, k, j, k);
         for (int i = k + 1; i < p; i++) {
             z = run_lutask(n, A, lda, nb, ib, Lx, ldlx, piv, TASK_TSTRF, i, k, k);
-            if (z && !first)
+            if (z && (!first || z < first))
                 first = z;
             for (int j = k + 1; j < p; j++)
                 run_lutask(n, A, lda, nb, ib, Lx, ldlx, piv, TASK_SSSSM, i, j, k);

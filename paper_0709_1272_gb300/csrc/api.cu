@@ -23,7 +23,7 @@ void trace_target(unsigned long long **records, unsigned int *capacity)
     *capacity = (unsigned int)(g_trace_cap > 0xffffffffull ? 0xffffffffull : g_trace_cap);
 }
 
-static unsigned long long watchdog_ns_default()
+unsigned long long watchdog_ns_default()
 {
     const char *e = std::getenv("TILEQR_WATCHDOG_MS");
     long ms = e ? std::atol(e) : 0;
@@ -510,7 +510,7 @@ extern "C" int tileqr_task_graph(int64_t m, int64_t n, int nb, int domain, int w
         return -3;
     if (domain < 0)
         return -4;
-    if (what < 0 || what > 3)
+    if (what < 0 || what > 4)
         return -5;
     if (ntasks == nullptr)
         return -10;
@@ -566,6 +566,12 @@ extern "C" int tileqr_task_graph(int64_t m, int64_t n, int nb, int domain, int w
         }
         succ_ptr[list.size()] = pos;
         return 0;
+    }
+    const bool lu = what == 4;   // the LU graph is the flat factorization graph, LU kind names
+    if (lu) {
+        n = m;
+        domain = 0;
+        what = 0;
     }
     const int p = (int)((m + nb - 1) / nb), q = (int)((n + nb - 1) / nb);
     const TGraph G = make_graph(p, q, domain);
@@ -631,7 +637,7 @@ extern "C" int tileqr_task_graph(int64_t m, int64_t n, int nb, int domain, int w
     for (size_t t = 0; t < list.size(); t++) {
         const GTask a = list[t];
         const int kind = what >= 1 ? ga_kind(G, a.tt, a.k, a.i) : g_kind(G, a.tt, a.k, a.i, a.j);
-        tasks[4 * t + 0] = kind;
+        tasks[4 * t + 0] = lu ? lu_kind_of(kind) : kind;
         tasks[4 * t + 1] = a.i;
         tasks[4 * t + 2] = a.j;
         tasks[4 * t + 3] = a.k;

@@ -4,6 +4,7 @@
 // cores (tile_mixed.cuh) while DGEQRT/DTSQRT stay in FP64.
 #pragma once
 #include "graph.cuh"
+#include "release.cuh"
 #include "sched.cuh"
 #include "tile_f64.cuh"
 #include "tile_mixed.cuh"
@@ -85,21 +86,6 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
                                                         strip2_ptr<NB, S>(F, i, k));
         break;
     }
-    }
-}
-
-// Successors of a finished task in graph G, signalled cooperatively by all
-// threads of the CTA (the mirror of g_ndeps; see graph.cuh).
-__device__ static void release_graph(const Queues &Q, const TGraph &G, int kind, int k, int i, int j)
-{
-    const int fan = g_fanout(G, kind, k);
-    GTask sp[2];
-    const int nsp = g_specific(G, kind, k, i, j, sp);
-    for (int s = threadIdx.x; s < fan + nsp; s += NT) {
-        const GTask t = s < fan ? g_fan_task(kind, k, i, s) : sp[s - fan];
-        const int tk = g_kind(G, t.tt, t.k, t.i, t.j);
-        q_signal(Q, g_cidx(G, t.tt, t.k, t.i, t.j), g_ndeps(tk, t.k), kind_prio(tk),
-                 encode_task(t.k, t.i, t.j, t.tt));
     }
 }
 

@@ -7,6 +7,8 @@
 namespace tqr {
 
 bool factor_supported(int nb, int ib);
+// The scheduler watchdog limit (TILEQR_WATCHDOG_MS, default 10 s), in ns.
+unsigned long long watchdog_ns_default();
 // The task-trace buffer set by tileqr_set_trace (nullptr: tracing off).
 void trace_target(unsigned long long **records, unsigned int *capacity);
 bool factor_mixed_supported(int nb, int ib);

@@ -353,4 +353,24 @@ __host__ inline void cg_count(int p, unsigned long long cnt[4])
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// The tiled LU with tiled pairwise pivoting (Sec. 3.2.2, Algorithm 3) has the
+// task graph of Algorithm 2 (the flat tree) kernel for kernel: DGETRF reads
+// and writes the diagonal tile like DGEQRT, DGESSM reads its multipliers
+// like DLARFB, DTSTRF chains on U_kk like DTSQRT on R_kk, and DSSSSM updates
+// the pair (U_kj, A_ij) like DSSRFB.  The LU path therefore runs the graph
+// functions above with H = p; these are the LU names of the four kinds.
+enum { KL_GETRF = 0, KL_GESSM = 1, KL_TSTRF = 2, KL_SSSSM = 3 };
+
+__host__ __device__ inline int lu_kind_of(int qr_kind)
+{
+    switch (qr_kind) {
+    case K_GEQRT: return KL_GETRF;
+    case K_LARFB: return KL_GESSM;
+    case K_TSQRT: return KL_TSTRF;
+    default: return KL_SSSSM;
+    }
+}
+
 }  // namespace tqr

@@ -38,6 +38,8 @@ EXPORTED = [
     "tileqr_workspace_size_tree", "tileqr_factor_tree", "tileqr_get_tree_T", "tileqr_task_graph",
     "tileqr_apply_q", "tileqr_form_q",
     "tileqr_cholesky_workspace_size", "tileqr_cholesky", "tileqr_cholesky_get_L", "tileqr_cholesky_info",
+    "tileqr_lu_workspace_size", "tileqr_lu", "tileqr_lu_info", "tileqr_lu_get_factors",
+    "tileqr_lu_solve_workspace_size", "tileqr_lu_solve",
 ]
 
 
@@ -128,6 +130,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_cholesky": (i32, [i64, vp, i64, i32, i32, vp, sz, vp, dp]),
         "tileqr_cholesky_get_L": (i32, [dp, vp, i64, vp]),
         "tileqr_cholesky_info": (i32, [dp, vp, ctypes.POINTER(i64)]),
+        "tileqr_lu_workspace_size": (i32, [i64, i32, i32, ctypes.POINTER(sz)]),
+        "tileqr_lu": (i32, [i64, vp, i64, i32, i32, i32, vp, sz, vp, dp]),
+        "tileqr_lu_info": (i32, [dp, vp, ctypes.POINTER(i64)]),
+        "tileqr_lu_get_factors": (i32, [dp, vp, i64, vp, i64, vp, i64, vp]),
+        "tileqr_lu_solve_workspace_size": (i32, [dp, i64, ctypes.POINTER(sz)]),
+        "tileqr_lu_solve": (i32, [dp, vp, i64, i64, vp, sz, vp]),
         "tileqr_task_graph": (i32, [i64, i64, i32, i32, i32, vp, vp, vp, vp, ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)]),
     }
@@ -305,6 +313,82 @@ class CholeskyFactorization:
         _check(load().tileqr_cholesky_get_L(ctypes.byref(self.desc), ctypes.c_void_p(L.data_ptr()), max(n, 1),
                                             _stream_ptr(stream)), "tileqr_cholesky_get_L")
         return L
+
+
+def tileqr_lu_workspace_size(n: int, nb: int, ib: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().tileqr_lu_workspace_size(n, nb, ib, ctypes.byref(out)), "tileqr_lu_workspace_size")
+    return out.value
+
+
+def tileqr_lu(A: torch.Tensor, nb: int = 128, ib: int = 16, workspace: torch.Tensor | None = None,
+              stream=None, flags: int = 0) -> "LUFactorization":
+    """Tiled LU with tiled pairwise pivoting (Algorithm 3) of a square FP64 matrix."""
+    A = as_colmajor(A)
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("tileqr_lu needs a square matrix")
+    need = tileqr_lu_workspace_size(n, nb, ib)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=A.device)
+    d = tileqr_desc()
+    rc = load().tileqr_lu(n, ctypes.c_void_p(A.data_ptr()), _ld(A), nb, ib, flags,
+                          ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream_ptr(stream),
+                          ctypes.byref(d))
+    _check(rc, "tileqr_lu")
+    return LUFactorization(d, workspace, A.device)
+
+
+class LUFactorization:
+    """A tiled LU factorization (N U = A) in a caller-owned (torch) workspace."""
+
+    def __init__(self, desc: tileqr_desc, workspace: torch.Tensor, device):
+        self.desc, self.workspace, self.device = desc, workspace, device
+        self._solve_ws = None
+
+    def status(self, stream=None) -> int:
+        return load().tileqr_status(ctypes.byref(self.desc), _stream_ptr(stream))
+
+    def check(self, stream=None):
+        _check(self.status(stream), "tileqr_lu")
+        return self
+
+    def info(self, stream=None) -> int:
+        out = ctypes.c_int64(0)
+        _check(load().tileqr_lu_info(ctypes.byref(self.desc), _stream_ptr(stream), ctypes.byref(out)),
+               "tileqr_lu_info")
+        return int(out.value)
+
+    def factors(self, stream=None):
+        """(F, Lx, piv): F n x n (U and the multipliers), Lx (p*ib) x n, piv
+        p x n int32, all column-major device tensors."""
+        d = self.desc
+        n, p, ib = d.n, d.p, d.ib
+        F = colmajor_empty(n, n, self.device)
+        Lx = colmajor_empty(max(p * ib, 1), n, self.device)
+        piv = torch.empty((n, max(p, 1)), dtype=torch.int32, device=self.device).t()
+        _check(load().tileqr_lu_get_factors(ctypes.byref(d), ctypes.c_void_p(F.data_ptr()), max(n, 1),
+                                            ctypes.c_void_p(Lx.data_ptr()), max(p * ib, 1),
+                                            ctypes.c_void_p(piv.data_ptr()), max(p, 1), _stream_ptr(stream)),
+               "tileqr_lu_get_factors")
+        return F, Lx, piv
+
+    def solve(self, B: torch.Tensor, stream=None) -> torch.Tensor:
+        """A^{-1} B (B: n x nrhs or n, FP64 on the device), in a new tensor."""
+        vec = B.dim() == 1
+        Bm = as_colmajor(B.reshape(-1, 1) if vec else B)
+        X = colmajor_empty(Bm.shape[0], Bm.shape[1], self.device)
+        X.copy_(Bm)
+        nrhs = X.shape[1]
+        need = ctypes.c_size_t(0)
+        _check(load().tileqr_lu_solve_workspace_size(ctypes.byref(self.desc), nrhs, ctypes.byref(need)),
+               "tileqr_lu_solve_workspace_size")
+        if self._solve_ws is None or self._solve_ws.numel() < need.value:
+            self._solve_ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=self.device)
+        _check(load().tileqr_lu_solve(ctypes.byref(self.desc), ctypes.c_void_p(X.data_ptr()), _ld(X), nrhs,
+                                      ctypes.c_void_p(self._solve_ws.data_ptr()), self._solve_ws.numel(),
+                                      _stream_ptr(stream)), "tileqr_lu_solve")
+        return X.reshape(-1) if vec else X
 
 
 class Factorization:

@@ -124,6 +124,15 @@ def test_cholesky_graph(tq, n, nb):
     _compare(keys, ndeps, edges, otasks, opreds)
 
 
+@pytest.mark.parametrize("n,nb", [(320, 64), (64 * 9, 64), (100, 64), (64, 64), (1024, 128)])
+def test_lu_graph(tq, n, nb):
+    # Algorithm 3's graph, executed with the flat-tree graph functions
+    keys, ndeps, edges = _graph(tq, n, n, nb, 0, 4)
+    npad = -(-n // nb) * nb
+    otasks, opreds = oracle.lu_dependencies(npad, nb)
+    _compare(keys, ndeps, edges, otasks, opreds)
+
+
 def test_task_counts_match_the_workspace_queues(tq):
     # the write-once ready queues are sized from closed-form counts; they must
     # equal the enumerated graph
