@@ -52,7 +52,7 @@ def kernel_source_hash():
     h = hashlib.sha256()
     for rel in ("paper_0709_1272_gb300/csrc/common.cuh", "paper_0709_1272_gb300/csrc/sched.cuh",
                 "paper_0709_1272_gb300/csrc/tile_f64.cuh", "paper_0709_1272_gb300/csrc/dag.cuh",
-                "paper_0709_1272_gb300/csrc/factor.cu"):
+                "paper_0709_1272_gb300/csrc/release.cuh", "paper_0709_1272_gb300/csrc/factor.cu"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -329,6 +329,70 @@ def run_cholesky(args, dev, rank, world, barrier, dist):
             "timing": "CUDA events around the factorizations (layout conversion included), max over ranks"}
 
 
+def run_lu(args, dev, rank, world, barrier, dist):
+    """Tiled LU with tiled pairwise pivoting (Sec. 3.2.2, Algorithm 3): n x n
+    N(0,1), nb 128, ib 16, FP64 task graph; rate with LU's 2n^3/3 operation
+    count (the algorithm performs (1 + ib/(2nb)) times that, Sec. 3.2.3).
+    Accuracy as in Sec. 3.2.4: the solve's backward error ||b - A x||_inf /
+    (||A||_inf ||x||_inf) and the growth ||U||_inf / ||A||_inf, at this size
+    and at n = 2048 for the tile counts the library builds (p = 16, 32)."""
+    import torch
+    from paper_0709_1272_gb300 import replicas, tileqr
+    n, nb, ib = args.n, 128, 16
+    g = torch.Generator(device=dev).manual_seed(20070709 + 8 + 1000 * rank)
+    A = torch.randn((n, n), generator=g, dtype=torch.float64, device=dev).t()
+    ws = torch.empty(tileqr.tileqr_lu_workspace_size(n, nb, ib), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    tileqr.tileqr_lu(A, nb, ib, workspace=ws).check()   # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(2, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        f = tileqr.tileqr_lu(A, nb, ib, workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    f.check()
+    info = f.info()
+    t = replicas.max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps, dist, dev)
+    ops = 2.0 * n ** 3 / 3.0
+    peaks = measured_peaks()
+    fp64_peak = NSM * FP64_FLOP_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
+    inf = lambda M: M.abs().sum(dim=1).max().item()
+
+    def accuracy(Am, fm):
+        B = torch.randn((Am.shape[0], 4), generator=g, dtype=torch.float64, device=dev)
+        X = fm.solve(B)
+        U = torch.triu(fm.factors()[0])
+        nA = inf(Am)
+        return inf(B - Am @ X) / (nA * inf(X)), inf(U) / nA
+
+    be, growth = accuracy(A, f)
+    del ws
+    sweep = {}
+    for nbs in (128, 64):
+        n2 = 2048
+        bes, grs = [], []
+        for smp in range(5):
+            A2 = torch.randn((n2, n2), generator=g, dtype=torch.float64, device=dev).t()
+            f2 = tileqr.tileqr_lu(A2, nbs, 16).check()
+            b2, g2 = accuracy(A2, f2)
+            bes.append(b2)
+            grs.append(g2)
+        sweep[f"p={n2 // nbs}"] = {"n": n2, "nb": nbs, "ib": 16, "samples": 5,
+                                   "solve_backward_mean": sum(bes) / len(bes), "solve_backward_max": max(bes),
+                                   "growth_U_mean": sum(grs) / len(grs)}
+    del A, f
+    return {"workload": f"tiled LU with tiled pairwise pivoting (Algorithm 3), {n}x{n} N(0,1), nb={nb}, ib={ib}, "
+                        f"FP64 task graph", "value": world * ops / t / 1e9, "unit": UNIT, "ms_per_step": t * 1e3,
+            "steps": reps, "pct_fp64_peak": 100.0 * (ops / t / 1e9) / fp64_peak,
+            "algorithmic_gflops": (ops * (1.0 + ib / (2.0 * nb))) / t / 1e9,
+            "zero_pivot_info": info, "solve_backward_error": be, "growth_U": growth,
+            "stability_n2048": sweep,
+            "timing": "CUDA events around the factorizations (layout conversion included), max over ranks"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -351,6 +415,10 @@ def main():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-cholesky", action="store_true",
                     help="skip the tiled Cholesky (Algorithm 1) measurement")
+    ap.add_argument("--only", choices=["lu", "cholesky"], default=None,
+                    help="run only this secondary measurement (at --n) and print its JSON object")
+    ap.add_argument("--no-lu", action="store_true",
+                    help="skip the tiled LU (Algorithm 3) measurement")
     ap.add_argument("--no-tall", action="store_true",
                     help="skip the tall-skinny (262144 x 512, flat vs tree) measurement")
     ap.add_argument("--tall-m", type=int, default=262144)
@@ -379,6 +447,19 @@ def main():
     tileqr.load()
     sched = tileqr.TILEQR_SCHED_DAG if args.schedule == "dag" else tileqr.TILEQR_SCHED_BULK
     m, n, nb, ib = args.m, args.n, args.nb, args.ib
+
+    if args.only:
+        # one secondary measurement alone (its JSON object on one line), e.g.
+        # for a profiler run of that path
+        def barrier():
+            if dist is not None:
+                dist.barrier()
+        section = {"lu": run_lu, "cholesky": run_cholesky}[args.only](args, dev, rank, world, barrier, dist)
+        if rank == 0:
+            print(json.dumps({"section": args.only, **section}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
 
     A_host = inputs.normal_matrix(m, n, seed=20070709 + 1 + 1000 * rank)
     A = tileqr.to_device_colmajor(A_host, dev)
@@ -517,6 +598,12 @@ def main():
         torch.cuda.empty_cache()
         chol = run_cholesky(args, dev, rank, world, barrier, dist)
 
+    # ---- tiled LU with tiled pairwise pivoting (Algorithm 3), same order
+    lu = None
+    if not args.no_lu and m == n:
+        torch.cuda.empty_cache()
+        lu = run_lu(args, dev, rank, world, barrier, dist)
+
     # ---- tall-skinny 262144 x 512: flat tree vs tree form
     tall = None
     if not args.no_tall:
@@ -565,6 +652,8 @@ def main():
         out["tall_skinny"] = tall
     if chol:
         out["cholesky"] = chol
+    if lu:
+        out["lu"] = lu
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(nb, ib)
     print(json.dumps(out), flush=True)
