@@ -48,26 +48,28 @@ def measured_peaks():
         return {}
 
 
-def kernel_source_hash():
+QR_SOURCES = ("common.cuh", "sched.cuh", "tile_f64.cuh", "dag.cuh", "release.cuh", "factor.cu")
+LU_SOURCES = ("common.cuh", "sched.cuh", "graph.cuh", "release.cuh", "lu.cuh", "lu.cu")
+
+
+def kernel_source_hash(files=QR_SOURCES):
     h = hashlib.sha256()
-    for rel in ("paper_0709_1272_gb300/csrc/common.cuh", "paper_0709_1272_gb300/csrc/sched.cuh",
-                "paper_0709_1272_gb300/csrc/tile_f64.cuh", "paper_0709_1272_gb300/csrc/dag.cuh",
-                "paper_0709_1272_gb300/csrc/release.cuh", "paper_0709_1272_gb300/csrc/factor.cu"):
-        with open(os.path.join(ROOT, rel), "rb") as fh:
+    for rel in files:
+        with open(os.path.join(ROOT, "paper_0709_1272_gb300", "csrc", rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 
 
-def profiled_traffic(workload_key):
-    """DRAM bytes per launch of the task-graph kernel from the committed ncu
-    summary, if it was taken on the current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", "k_factor_dag_fp64.md")
+def profiled_traffic(workload_key, profile="k_factor_dag_fp64.md", files=QR_SOURCES):
+    """DRAM bytes per launch of a task-graph kernel from its committed ncu
+    summary, if that was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", profile)
     try:
         txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
-    if not m or m.group(1) != kernel_source_hash():
+    if not m or m.group(1) != kernel_source_hash(files):
         return None
     m = re.search(rf"traffic_bytes_per_launch\[{re.escape(workload_key)}\]:\s*([0-9.eE+]+)", txt)
     return float(m.group(1)) if m else None
@@ -384,12 +386,18 @@ def run_lu(args, dev, rank, world, barrier, dist):
                                    "solve_backward_mean": sum(bes) / len(bes), "solve_backward_max": max(bes),
                                    "growth_U_mean": sum(grs) / len(grs)}
     del A, f
+    alg = ops * (1.0 + ib / (2.0 * nb))
+    roof = {"bound": "alu", "achieved": alg / t / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
+            "frac": alg / t / 1e9 / fp64_peak,
+            "traffic": profiled_traffic(f"{n}x{n}/nb{nb}/ib{ib}", "k_lu_dag_fp64.md", LU_SOURCES),
+            "kernel": f"k_lu_dag<{nb},{ib}>",
+            "achieved_flops": "(2n^3/3)(1+ib/(2nb)) per factorization / its CUDA-event time"}
     return {"workload": f"tiled LU with tiled pairwise pivoting (Algorithm 3), {n}x{n} N(0,1), nb={nb}, ib={ib}, "
                         f"FP64 task graph", "value": world * ops / t / 1e9, "unit": UNIT, "ms_per_step": t * 1e3,
             "steps": reps, "pct_fp64_peak": 100.0 * (ops / t / 1e9) / fp64_peak,
             "algorithmic_gflops": (ops * (1.0 + ib / (2.0 * nb))) / t / 1e9,
             "zero_pivot_info": info, "solve_backward_error": be, "growth_U": growth,
-            "stability_n2048": sweep,
+            "stability_n2048": sweep, "roofline": roof,
             "timing": "CUDA events around the factorizations (layout conversion included), max over ranks"}
 
 
