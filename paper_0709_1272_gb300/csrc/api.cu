@@ -10,6 +10,7 @@
 
 #include "factor.h"
 #include "graph.cuh"
+#include "tile_mixed.cuh"
 
 namespace tqr {
 static std::atomic<unsigned long long> g_launches{0};
@@ -34,7 +35,7 @@ unsigned long long watchdog_ns_default()
 }  // namespace tqr
 
 namespace tqr {
-WsLayout make_layout(int64_t m, int64_t n, int nb, int ib, int h)
+WsLayout make_layout(int64_t m, int64_t n, int nb, int ib, int h, int precision)
 {
     WsLayout L{};
     L.m = m;
@@ -52,13 +53,15 @@ WsLayout make_layout(int64_t m, int64_t n, int nb, int ib, int h)
     L.off_tiles = 0;
     L.off_T = align256(tiles);
     L.off_T2 = L.off_T + align256(tst);
-    L.off_ctrl = L.off_T2 + (tree ? align256(tst) : 0);
+    // pre-split T^T operands: 128 x 128 tf32 hi + lo per tile pair (128 KB)
+    const size_t tfb = (precision == TILEQR_TF32 && nb == 128) ? tf_pairs(L.p, L.steps) * TF_BYTES : 0;
+    L.off_TF = L.off_T2 + (tree ? align256(tst) : 0);
+    L.off_TF2 = L.off_TF + align256(tfb);
+    L.off_ctrl = L.off_TF2 + (tree ? align256(tfb) : 0);
     L.off_cnt = L.off_ctrl + 256;
     size_t off = L.off_cnt + align256(g_ncounters(G) * sizeof(unsigned int));
-    unsigned long long kinds[6], caps[K_NKIND] = {0, 0, 0, 0};
-    g_count(G, kinds);
-    for (int t = 0; t < 6; t++)
-        caps[kind_prio(t)] += kinds[t];
+    unsigned long long caps[K_NKIND];
+    g_level_counts(G, caps);
     unsigned long long tot = 0;
     for (int t = 0; t < K_NKIND; t++) {
         L.cap[t] = (unsigned int)caps[t];
@@ -99,7 +102,7 @@ extern "C" int tileqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int p
         return -5;
     if (!bytes)
         return -6;
-    *bytes = make_layout(m, n, nb, ib).end;
+    *bytes = make_layout(m, n, nb, ib, 0, precision).end;
     return 0;
 }
 
@@ -115,7 +118,7 @@ extern "C" int tileqr_workspace_size_tree(int64_t m, int64_t n, int nb, int ib, 
         return -6;
     if (!bytes)
         return -7;
-    *bytes = make_layout(m, n, nb, ib, domain).end;
+    *bytes = make_layout(m, n, nb, ib, domain, precision).end;
     return 0;
 }
 
@@ -152,7 +155,7 @@ static int factor_impl(int64_t m, int64_t n, const double *A, int64_t lda, int n
         return TILEQR_ERR_UNSUPPORTED;
     if (precision == TILEQR_TF32 && (schedule != TILEQR_SCHED_DAG || !factor_mixed_supported(nb, ib)))
         return TILEQR_ERR_UNSUPPORTED;
-    const WsLayout L = make_layout(m, n, nb, ib, domain);
+    const WsLayout L = make_layout(m, n, nb, ib, domain, precision);
     const bool tree = L.H < L.p;
     if (tree && schedule != TILEQR_SCHED_DAG)
         return TILEQR_ERR_UNSUPPORTED;
@@ -183,7 +186,7 @@ static int factor_impl(int64_t m, int64_t n, const double *A, int64_t lda, int n
     if (cudaMemsetAsync(ws + L.off_ctrl, 0, L.end - L.off_ctrl, st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
     // T2 strips of rows that are not merged stay zero (documented contents)
-    if (tree && cudaMemsetAsync(ws + L.off_T2, 0, L.off_ctrl - L.off_T2, st) != cudaSuccess)
+    if (tree && cudaMemsetAsync(ws + L.off_T2, 0, L.off_TF - L.off_T2, st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
     if (m == 0 || n == 0)
         return 0;

@@ -56,7 +56,7 @@ struct BatchLayout {
     double flops;
 };
 
-BatchLayout batch_layout(int count, const int64_t *m, const int64_t *n, int nb, int ib,
+BatchLayout batch_layout(int count, const int64_t *m, const int64_t *n, int nb, int ib, int precision,
                          std::vector<MatInfo> *infos_out)
 {
     BatchLayout B{};
@@ -84,6 +84,10 @@ BatchLayout batch_layout(int count, const int64_t *m, const int64_t *n, int nb, 
         data += align256((size_t)mi.p * mi.q * nb * nb * sizeof(double));
         mi.T = (double *)(uintptr_t)data;
         data += align256((size_t)mi.p * mi.q * ib * nb * sizeof(double));
+        if (precision == TILEQR_TF32 && mi.steps > 0) {
+            mi.TF = (unsigned char *)(uintptr_t)data;
+            data += align256(tf_pairs(mi.p, mi.steps) * TF_BYTES);
+        }
         const double mm = (double)m[b], nn = (double)n[b];
         if (m[b] >= n[b])
             B.flops += 2.0 * nn * nn * (mm - nn / 3.0);
@@ -186,7 +190,7 @@ extern "C" int tileqr_batched_workspace_size(int count, const int64_t *m, const 
         return rc;
     if (bytes == nullptr)
         return -7;
-    *bytes = batch_layout(count, m, n, nb, ib, nullptr).end;
+    *bytes = batch_layout(count, m, n, nb, ib, precision, nullptr).end;
     return 0;
 }
 
@@ -202,7 +206,7 @@ extern "C" int tileqr_batched_prepare(int count, const int64_t *m, const int64_t
     if (out == nullptr)
         return -12;
     std::vector<MatInfo> infos;
-    const BatchLayout B = batch_layout(count, m, n, nb, ib, &infos);
+    const BatchLayout B = batch_layout(count, m, n, nb, ib, precision, &infos);
     if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < B.end)
         return TILEQR_ERR_WORKSPACE;
     char *ws = (char *)workspace;
@@ -215,6 +219,8 @@ extern "C" int tileqr_batched_prepare(int count, const int64_t *m, const int64_t
         infos[b].lda = lda[b];
         infos[b].tiles = (double *)(ws + B.off_data + (uintptr_t)infos[b].tiles);
         infos[b].T = (double *)(ws + B.off_data + (uintptr_t)infos[b].T);
+        if (precision == TILEQR_TF32 && infos[b].steps > 0)
+            infos[b].TF = (unsigned char *)(ws + B.off_data + (uintptr_t)infos[b].TF);
     }
     std::memset(out, 0, sizeof(*out));
     out->count = count;

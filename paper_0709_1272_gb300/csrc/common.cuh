@@ -58,7 +58,7 @@ struct SchedCtrl {
     int error;                    // TILEQR_ERR_* or 0
     int nonfinite;                // set by the layout kernel
     unsigned int trace_cursor;    // next free trace record
-    unsigned long long info;      // Cholesky: first non-positive pivot column + 1
+    unsigned long long info;      // Cholesky: first non-positive pivot column + 1; LU: ~(zero-pivot column)
     unsigned long long pad[10];
 };
 static_assert(sizeof(SchedCtrl) <= 256, "control block must fit its 256-byte slot");
@@ -66,17 +66,21 @@ static_assert(sizeof(SchedCtrl) <= 256, "control block must fit its 256-byte slo
 // Byte layout of the workspace (every piece 256-byte aligned).  H is the
 // domain size of the elimination tree (H == p: Algorithm 2's flat tree); a
 // tree layout adds the DTTQRT T strips (T2) and a second counter bank.
+// TF / TF2 (pre-split T^T operands, TILEQR_TF32 only) are empty otherwise.
 struct WsLayout {
     int64_t m, n;
     int nb, ib, p, q, steps, H;
-    size_t off_tiles, off_T, off_T2, off_ctrl, off_cnt, off_q[K_NKIND], end;
+    size_t off_tiles, off_T, off_T2, off_TF, off_TF2, off_ctrl, off_cnt, off_q[K_NKIND], end;
     unsigned int cap[K_NKIND];
     unsigned int total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-WsLayout make_layout(int64_t m, int64_t n, int nb, int ib, int h = 0);
+// precision TILEQR_TF32 (nb 128) adds, per tile pair (i, k), the full T^T of
+// the panel's reflectors as pre-split tf32 MMA operands (TF; TF2 for the
+// tree form's DTTQRT), used by the tensor-core update tasks.
+WsLayout make_layout(int64_t m, int64_t n, int nb, int ib, int h = 0, int precision = TILEQR_FP64);
 
 // ---------------------------------------------------------------------------
 // Global-memory access that bypasses L1: tiles are written by other SMs

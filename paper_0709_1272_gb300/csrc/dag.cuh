@@ -15,6 +15,9 @@ struct FactorArgs {
     double *tiles;
     double *T;
     double *T2;   // DTTQRT T strips (tree form only)
+    // mixed precision: the panels' full T^T as pre-split tf32 operands
+    // (TF_BYTES per tile pair; TF2 for DTTQRT), or nullptr
+    unsigned char *TF, *TF2;
     int p, q, steps;
     TGraph G;
 };
@@ -35,6 +38,11 @@ __device__ __forceinline__ double *strip2_ptr(const FactorArgs &F, int i, int k)
     return F.T2 + ((size_t)k * F.p + i) * (size_t)S * NB;
 }
 
+__device__ __forceinline__ unsigned char *tf_ptr(unsigned char *base, int p, int i, int k)
+{
+    return base + tf_index(p, i, k) * (size_t)TF_BYTES;
+}
+
 // Run the tile kernel of one task.  DTSQRT / DSSRFB eliminate row i into the
 // head of its domain (row k in Algorithm 2); DTTQRT / DTTMQR merge domain
 // head i into its partner head, reading only the upper triangle of tile
@@ -44,44 +52,74 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
                                          uint32_t tmem, uint64_t *mbar, uint32_t &mphase, int *err)
 {
     const TGraph &G = F.G;
+    unsigned char *smb = (unsigned char *)sm;
     switch (kind) {
     case K_GEQRT:
         task_geqrt<NB, S, MIXED>(sm, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
+        if constexpr (MIXED)
+            if (F.TF) {
+                __syncthreads();
+                mixed_build_tfull<S, VK_UNIT>(smb, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k),
+                                              tf_ptr(F.TF, F.p, i, k));
+            }
         break;
     case K_TSQRT:
         task_tsqrt<NB, S, MIXED, false>(sm, tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), k),
                                         tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
+        if constexpr (MIXED)
+            if (F.TF) {
+                __syncthreads();
+                mixed_build_tfull<S, VK_FULL>(smb, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k),
+                                              tf_ptr(F.TF, F.p, i, k));
+            }
         break;
     case K_TTQRT:
         task_tsqrt<NB, S, MIXED, true>(sm, tile_ptr<NB, S>(F, g_partner(G, k, i), k), tile_ptr<NB, S>(F, i, k),
                                        strip2_ptr<NB, S>(F, i, k));
+        if constexpr (MIXED)
+            if (F.TF2) {
+                __syncthreads();
+                mixed_build_tfull<S, VK_UPPER>(smb, tile_ptr<NB, S>(F, i, k), strip2_ptr<NB, S>(F, i, k),
+                                               tf_ptr(F.TF2, F.p, i, k));
+            }
         break;
     case K_LARFB:
-        if constexpr (MIXED)
-            task_update_mixed<S, VK_UNIT>((unsigned char *)sm, nullptr, tile_ptr<NB, S>(F, i, j),
-                                          tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), tmem, mbar, mphase,
-                                          err);
-        else
+        if constexpr (MIXED) {
+            if (F.TF)
+                task_update_mixed_tf<S, VK_UNIT>(smb, nullptr, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                                 tf_ptr(F.TF, F.p, i, k), tmem, mbar, mphase, err);
+            else
+                task_update_mixed<S, VK_UNIT>(smb, nullptr, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                              strip_ptr<NB, S>(F, i, k), tmem, mbar, mphase, err);
+        } else {
             task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
+        }
         break;
     case K_SSRFB: {
         double *top = tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), j);
-        if constexpr (MIXED)
-            task_update_mixed<S, VK_FULL>((unsigned char *)sm, top, tile_ptr<NB, S>(F, i, j),
-                                          tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), tmem, mbar, mphase,
-                                          err);
-        else
+        if constexpr (MIXED) {
+            if (F.TF)
+                task_update_mixed_tf<S, VK_FULL>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                                 tf_ptr(F.TF, F.p, i, k), tmem, mbar, mphase, err);
+            else
+                task_update_mixed<S, VK_FULL>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                              strip_ptr<NB, S>(F, i, k), tmem, mbar, mphase, err);
+        } else {
             task_ssrfb<NB, S>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
                               strip_ptr<NB, S>(F, i, k));
+        }
         break;
     }
     default: {   // K_TTMQR
         double *top = tile_ptr<NB, S>(F, g_partner(G, k, i), j);
-        if constexpr (MIXED)
-            task_update_mixed<S, VK_UPPER>((unsigned char *)sm, top, tile_ptr<NB, S>(F, i, j),
-                                           tile_ptr<NB, S>(F, i, k), strip2_ptr<NB, S>(F, i, k), tmem, mbar,
-                                           mphase, err);
-        else
+        if constexpr (MIXED) {
+            if (F.TF2)
+                task_update_mixed_tf<S, VK_UPPER>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                                  tf_ptr(F.TF2, F.p, i, k), tmem, mbar, mphase, err);
+            else
+                task_update_mixed<S, VK_UPPER>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                               strip2_ptr<NB, S>(F, i, k), tmem, mbar, mphase, err);
+        } else
             task_ssrfb<NB, S, FactorW<NB>::value, true>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
                                                         strip2_ptr<NB, S>(F, i, k));
         break;
@@ -95,6 +133,7 @@ struct DagCfg {
     static constexpr size_t SMEM = MIXED ? (F64Cfg<NB, S>::SMEM > (size_t)MixCfg<S>::SMEM ? F64Cfg<NB, S>::SMEM
                                                                                            : (size_t)MixCfg<S>::SMEM)
                                          : F64Cfg<NB, S>::SMEM;
+    static_assert(!MIXED || (SMEM >= TF_BUILD_SMEM && SMEM >= TF_UPDATE_SMEM), "full-T path fits");
     static constexpr int CTAS_PER_SM = MIXED ? 1 : F64Cfg<NB, S>::CTAS_PER_SM;
 };
 
@@ -170,6 +209,7 @@ namespace tqr {
 struct MatInfo {
     double *tiles;
     double *T;
+    unsigned char *TF;   // mixed precision: the panels' pre-split T^T operands (else nullptr)
     const double *A;
     int64_t m, n, lda;
     int p, q, steps, pad;
@@ -271,6 +311,8 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
                 s_F.tiles = mi.tiles;
                 s_F.T = mi.T;
                 s_F.T2 = nullptr;
+                s_F.TF = mi.TF;
+                s_F.TF2 = nullptr;
                 s_F.p = mi.p;
                 s_F.q = mi.q;
                 s_F.steps = mi.steps;

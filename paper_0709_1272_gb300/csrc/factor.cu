@@ -79,6 +79,7 @@ static int launch_factor_t(const WsLayout &L, char *ws, int schedule, int flags,
     F.tiles = (double *)(ws + L.off_tiles);
     F.T = (double *)(ws + L.off_T);
     F.T2 = (L.H < L.p) ? (double *)(ws + L.off_T2) : nullptr;
+    F.TF = F.TF2 = nullptr;
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;
@@ -169,6 +170,7 @@ static int launch_factor_dag_at_t(const WsLayout &L, double *tiles, double *T, c
     F.tiles = tiles;
     F.T = T;
     F.T2 = nullptr;
+    F.TF = F.TF2 = nullptr;
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;

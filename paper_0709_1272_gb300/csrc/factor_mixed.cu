@@ -28,6 +28,8 @@ static int launch_factor_mixed_t(const WsLayout &L, char *ws, int flags, cudaStr
     F.tiles = (double *)(ws + L.off_tiles);
     F.T = (double *)(ws + L.off_T);
     F.T2 = (L.H < L.p) ? (double *)(ws + L.off_T2) : nullptr;
+    F.TF = L.off_TF2 > L.off_TF ? (unsigned char *)(ws + L.off_TF) : nullptr;
+    F.TF2 = (F.T2 != nullptr && L.off_ctrl > L.off_TF2) ? (unsigned char *)(ws + L.off_TF2) : nullptr;
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;

@@ -31,11 +31,16 @@ namespace tqr {
 
 enum { K_TTQRT = 4, K_TTMQR = 5 };
 
-// Ready-queue level of a kind (the four priorities of Sec. 4; the tree's
-// merge joins the panel level, its update the row-update level).
-__host__ __device__ inline int kind_prio(int kind)
+// Ready-queue level of a task (the four priorities of Sec. 4; the tree's
+// merge joins the panel level, its update the row-update level).  An update
+// of column k+1 (j == k + 1) feeds the next step's panel, so it moves up one
+// level: otherwise it waits behind the whole backlog of its kind and delays
+// every later step.
+__host__ __device__ inline int kind_prio(int kind, int k = -1, int j = -2)
 {
-    return kind < 4 ? kind : (kind == K_TTQRT ? 1 : 2);
+    const int base = kind < 4 ? kind : (kind == K_TTQRT ? 1 : 2);
+    const bool update = kind == K_LARFB || kind == K_SSRFB || kind == K_TTMQR;
+    return (update && j == k + 1) ? base - 1 : base;
 }
 
 struct TGraph {
@@ -240,6 +245,23 @@ __host__ __device__ inline int ga_specific(const TGraph &G, int kind, int k, int
         out[s] = t[s];
     return n;
 }
+// Tasks per ready-queue level (kind_prio), for the write-once queues.
+__host__ inline void g_level_counts(const TGraph &G, unsigned long long caps[K_NKIND])
+{
+    for (int t = 0; t < K_NKIND; t++)
+        caps[t] = 0;
+    for (int k = 0; k < G.steps; k++) {
+        const unsigned long long P = G.p - k, nd = g_ndom(G, k), nq = G.q - k - 1;
+        const unsigned long long c1 = nq > 0 ? 1 : 0, rest = nq > 0 ? nq - 1 : 0;
+        caps[0] += nd;                              // GEQRT
+        caps[1] += (P - nd) + (nd - 1);             // TSQRT, TTQRT
+        caps[1] += nd * c1 + (nd - 1) * c1;         // LARFB, TTMQR on column k+1
+        caps[2] += nd * rest + (nd - 1) * rest;     // the other LARFB, TTMQR
+        caps[2] += (P - nd) * c1;                   // SSRFB on column k+1
+        caps[3] += (P - nd) * rest;                 // the other SSRFB
+    }
+}
+
 // Q itself (tileqr_apply_q) runs the same tasks in the reverse graph: a task
 // is released by its forward successors (count: ga_specific) and on
 // completion signals its forward predecessors, listed here:

@@ -39,15 +39,9 @@ static LuLayout lu_layout(int64_t n, int nb, int ib)
     L.off_ctrl = L.off_piv + align256(pp * nb * sizeof(int));
     L.off_cnt = L.off_ctrl + 256;
     size_t off = L.off_cnt + align256(pp * L.p * sizeof(unsigned int));
-    // queue levels = the QR kinds: GETRF 0, TSTRF 1, GESSM 2, SSSSM 3
-    unsigned long long cnt[K_NKIND] = {0, 0, 0, 0};
-    for (int k = 0; k < L.p; k++) {
-        const unsigned long long r = L.p - k - 1;
-        cnt[K_GEQRT] += 1;
-        cnt[K_TSQRT] += r;
-        cnt[K_LARFB] += r;
-        cnt[K_SSRFB] += r * r;
-    }
+    // queue levels of the QR kinds (GETRF as DGEQRT, TSTRF as DTSQRT, ...)
+    unsigned long long cnt[K_NKIND];
+    g_level_counts(make_graph(L.p, L.p, 0), cnt);
     unsigned long long tot = 0;
     for (int t = 0; t < K_NKIND; t++) {
         L.cap[t] = (unsigned int)cnt[t];

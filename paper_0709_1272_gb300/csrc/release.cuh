@@ -15,7 +15,7 @@ __device__ static void release_graph(const Queues &Q, const TGraph &G, int kind,
     for (int s = threadIdx.x; s < fan + nsp; s += NT) {
         const GTask t = s < fan ? g_fan_task(kind, k, i, s) : sp[s - fan];
         const int tk = g_kind(G, t.tt, t.k, t.i, t.j);
-        q_signal(Q, g_cidx(G, t.tt, t.k, t.i, t.j), g_ndeps(tk, t.k), kind_prio(tk),
+        q_signal(Q, g_cidx(G, t.tt, t.k, t.i, t.j), g_ndeps(tk, t.k), kind_prio(tk, t.k, t.j),
                  encode_task(t.k, t.i, t.j, t.tt));
     }
 }

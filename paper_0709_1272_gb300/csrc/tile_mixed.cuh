@@ -389,4 +389,362 @@ __device__ __noinline__ bool task_update_mixed(unsigned char *sm, double *Bt, do
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// The full b x b T of a panel's reflectors, for the update below.  With
+// H_1 ... H_b = I - V T V^T (T upper triangular), the inner blocks' T_l
+// (Sec. 3.2.3) are the diagonal blocks of T and the blocks above follow from
+// the compact-WY recursion
+//   T[0:j0, j0:j0+s] = -T[0:j0, 0:j0] (V[:, 0:j0]^T V[:, j0:j0+s]) T_l.
+// Applying I - V T^T V^T with it is the same operator as applying the inner
+// blocks in order.  The panel task forms T once per tile pair in FP32 on the
+// CUDA cores and stores T^T split into tf32 hi + lo, in the K-major operand
+// layout of the MMA (4 chunks of 32 K: hi 16 KB then lo 16 KB), so every
+// update task of that panel copies it as is.  V^T V is taken over the
+// reflectors' stored parts (the identity parts of distinct reflectors are
+// orthogonal).
+constexpr int TF_CHUNK_BYTES = 2 * 128 * 32 * 4;
+constexpr int TF_BYTES = 4 * TF_CHUNK_BYTES;
+// Operands are kept for the tile pairs (i, k), k < steps, i >= k only, in
+// step-major order: pair (i, k) is number k p - k (k - 1) / 2 + (i - k).
+__host__ __device__ inline size_t tf_pairs(int p, int steps)
+{
+    return (size_t)steps * p - (size_t)steps * (steps - 1) / 2;
+}
+__host__ __device__ inline size_t tf_index(int p, int i, int k)
+{
+    return (size_t)k * p - (size_t)k * (k - 1) / 2 + (size_t)(i - k);
+}
+constexpr size_t TF_BUILD_SMEM = (size_t)3 * 128 * 132 * 4;
+
+template <int S, int VK>
+__device__ __noinline__ void mixed_build_tfull(unsigned char *smb, const double *Vt, const double *Tt,
+                                               unsigned char *TFg)
+{
+    constexpr int NB = 128, LD = NB + 4;
+    float *Vs = (float *)smb;    // V [r][a]
+    float *Tf = Vs + NB * LD;    // T [a][a']; first V^T V above the block diagonal
+    float *Ys = Tf + NB * LD;    // merge scratch [a][c], ld LD
+    const int tid = threadIdx.x;
+    // V (16 loads in flight per thread) and a zeroed T
+    for (int it = 0; it < NB * NB / (16 * NT); it++) {
+        double v[16];
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            const int idx = tid + NT * (16 * it + e);
+            v[e] = mixed_v_elem<VK>(Vt, idx & (NB - 1), idx >> 7);
+        }
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            const int idx = tid + NT * (16 * it + e);
+            Vs[(idx & (NB - 1)) * LD + (idx >> 7)] = f64_to_f32_bits(v[e]);
+            Tf[(idx >> 7) * LD + (idx & (NB - 1))] = 0.0f;
+        }
+    }
+    __syncthreads();
+    // diagonal blocks T_l from the strip (S x NB, ld S)
+    {
+        constexpr int PER = S * NB / NT;
+        double t[PER];
+#pragma unroll
+        for (int e = 0; e < PER; e++)
+            t[e] = ldcg(Tt + tid + NT * e);
+#pragma unroll
+        for (int e = 0; e < PER; e++) {
+            const int idx = tid + NT * e, col = idx / S, b = idx - col * S, j0 = col - col % S;
+            if (j0 + b <= col)
+                Tf[(j0 + b) * LD + col] = f64_to_f32_bits(t[e]);
+        }
+    }
+    // V^T V above the block diagonal, 4 x 8 per thread: rows 4 ia.., columns 8 ic..
+    {
+        int u = tid, ia = -1, ic = -1;
+        for (int x = 0; x < NB / 4 && ia < 0; x++) {
+            const int first = ((4 * x) / S + 1) * (S / 8);
+            const int cnt = NB / 8 - first;
+            if (u < cnt) {
+                ia = x;
+                ic = first + u;
+            } else {
+                u -= cnt;
+            }
+        }
+        if (ia >= 0) {
+            float acc[4][8];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    acc[i][j] = 0.0f;
+#pragma unroll 4
+            for (int r = 0; r < NB; r++) {
+                const float4 a0 = *(const float4 *)(Vs + r * LD + 4 * ia);
+                const float4 c0 = *(const float4 *)(Vs + r * LD + 8 * ic);
+                const float4 c1 = *(const float4 *)(Vs + r * LD + 8 * ic + 4);
+                const float av[4] = {a0.x, a0.y, a0.z, a0.w};
+                const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 8; j++)
+                        acc[i][j] = fmaf(av[i], cv[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 8; j += 4)
+                    *(float4 *)(Tf + (4 * ia + i) * LD + 8 * ic + j) =
+                        make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
+        }
+    }
+    __syncthreads();
+    // Recursive doubling: adjacent blocks of size B (each with its final T)
+    // merge into one of size 2B through T12 = -T1 (G12 T2), the compact-WY
+    // rule for the product of two reflector blocks.  Each product: outputs
+    // B x B per merge, 2 x 4 of them per thread (rows 2 g.., columns 4 h..).
+    for (int B = S; B < NB; B *= 2) {
+        const int nmerge = NB / (2 * B);
+        const int gcols = B / 4, units = nmerge * (B / 2) * gcols;
+        // Y = G12 T2 (T2 upper: columns c use rows c2 <= c)
+        for (int u = tid; u < units; u += NT) {
+            const int mg = u / ((B / 2) * gcols), w = u - mg * (B / 2) * gcols;
+            const int g = w / gcols, h = w - g * gcols;
+            const int x = mg * 2 * B, r0 = x + 2 * g, c0 = x + B + 4 * h;
+            float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+            for (int k = x + B; k < c0 + 4; k++) {
+                const float g0 = Tf[r0 * LD + k], g1 = Tf[(r0 + 1) * LD + k];
+                const float4 t = *(const float4 *)(Tf + k * LD + c0);
+                acc[0][0] = fmaf(g0, t.x, acc[0][0]);
+                acc[0][1] = fmaf(g0, t.y, acc[0][1]);
+                acc[0][2] = fmaf(g0, t.z, acc[0][2]);
+                acc[0][3] = fmaf(g0, t.w, acc[0][3]);
+                acc[1][0] = fmaf(g1, t.x, acc[1][0]);
+                acc[1][1] = fmaf(g1, t.y, acc[1][1]);
+                acc[1][2] = fmaf(g1, t.z, acc[1][2]);
+                acc[1][3] = fmaf(g1, t.w, acc[1][3]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+                *(float4 *)(Ys + (r0 + i) * LD + c0) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        }
+        __syncthreads();
+        // T12 = -T1 Y (T1 upper: row r uses rows k >= r)
+        for (int u = tid; u < units; u += NT) {
+            const int mg = u / ((B / 2) * gcols), w = u - mg * (B / 2) * gcols;
+            const int g = w / gcols, h = w - g * gcols;
+            const int x = mg * 2 * B, r0 = x + 2 * g, c0 = x + B + 4 * h;
+            float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+            for (int k = r0; k < x + B; k++) {
+                const float t0 = Tf[r0 * LD + k], t1 = Tf[(r0 + 1) * LD + k];
+                const float4 y = *(const float4 *)(Ys + k * LD + c0);
+                acc[0][0] = fmaf(t0, y.x, acc[0][0]);
+                acc[0][1] = fmaf(t0, y.y, acc[0][1]);
+                acc[0][2] = fmaf(t0, y.z, acc[0][2]);
+                acc[0][3] = fmaf(t0, y.w, acc[0][3]);
+                acc[1][0] = fmaf(t1, y.x, acc[1][0]);
+                acc[1][1] = fmaf(t1, y.y, acc[1][1]);
+                acc[1][2] = fmaf(t1, y.z, acc[1][2]);
+                acc[1][3] = fmaf(t1, y.w, acc[1][3]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+                *(float4 *)(Tf + (r0 + i) * LD + c0) =
+                    make_float4(-acc[i][0], -acc[i][1], -acc[i][2], -acc[i][3]);
+        }
+        __syncthreads();
+    }
+    // T^T: element (row a, K = a') of chunk a' / 32, 4 consecutive K per store
+    for (int u = tid; u < NB * (NB / 4); u += NT) {
+        const int a = u & (NB - 1), ap = 4 * (u >> 7);
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+            v[e] = (ap + e <= a) ? Tf[(ap + e) * LD + a] : 0.0f;
+        float4 h, l;
+        tc::split_tf32(v[0], h.x, l.x);
+        tc::split_tf32(v[1], h.y, l.y);
+        tc::split_tf32(v[2], h.z, l.z);
+        tc::split_tf32(v[3], h.w, l.w);
+        const uint32_t off = (ap >> 5) * TF_CHUNK_BYTES + tc::kmajor_off(a, ap & 31, 32);
+        __stcg((float4 *)(TFg + off), h);
+        __stcg((float4 *)(TFg + off + TF_CHUNK_BYTES / 2), l);
+    }
+}
+
+// The update with the panel's full T (pre-split by mixed_build_tfull):
+//   P = V^T C;  W = T^T (B + P);  B -= W;  D = V W;  C -= D
+// three 128 x 128 x 128 3xTF32 products with FP32 accumulation in tensor
+// memory (P and D in columns 0..127, W in 128..255), each in 4 K-chunks of
+// 32 on double-buffered operands.  Shared memory: R1 (128 KB) holds the two
+// operand sets of the P rounds, then all 4 chunks of the B operand of the W
+// and D products (Y = B + P, then W^T: row c, K = reflector); R2 (64 KB) the
+// double-buffered A operand of those (T^T chunks, then V chunks).  Returns
+// false on a tensor-core wait timeout (an error is recorded).
+constexpr size_t TF_UPDATE_SMEM = 192 * 1024;
+
+template <int S, int VK>
+__device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt, double *Ct, const double *Vt,
+                                                  const unsigned char *TFg, uint32_t tmem, uint64_t *mbar,
+                                                  uint32_t &phase, int *err)
+{
+    constexpr int NB = 128, KC = 32, OPB = NB * KC * 4, R2 = 8 * OPB;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = tc::smem_addr(sm);
+    const uint32_t idesc = tc::idesc_tf32(128, 128);
+    const uint32_t SBO = KC * 32, LBO = 128;
+    bool ok = true;
+    auto fail = [&]() {
+        if (tid == 0)
+            atomicCAS(err, 0, TILEQR_ERR_TIMEOUT);
+        return false;
+    };
+    // 3xTF32 products of one K chunk: A (hi at a, lo at a + OPB) x B (likewise)
+    auto mma_chunk = [&](uint32_t d, uint32_t a, uint32_t b, bool first) {
+        for (int ks = 0; ks < KC / 8; ks++) {
+            const uint32_t o = ks * 256;
+            const uint64_t ah = tc::smem_desc(a + o, LBO, SBO), al = tc::smem_desc(a + OPB + o, LBO, SBO);
+            const uint64_t bh = tc::smem_desc(b + o, LBO, SBO), bl = tc::smem_desc(b + OPB + o, LBO, SBO);
+            tc::mma_tf32(d, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
+            tc::mma_tf32(d, ah, bl, idesc, 1u);
+            tc::mma_tf32(d, al, bh, idesc, 1u);
+        }
+    };
+    const int a_row = 32 * (warp & 3) + lane;   // this thread's tensor-memory lane
+    const int cbase = (warp >> 2) * 64;
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    const int kq = warp & 3;                    // K chunk of this thread's reflector rows
+
+    // ---- P = V^T C: A = V^T (row = reflector, K = tile row), B = C^T (row =
+    // column); sets at 0 and 4 OPB
+    for (int rr = 0; rr < NB / KC; rr++) {
+        const int b = rr & 1, r0 = rr * KC, so = b * 4 * OPB;
+        if (rr >= 2)
+            ok &= mixed_wait(mbar, phase, b);
+        double v[4][4], c[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+            const int u = tid + x * NT, j = u & 7, m = u >> 3, r = r0 + 4 * j;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                v[x][e] = mixed_v_elem<VK>(Vt, r + e, m);
+                c[x][e] = ldcg(Ct + (size_t)m * NB + r + e);
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+            const int u = tid + x * NT, j = u & 7, m = u >> 3;
+            const uint32_t off = tc::kmajor_off(m, 4 * j, KC);
+            store_split4(sm, so, so + OPB, off, f64_to_f32_bits(v[x][0]), f64_to_f32_bits(v[x][1]),
+                         f64_to_f32_bits(v[x][2]), f64_to_f32_bits(v[x][3]));
+            store_split4(sm, so + 2 * OPB, so + 3 * OPB, off, f64_to_f32_bits(c[x][0]), f64_to_f32_bits(c[x][1]),
+                         f64_to_f32_bits(c[x][2]), f64_to_f32_bits(c[x][3]));
+        }
+        mixed_issue(&mbar[b], [&]() { mma_chunk(tmem, sbase + so, sbase + so + 2 * OPB, rr == 0); });
+    }
+    ok &= mixed_wait(mbar, phase, 0);
+    ok &= mixed_wait(mbar, phase, 1);
+    if (!__syncthreads_and(ok))
+        return fail();
+
+    // ---- Y = P + B into R1 as the B operand of W = T^T Y (row c, K = reflector)
+    for (int h = 0; h < 2; h++) {
+        const int c0 = cbase + 32 * h;
+        float v[32];
+        double bv[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+            bv[j] = Bt ? ldcg(Bt + (size_t)(c0 + j) * NB + a_row) : 0.0;
+        tc::tmem_ld32(tmem + lane_off + c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            float hi, lo;
+            tc::split_tf32(v[j] + (Bt ? f64_to_f32_bits(bv[j]) : 0.0f), hi, lo);
+            const uint32_t off = kq * 2 * OPB + tc::kmajor_off(c0 + j, lane, KC);
+            *(float *)(sm + off) = hi;
+            *(float *)(sm + off + OPB) = lo;
+        }
+    }
+    // ---- W = T^T Y: A = T^T chunks copied from the panel's pre-split operand
+    for (int kk = 0; kk < NB / KC; kk++) {
+        const int b = kk & 1;
+        if (kk >= 2)
+            ok &= mixed_wait(mbar, phase, b);
+        const float4 *src = (const float4 *)(TFg + (size_t)kk * TF_CHUNK_BYTES);
+        float4 *dst = (float4 *)(sm + R2 + b * 2 * OPB);
+        for (int e = tid; e < TF_CHUNK_BYTES / 16; e += NT)
+            dst[e] = __ldcg(src + e);
+        mixed_issue(&mbar[b],
+                    [&]() { mma_chunk(tmem + 128, sbase + R2 + b * 2 * OPB, sbase + kk * 2 * OPB, kk == 0); });
+    }
+    ok &= mixed_wait(mbar, phase, 0);
+    ok &= mixed_wait(mbar, phase, 1);
+    if (!__syncthreads_and(ok))
+        return fail();
+
+    // ---- B -= W (FP64); W^T into R1 as the B operand of D = V W
+    for (int h = 0; h < 2; h++) {
+        const int c0 = cbase + 32 * h;
+        float w[32];
+        tc::tmem_ld32(tmem + 128 + lane_off + c0, w);
+        if (Bt) {
+            double bv[32];
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                bv[j] = ldcg(Bt + (size_t)(c0 + j) * NB + a_row);
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                stcg(Bt + (size_t)(c0 + j) * NB + a_row, bv[j] - f32_to_f64_bits(w[j]));
+        }
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            float hi, lo;
+            tc::split_tf32(w[j], hi, lo);
+            const uint32_t off = kq * 2 * OPB + tc::kmajor_off(c0 + j, lane, KC);
+            *(float *)(sm + off) = hi;
+            *(float *)(sm + off + OPB) = lo;
+        }
+    }
+    // ---- D = V W: A = V (row = tile row, K = reflector) chunks staged in R2
+    for (int kk = 0; kk < NB / KC; kk++) {
+        const int b = kk & 1, k0 = kk * KC, ao = R2 + b * 2 * OPB;
+        if (kk >= 2)
+            ok &= mixed_wait(mbar, phase, b);
+        double v[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+            const int u = tid + x * NT, r = u & (NB - 1), j = u >> 7, k = k0 + 4 * j;
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                v[x][e] = mixed_v_elem<VK>(Vt, r, k + e);
+        }
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+            const int u = tid + x * NT, r = u & (NB - 1), j = u >> 7;
+            store_split4(sm, ao, ao + OPB, tc::kmajor_off(r, 4 * j, KC), f64_to_f32_bits(v[x][0]),
+                         f64_to_f32_bits(v[x][1]), f64_to_f32_bits(v[x][2]), f64_to_f32_bits(v[x][3]));
+        }
+        mixed_issue(&mbar[b], [&]() { mma_chunk(tmem, sbase + ao, sbase + kk * 2 * OPB, kk == 0); });
+    }
+    ok &= mixed_wait(mbar, phase, 0);
+    ok &= mixed_wait(mbar, phase, 1);
+    if (!__syncthreads_and(ok))
+        return fail();
+
+    // ---- C -= D (FP64), row = tensor-memory lane
+    for (int h = 0; h < 2; h++) {
+        const int c0 = cbase + 32 * h;
+        float v[32];
+        double old[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+            old[j] = ldcg(Ct + (size_t)(c0 + j) * NB + a_row);
+        tc::tmem_ld32(tmem + lane_off + c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+            stcg(Ct + (size_t)(c0 + j) * NB + a_row, old[j] - f32_to_f64_bits(v[j]));
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    return true;
+}
+
 }  // namespace tqr

@@ -152,3 +152,35 @@ def test_task_counts_match_the_workspace_queues(tq):
             exp[3] += (P - nd) * nq
             exp[5] += (nd - 1) * nq
         assert list(kinds) == exp
+
+
+def _level(kind, k, j):
+    """Ready-queue level of a task: the kind's level (tree merge with the
+    panels, tree update with the row updates), one level up for an update of
+    column k+1, which feeds the next step's panel."""
+    base = kind if kind < 4 else (1 if kind == 4 else 2)
+    return base - 1 if (kind in (2, 3, 5) and j == k + 1) else base
+
+
+def _level_counts_closed_form(p, q, h):
+    # the closed form the library sizes its write-once queues with
+    H = p if (h <= 0 or h > p) else h
+    caps = [0] * 4
+    for k in range(min(p, q)):
+        P, nq = p - k, q - k - 1
+        nd = -(-P // H)
+        c1, rest = (1, nq - 1) if nq > 0 else (0, 0)
+        caps[0] += nd
+        caps[1] += (P - nd) + (nd - 1) + nd * c1 + (nd - 1) * c1
+        caps[2] += nd * rest + (nd - 1) * rest + (P - nd) * c1
+        caps[3] += (P - nd) * rest
+    return caps
+
+
+@pytest.mark.parametrize("m,n,nb,h", CASES + [(128 * 40, 128 * 40, 128, 0), (128 * 40, 128 * 40, 128, 8)])
+def test_queue_levels_match_the_enumerated_graph(tq, m, n, nb, h):
+    tasks, _, _, _ = tq.tileqr_task_graph(m, n, nb, h, 0)
+    cnt = [0] * 4
+    for kind, i, j, k in tasks:
+        cnt[_level(int(kind), int(k), int(j))] += 1
+    assert cnt == _level_counts_closed_form(-(-m // nb), -(-n // nb), h)
