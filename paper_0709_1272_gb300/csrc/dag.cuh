@@ -16,7 +16,7 @@ struct FactorArgs {
     double *T;
     double *T2;   // DTTQRT T strips (tree form only)
     // mixed precision: the panels' full T^T as pre-split tf32 operands
-    // (TF_BYTES per tile pair; TF2 for DTTQRT), or nullptr
+    // (TF_BYTES per tile pair; TF2 for DTTQRT); unused in FP64
     unsigned char *TF, *TF2;
     int p, q, steps;
     TGraph G;
@@ -57,7 +57,7 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
     case K_GEQRT:
         task_geqrt<NB, S, MIXED>(sm, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
         if constexpr (MIXED)
-            if (F.TF) {
+            {
                 __syncthreads();
                 mixed_build_tfull<S, VK_UNIT>(smb, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k),
                                               tf_ptr(F.TF, F.p, i, k));
@@ -67,7 +67,7 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
         task_tsqrt<NB, S, MIXED, false>(sm, tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), k),
                                         tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
         if constexpr (MIXED)
-            if (F.TF) {
+            {
                 __syncthreads();
                 mixed_build_tfull<S, VK_FULL>(smb, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k),
                                               tf_ptr(F.TF, F.p, i, k));
@@ -77,7 +77,7 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
         task_tsqrt<NB, S, MIXED, true>(sm, tile_ptr<NB, S>(F, g_partner(G, k, i), k), tile_ptr<NB, S>(F, i, k),
                                        strip2_ptr<NB, S>(F, i, k));
         if constexpr (MIXED)
-            if (F.TF2) {
+            {
                 __syncthreads();
                 mixed_build_tfull<S, VK_UPPER>(smb, tile_ptr<NB, S>(F, i, k), strip2_ptr<NB, S>(F, i, k),
                                                tf_ptr(F.TF2, F.p, i, k));
@@ -85,12 +85,8 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
         break;
     case K_LARFB:
         if constexpr (MIXED) {
-            if (F.TF)
-                task_update_mixed_tf<S, VK_UNIT>(smb, nullptr, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                                 tf_ptr(F.TF, F.p, i, k), tmem, mbar, mphase, err);
-            else
-                task_update_mixed<S, VK_UNIT>(smb, nullptr, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                              strip_ptr<NB, S>(F, i, k), tmem, mbar, mphase, err);
+            task_update_mixed_tf<S, VK_UNIT>(smb, nullptr, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                             tf_ptr(F.TF, F.p, i, k), tmem, mbar, mphase, err);
         } else {
             task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
         }
@@ -98,12 +94,8 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
     case K_SSRFB: {
         double *top = tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), j);
         if constexpr (MIXED) {
-            if (F.TF)
-                task_update_mixed_tf<S, VK_FULL>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                                 tf_ptr(F.TF, F.p, i, k), tmem, mbar, mphase, err);
-            else
-                task_update_mixed<S, VK_FULL>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                              strip_ptr<NB, S>(F, i, k), tmem, mbar, mphase, err);
+            task_update_mixed_tf<S, VK_FULL>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                             tf_ptr(F.TF, F.p, i, k), tmem, mbar, mphase, err);
         } else {
             task_ssrfb<NB, S>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
                               strip_ptr<NB, S>(F, i, k));
@@ -113,12 +105,8 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
     default: {   // K_TTMQR
         double *top = tile_ptr<NB, S>(F, g_partner(G, k, i), j);
         if constexpr (MIXED) {
-            if (F.TF2)
-                task_update_mixed_tf<S, VK_UPPER>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                                  tf_ptr(F.TF2, F.p, i, k), tmem, mbar, mphase, err);
-            else
-                task_update_mixed<S, VK_UPPER>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                               strip2_ptr<NB, S>(F, i, k), tmem, mbar, mphase, err);
+            task_update_mixed_tf<S, VK_UPPER>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                              tf_ptr(F.TF2, F.p, i, k), tmem, mbar, mphase, err);
         } else
             task_ssrfb<NB, S, FactorW<NB>::value, true>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
                                                         strip2_ptr<NB, S>(F, i, k));
@@ -130,10 +118,10 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
 // Dynamic shared memory and CTAs per SM of the persistent kernel.
 template <int NB, int S, bool MIXED>
 struct DagCfg {
-    static constexpr size_t SMEM = MIXED ? (F64Cfg<NB, S>::SMEM > (size_t)MixCfg<S>::SMEM ? F64Cfg<NB, S>::SMEM
-                                                                                           : (size_t)MixCfg<S>::SMEM)
+    static constexpr size_t MIX = TF_BUILD_SMEM > TF_UPDATE_SMEM ? TF_BUILD_SMEM : TF_UPDATE_SMEM;
+    static constexpr size_t SMEM = MIXED ? (F64Cfg<NB, S>::SMEM > MIX ? F64Cfg<NB, S>::SMEM : MIX)
                                          : F64Cfg<NB, S>::SMEM;
-    static_assert(!MIXED || (SMEM >= TF_BUILD_SMEM && SMEM >= TF_UPDATE_SMEM), "full-T path fits");
+    static_assert(SMEM <= 232448, "shared memory budget");
     static constexpr int CTAS_PER_SM = MIXED ? 1 : F64Cfg<NB, S>::CTAS_PER_SM;
 };
 
@@ -149,7 +137,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_fac
     if (MIXED) {
         // one tensor-memory allocation and one mbarrier per persistent CTA
         if ((threadIdx.x >> 5) == 0)
-            tc::tmem_alloc(&s_tmem, MixCfg<S>::TMEM_COLS);
+            tc::tmem_alloc(&s_tmem, MIX_TMEM_COLS);
         if (threadIdx.x == 0)
             for (int b = 0; b < 2; b++)
                 tc::mbar_init(&s_mbar[b], 1);
@@ -193,7 +181,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_fac
         tc::fence_before_sync();
         __syncthreads();
         if ((threadIdx.x >> 5) == 0)
-            tc::tmem_dealloc(tmem, MixCfg<S>::TMEM_COLS);
+            tc::tmem_dealloc(tmem, MIX_TMEM_COLS);
     }
 }
 
@@ -282,7 +270,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
     uint32_t tmem = 0, mphase = 0;
     if (MIXED) {
         if ((threadIdx.x >> 5) == 0)
-            tc::tmem_alloc(&s_tmem, MixCfg<S>::TMEM_COLS);
+            tc::tmem_alloc(&s_tmem, MIX_TMEM_COLS);
         if (threadIdx.x == 0)
             for (int b = 0; b < 2; b++)
                 tc::mbar_init(&s_mbar[b], 1);
@@ -343,7 +331,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
         tc::fence_before_sync();
         __syncthreads();
         if ((threadIdx.x >> 5) == 0)
-            tc::tmem_dealloc(tmem, MixCfg<S>::TMEM_COLS);
+            tc::tmem_dealloc(tmem, MIX_TMEM_COLS);
     }
 }
 

@@ -1,6 +1,7 @@
 // factor_mixed.cu -- the mixed-precision build of the persistent task-graph
-// kernel (TILEQR_TF32): DLARFB / DSSRFB as 3xTF32 products on the tcgen05
-// tensor cores with FP32 accumulation, DGEQRT / DTSQRT in FP64 (nb = 128).
+// kernel (TILEQR_TF32): DLARFB / DSSRFB / DTTMQR as 3xTF32 products on the
+// tcgen05 tensor cores with FP32 accumulation, with the panels' full T formed
+// once per panel; DGEQRT / DTSQRT / DTTQRT in FP64 (nb = 128).
 #include "dag.cuh"
 #include "factor.h"
 
@@ -30,6 +31,9 @@ static int launch_factor_mixed_t(const WsLayout &L, char *ws, int flags, cudaStr
     F.T2 = (L.H < L.p) ? (double *)(ws + L.off_T2) : nullptr;
     F.TF = L.off_TF2 > L.off_TF ? (unsigned char *)(ws + L.off_TF) : nullptr;
     F.TF2 = (F.T2 != nullptr && L.off_ctrl > L.off_TF2) ? (unsigned char *)(ws + L.off_TF2) : nullptr;
+    // the tensor-core updates need the panels' T^T operands (a TILEQR_TF32 layout)
+    if (F.TF == nullptr || (F.T2 != nullptr && F.TF2 == nullptr))
+        return TILEQR_ERR_WORKSPACE;
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;

@@ -1,18 +1,15 @@
-// tile_mixed.cuh -- mixed-precision DSSRFB / DLARFB on the tcgen05 tensor
-// cores (nb = 128), for the TILEQR_TF32 precision mode.
+// tile_mixed.cuh -- mixed-precision DSSRFB / DLARFB / DTTMQR on the tcgen05
+// tensor cores (nb = 128), for the TILEQR_TF32 precision mode.
 //
-// The tiles stay FP64.  One update task computes, with V the task's
-// reflectors (b x b: the full DTSQRT tile, or the unit-lower DGEQRT tile),
-// T_l its s x s T blocks, B the top tile's rows (DSSRFB only) and C the
-// updated tile:
-//   P = V^T C,  G = V^T V                       (tcgen05, K = 128)
-//   W_l = T_l^T (B_l + P_l - G_{l,<l} W_{<l}),  l = 0..t-1   (FP32, CUDA cores)
-//   B -= W (FP64),  D = V W (tcgen05),  C -= D (FP64)
-// This is the inner-blocked application of Sec. 3.2.3 (blocks applied in
-// order, each with its own T_l) reassociated so that the block recurrence
-// only touches s x b panels: Y_l = B_l + V_l^T (C - sum_{l'<l} V_l' W_l')
-// = B_l + P_l - sum_{l'<l} (V_l^T V_l') W_l'.  For DSSRFB, V = [I; V_A]
-// and the identity parts of distinct blocks are orthogonal, so G = V_A^T V_A.
+// The tiles stay FP64.  The panel task (DGEQRT / DTSQRT / DTTQRT, in FP64)
+// also forms the full b x b T of its reflectors once (mixed_build_tfull) and
+// stores T^T as pre-split tf32 operands.  One update task then computes,
+// with V the task's reflectors (b x b: the full DTSQRT tile, the unit-lower
+// DGEQRT tile or the upper DTTQRT triangle), B the top tile (DSSRFB /
+// DTTMQR only) and C the updated tile:
+//   P = V^T C;  W = T^T (B + P);  B -= W;  D = V W;  C -= D
+// the application of the panel's reflectors, the same operator as the inner
+// blocks of Sec. 3.2.3 applied in order (T's diagonal blocks are the T_l).
 //
 // Products: 3xTF32 (x = hi + lo, hi*hi + hi*lo + lo*hi), FP32 accumulation
 // in tensor memory.  FP64 <-> FP32 conversions use integer bit operations
@@ -23,31 +20,7 @@
 
 namespace tqr {
 
-template <int S>
-struct MixCfg {
-    static constexpr int NB = 128;
-    static constexpr int KC = 32;                    // K extent of a staged operand chunk
-    static constexpr int OPB = NB * KC * 4;          // one 128 x 32 tf32 operand: 16 KB
-    static constexpr int OPSET = 4 * OPB;            // A hi, A lo, B hi, B lo: 64 KB
-    static constexpr int LDF = NB + 1;               // ld of the FP32 P / W panel (conflict-free columns)
-    static constexpr int LDG = NB + 4;               // ld of G (rows 16-byte aligned: float4 reads)
-    static constexpr int OFF_AHI = 0;
-    static constexpr int OFF_ALO = OPB;
-    static constexpr int OFF_BHI = 2 * OPB;
-    static constexpr int OFF_BLO = 3 * OPB;
-    static constexpr int OFF_PW = OPSET;                            // P + B, then W (FP32)
-    static constexpr int OFF_G = OFF_PW + NB * LDF * 4;             // G (FP32)
-    static constexpr int OFF_T = OFF_G + NB * LDG * 4;              // T strip (FP32, s x 128)
-    static constexpr int SMEM = OFF_T + S * NB * 4;
-    static constexpr int TMEM_COLS = 256;                           // P / D at 0, G at 128
-    static_assert(S == 16 || S == 32, "ib 16 or 32");
-    static_assert(SMEM <= 232448, "shared memory budget");
-    // the second operand set of the double-buffered MMA rounds: the P / W area
-    // while P is still in tensor memory (phase 1), the G area once the block
-    // recurrence is done (phase 3)
-    static_assert(NB * LDF * 4 >= OPSET && NB * LDG * 4 >= OPSET, "second operand set fits");
-    static_assert(OFF_PW % 128 == 0 && OFF_G % 128 == 0, "operand sets 128-byte aligned");
-};
+constexpr int MIX_TMEM_COLS = 256;   // P / D in columns 0..127, W in 128..255
 
 // FP64 -> FP32 with integer operations: exponent rebias, mantissa funnel
 // shift, round half away from zero; |x| below the FP32 normal range flushes
@@ -139,254 +112,6 @@ __device__ __forceinline__ bool mixed_wait(uint64_t *mbar, uint32_t &phase, int 
     phase ^= 1u << b;
     tc::fence_after_sync();
     return ok;
-}
-
-// Mixed DSSRFB (Bt != nullptr, V = full DTSQRT tile), DLARFB (Bt ==
-// nullptr, V = unit-lower DGEQRT tile) or DTTMQR (Bt != nullptr, V = upper
-// DTTQRT triangle: V = [I; V_B] as for DSSRFB, so G = V_B^T V_B again) on
-// FP64 tiles.  mbar: two mbarriers (one per operand set).  Returns false on a
-// tensor-core wait timeout (an error is recorded; the tile contents are then
-// undefined); the outcome is the same in every thread.
-template <int S, int VK>
-__device__ __noinline__ bool task_update_mixed(unsigned char *sm, double *Bt, double *Ct, const double *Vt,
-                                               const double *Tt, uint32_t tmem, uint64_t *mbar, uint32_t &phase,
-                                               int *err)
-{
-    using M = MixCfg<S>;
-    constexpr int NB = 128, KC = M::KC, LDF = M::LDF, LDG = M::LDG, T_ = NB / S;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    float *PW = (float *)(sm + M::OFF_PW);
-    float *GS = (float *)(sm + M::OFF_G);
-    float *TS = (float *)(sm + M::OFF_T);
-    const uint32_t sbase = tc::smem_addr(sm);
-    const uint32_t idesc = tc::idesc_tf32(128, 128);
-    const uint32_t SBO = KC * 32, LBO = 128;
-    bool ok = true;
-
-    // ---- phase 1: P = V^T C and G = V^T V, K (tile rows) in 4 chunks of 32.
-    // Unit u of a chunk: operand row m (reflector m for A, tile column m for
-    // B), K = tile rows r0 + 4j .. +3; 8 lanes cover 32 contiguous doubles of
-    // one column.  All loads of a thread are issued before any conversion.
-    {
-        const int set_off[2] = {0, M::OFF_PW};
-        for (int rr = 0; rr < NB / KC; rr++) {
-            const int b = rr & 1, r0 = rr * KC;
-            if (rr >= 2)
-                ok &= mixed_wait(mbar, phase, b);   // set b was read by round rr - 2
-            double v[4][4], c[4][4];
-#pragma unroll
-            for (int x = 0; x < 4; x++) {
-                const int u = tid + x * NT, j = u & 7, m = u >> 3, r = r0 + 4 * j;
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    v[x][e] = mixed_v_elem<VK>(Vt, r + e, m);
-                    c[x][e] = ldcg(Ct + (size_t)m * NB + r + e);
-                }
-            }
-#pragma unroll
-            for (int x = 0; x < 4; x++) {
-                const int u = tid + x * NT, j = u & 7, m = u >> 3;
-                const uint32_t off = tc::kmajor_off(m, 4 * j, KC);
-                store_split4(sm, set_off[b] + M::OFF_AHI, set_off[b] + M::OFF_ALO, off, f64_to_f32_bits(v[x][0]),
-                             f64_to_f32_bits(v[x][1]), f64_to_f32_bits(v[x][2]), f64_to_f32_bits(v[x][3]));
-                store_split4(sm, set_off[b] + M::OFF_BHI, set_off[b] + M::OFF_BLO, off, f64_to_f32_bits(c[x][0]),
-                             f64_to_f32_bits(c[x][1]), f64_to_f32_bits(c[x][2]), f64_to_f32_bits(c[x][3]));
-            }
-            const uint32_t base = sbase + set_off[b];
-            mixed_issue(&mbar[b], [&]() {
-                for (int ks = 0; ks < KC / 8; ks++) {
-                    const uint32_t o = ks * 256;
-                    const uint64_t ah = tc::smem_desc(base + M::OFF_AHI + o, LBO, SBO);
-                    const uint64_t al = tc::smem_desc(base + M::OFF_ALO + o, LBO, SBO);
-                    const uint64_t bh = tc::smem_desc(base + M::OFF_BHI + o, LBO, SBO);
-                    const uint64_t bl = tc::smem_desc(base + M::OFF_BLO + o, LBO, SBO);
-                    const uint32_t acc = (rr | ks) ? 1u : 0u;
-                    tc::mma_tf32(tmem, ah, bh, idesc, acc);          // P
-                    tc::mma_tf32(tmem, ah, bl, idesc, 1u);
-                    tc::mma_tf32(tmem, al, bh, idesc, 1u);
-                    tc::mma_tf32(tmem + 128, ah, ah, idesc, acc);    // G
-                    tc::mma_tf32(tmem + 128, ah, al, idesc, 1u);
-                    tc::mma_tf32(tmem + 128, al, ah, idesc, 1u);
-                }
-            });
-        }
-        ok &= mixed_wait(mbar, phase, 0);
-        ok &= mixed_wait(mbar, phase, 1);
-        ok = __syncthreads_and(ok);
-        if (!ok) {
-            if (tid == 0)
-                atomicCAS(err, 0, TILEQR_ERR_TIMEOUT);
-            return false;
-        }
-    }
-
-    // ---- phase 2: P + B and G to shared memory (thread = TMEM lane = row),
-    // the T strip to FP32, then the block recurrence for W.  B is read here
-    // once, coalesced (a warp reads 32 consecutive rows of one column).
-    {
-        const int row = 32 * (warp & 3) + lane;
-        const int cbase = (warp >> 2) * 64;
-        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
-        for (int h = 0; h < 2; h++) {
-            const int c0 = cbase + 32 * h;
-            float v[32];
-            double bv[32];
-#pragma unroll
-            for (int j = 0; j < 32; j++)
-                bv[j] = Bt ? ldcg(Bt + (size_t)(c0 + j) * NB + row) : 0.0;
-            tc::tmem_ld32(tmem + lane_off + c0, v);
-#pragma unroll
-            for (int j = 0; j < 32; j++)
-                PW[row * LDF + c0 + j] = v[j] + (Bt ? f64_to_f32_bits(bv[j]) : 0.0f);
-            tc::tmem_ld32(tmem + 128 + lane_off + c0, v);
-#pragma unroll
-            for (int j = 0; j < 32; j++)
-                GS[row * LDG + c0 + j] = v[j];
-        }
-    }
-    for (int idx = tid; idx < S * NB; idx += NT)
-        TS[idx] = f64_to_f32_bits(ldcg(Tt + idx));
-    tc::fence_before_sync();
-    __syncthreads();
-
-    {
-        // thread (column c, half of the block's rows); G rows are read as
-        // float4 broadcasts (one address per warp)
-        const int c = tid & (NB - 1);
-        const int half = tid >> 7;
-        constexpr int HR = S / 2;   // rows of a block per thread
-        for (int l = 0; l < T_; l++) {
-            const int a0 = l * S + half * HR;
-            const int kdone = l * S;   // rows of W already final
-            float y[HR];
-#pragma unroll
-            for (int i = 0; i < HR; i++)
-                y[i] = PW[(a0 + i) * LDF + c];
-            for (int ap = 0; ap < kdone; ap += 4) {
-                const float w0 = PW[(ap + 0) * LDF + c], w1 = PW[(ap + 1) * LDF + c];
-                const float w2 = PW[(ap + 2) * LDF + c], w3 = PW[(ap + 3) * LDF + c];
-#pragma unroll
-                for (int i = 0; i < HR; i++) {
-                    const float4 g = *(const float4 *)(GS + (a0 + i) * LDG + ap);
-                    y[i] = fmaf(-g.x, w0, y[i]);
-                    y[i] = fmaf(-g.y, w1, y[i]);
-                    y[i] = fmaf(-g.z, w2, y[i]);
-                    y[i] = fmaf(-g.w, w3, y[i]);
-                }
-            }
-            // Y_l rows go into PW (P_l + B_l is consumed), then W_l = T_l^T Y_l
-#pragma unroll
-            for (int i = 0; i < HR; i++)
-                PW[(a0 + i) * LDF + c] = y[i];
-            __syncthreads();
-            float w[HR];
-#pragma unroll
-            for (int i = 0; i < HR; i++) {
-                const int a = half * HR + i;   // row within the block
-                float acc = 0.0f;
-                for (int a2 = 0; a2 <= a; a2++)
-                    acc = fmaf(TS[(l * S + a) * S + a2], PW[(l * S + a2) * LDF + c], acc);
-                w[i] = acc;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < HR; i++)
-                PW[(a0 + i) * LDF + c] = w[i];
-            __syncthreads();
-        }
-    }
-
-    // B -= W (FP64), coalesced: thread = row, 64 columns
-    if (Bt) {
-        const int row = 32 * (warp & 3) + lane;
-        const int cbase = (warp >> 2) * 64;
-        for (int h = 0; h < 2; h++) {
-            const int c0 = cbase + 32 * h;
-            double bv[32];
-#pragma unroll
-            for (int j = 0; j < 32; j++)
-                bv[j] = ldcg(Bt + (size_t)(c0 + j) * NB + row);
-#pragma unroll
-            for (int j = 0; j < 32; j++)
-                stcg(Bt + (size_t)(c0 + j) * NB + row, bv[j] - f32_to_f64_bits(PW[row * LDF + c0 + j]));
-        }
-    }
-
-    // ---- phase 3: D = V W, K (reflectors) in 4 chunks of 32, operand sets
-    // alternating between the set at 0 and the G area (G is no longer needed).
-    // Unit u: operand row r (tile row for A, tile column c = r for B), K =
-    // reflectors k0 + 4j .. +3; lanes run over consecutive rows.
-    {
-        const int set_off[2] = {0, M::OFF_G};
-        for (int kk = 0; kk < NB / KC; kk++) {
-            const int b = kk & 1, k0 = kk * KC;
-            if (kk >= 2)
-                ok &= mixed_wait(mbar, phase, b);
-            double v[4][4];
-#pragma unroll
-            for (int x = 0; x < 4; x++) {
-                const int u = tid + x * NT, r = u & (NB - 1), j = u >> 7, k = k0 + 4 * j;
-#pragma unroll
-                for (int e = 0; e < 4; e++)
-                    v[x][e] = mixed_v_elem<VK>(Vt, r, k + e);
-            }
-#pragma unroll
-            for (int x = 0; x < 4; x++) {
-                const int u = tid + x * NT, r = u & (NB - 1), j = u >> 7, k = k0 + 4 * j;
-                const uint32_t off = tc::kmajor_off(r, 4 * j, KC);
-                store_split4(sm, set_off[b] + M::OFF_AHI, set_off[b] + M::OFF_ALO, off, f64_to_f32_bits(v[x][0]),
-                             f64_to_f32_bits(v[x][1]), f64_to_f32_bits(v[x][2]), f64_to_f32_bits(v[x][3]));
-                // B operand (column c = r, reflector k) = W[k][c]
-                store_split4(sm, set_off[b] + M::OFF_BHI, set_off[b] + M::OFF_BLO, off, PW[k * LDF + r],
-                             PW[(k + 1) * LDF + r], PW[(k + 2) * LDF + r], PW[(k + 3) * LDF + r]);
-            }
-            const uint32_t base = sbase + set_off[b];
-            mixed_issue(&mbar[b], [&]() {
-                for (int ks = 0; ks < KC / 8; ks++) {
-                    const uint32_t o = ks * 256;
-                    const uint64_t ah = tc::smem_desc(base + M::OFF_AHI + o, LBO, SBO);
-                    const uint64_t al = tc::smem_desc(base + M::OFF_ALO + o, LBO, SBO);
-                    const uint64_t bh = tc::smem_desc(base + M::OFF_BHI + o, LBO, SBO);
-                    const uint64_t bl = tc::smem_desc(base + M::OFF_BLO + o, LBO, SBO);
-                    const uint32_t acc = (kk | ks) ? 1u : 0u;
-                    tc::mma_tf32(tmem, ah, bh, idesc, acc);
-                    tc::mma_tf32(tmem, ah, bl, idesc, 1u);
-                    tc::mma_tf32(tmem, al, bh, idesc, 1u);
-                }
-            });
-        }
-        ok &= mixed_wait(mbar, phase, 0);
-        ok &= mixed_wait(mbar, phase, 1);
-        ok = __syncthreads_and(ok);
-        if (!ok) {
-            if (tid == 0)
-                atomicCAS(err, 0, TILEQR_ERR_TIMEOUT);
-            return false;
-        }
-    }
-
-    // ---- phase 4: C -= D (FP64), row r = TMEM lane; the 32 old values of a
-    // group are loaded before any store
-    {
-        const int r = 32 * (warp & 3) + lane;
-        const int cbase = (warp >> 2) * 64;
-        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
-        for (int h = 0; h < 2; h++) {
-            const int c0 = cbase + 32 * h;
-            float v[32];
-            double old[32];
-#pragma unroll
-            for (int j = 0; j < 32; j++)
-                old[j] = ldcg(Ct + (size_t)(c0 + j) * NB + r);
-            tc::tmem_ld32(tmem + lane_off + c0, v);
-#pragma unroll
-            for (int j = 0; j < 32; j++)
-                stcg(Ct + (size_t)(c0 + j) * NB + r, old[j] - f32_to_f64_bits(v[j]));
-        }
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -577,7 +302,8 @@ __device__ __noinline__ void mixed_build_tfull(unsigned char *smb, const double 
 // 32 on double-buffered operands.  Shared memory: R1 (128 KB) holds the two
 // operand sets of the P rounds, then all 4 chunks of the B operand of the W
 // and D products (Y = B + P, then W^T: row c, K = reflector); R2 (64 KB) the
-// double-buffered A operand of those (T^T chunks, then V chunks).  Returns
+// double-buffered A operand of those (T^T chunks, then V chunks), and before
+// each a per-warp transpose scratch for staging Y and W^T.  Returns
 // false on a tensor-core wait timeout (an error is recorded).
 constexpr size_t TF_UPDATE_SMEM = 192 * 1024;
 
@@ -612,6 +338,34 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     const int cbase = (warp >> 2) * 64;
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     const int kq = warp & 3;                    // K chunk of this thread's reflector rows
+    // Units of the P rounds (row m, K group j of 4): a warp covers 8 rows x 4
+    // K groups, so its 16-byte operand stores fall in 8 distinct bank groups.
+    auto p_row = [&](int x) { return (((x >> 1) * NWARP + warp) << 3) | (lane & 7); };
+    auto p_kgrp = [&](int x) { return ((x & 1) << 2) | (lane >> 3); };
+    // Transpose scratch of this warp in R2 (free while Y and W^T are staged):
+    // its 32 reflector rows x 32 columns, ld 33
+    float *xs = (float *)(sm + R2) + warp * 32 * 33;
+    // The warp's 32 x 32 block (rows = its tensor-memory lanes, columns
+    // c0..c0+31) into chunk kq of the B operand in R1 (row c, K = reflector):
+    // through the scratch, then 4 consecutive K per 16-byte store.
+    auto stage_bop = [&](const float (&val)[32], int c0) {
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+            xs[lane * 33 + j] = val[j];
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            float4 h, l;
+            tc::split_tf32(xs[(4 * q + 0) * 33 + lane], h.x, l.x);
+            tc::split_tf32(xs[(4 * q + 1) * 33 + lane], h.y, l.y);
+            tc::split_tf32(xs[(4 * q + 2) * 33 + lane], h.z, l.z);
+            tc::split_tf32(xs[(4 * q + 3) * 33 + lane], h.w, l.w);
+            const uint32_t off = kq * 2 * OPB + tc::kmajor_off(c0 + lane, 4 * q, KC);
+            *(float4 *)(sm + off) = h;
+            *(float4 *)(sm + off + OPB) = l;
+        }
+        __syncwarp();
+    };
 
     // ---- P = V^T C: A = V^T (row = reflector, K = tile row), B = C^T (row =
     // column); sets at 0 and 4 OPB
@@ -622,7 +376,7 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         double v[4][4], c[4][4];
 #pragma unroll
         for (int x = 0; x < 4; x++) {
-            const int u = tid + x * NT, j = u & 7, m = u >> 3, r = r0 + 4 * j;
+            const int m = p_row(x), j = p_kgrp(x), r = r0 + 4 * j;
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 v[x][e] = mixed_v_elem<VK>(Vt, r + e, m);
@@ -631,8 +385,7 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         }
 #pragma unroll
         for (int x = 0; x < 4; x++) {
-            const int u = tid + x * NT, j = u & 7, m = u >> 3;
-            const uint32_t off = tc::kmajor_off(m, 4 * j, KC);
+            const uint32_t off = tc::kmajor_off(p_row(x), 4 * p_kgrp(x), KC);
             store_split4(sm, so, so + OPB, off, f64_to_f32_bits(v[x][0]), f64_to_f32_bits(v[x][1]),
                          f64_to_f32_bits(v[x][2]), f64_to_f32_bits(v[x][3]));
             store_split4(sm, so + 2 * OPB, so + 3 * OPB, off, f64_to_f32_bits(c[x][0]), f64_to_f32_bits(c[x][1]),
@@ -655,14 +408,11 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
             bv[j] = Bt ? ldcg(Bt + (size_t)(c0 + j) * NB + a_row) : 0.0;
         tc::tmem_ld32(tmem + lane_off + c0, v);
 #pragma unroll
-        for (int j = 0; j < 32; j++) {
-            float hi, lo;
-            tc::split_tf32(v[j] + (Bt ? f64_to_f32_bits(bv[j]) : 0.0f), hi, lo);
-            const uint32_t off = kq * 2 * OPB + tc::kmajor_off(c0 + j, lane, KC);
-            *(float *)(sm + off) = hi;
-            *(float *)(sm + off + OPB) = lo;
-        }
+        for (int j = 0; j < 32; j++)
+            v[j] += Bt ? f64_to_f32_bits(bv[j]) : 0.0f;
+        stage_bop(v, c0);
     }
+    __syncthreads();   // every warp is done with its scratch in R2
     // ---- W = T^T Y: A = T^T chunks copied from the panel's pre-split operand
     for (int kk = 0; kk < NB / KC; kk++) {
         const int b = kk & 1;
@@ -694,15 +444,9 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
             for (int j = 0; j < 32; j++)
                 stcg(Bt + (size_t)(c0 + j) * NB + a_row, bv[j] - f32_to_f64_bits(w[j]));
         }
-#pragma unroll
-        for (int j = 0; j < 32; j++) {
-            float hi, lo;
-            tc::split_tf32(w[j], hi, lo);
-            const uint32_t off = kq * 2 * OPB + tc::kmajor_off(c0 + j, lane, KC);
-            *(float *)(sm + off) = hi;
-            *(float *)(sm + off + OPB) = lo;
-        }
+        stage_bop(w, c0);
     }
+    __syncthreads();   // every warp is done with its scratch in R2
     // ---- D = V W: A = V (row = tile row, K = reflector) chunks staged in R2
     for (int kk = 0; kk < NB / KC; kk++) {
         const int b = kk & 1, k0 = kk * KC, ao = R2 + b * 2 * OPB;
