@@ -48,6 +48,13 @@ def measured_peaks():
         return {}
 
 
+def tf32_peak_gflops():
+    """Dense TF32 tensor peak of this GPU: the measured dense bf16 peak (burst)
+    times the nominal tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s)."""
+    bf16 = float(measured_peaks().get("bf16_tflops", 1900.0))
+    return bf16 * 1e3 * (1.1 / 2.25), f"measured bf16 dense {bf16:.1f} TFLOP/s x nominal tf32/bf16 1.1/2.25"
+
+
 QR_SOURCES = ("common.cuh", "sched.cuh", "tile_f64.cuh", "dag.cuh", "release.cuh", "factor.cu")
 LU_SOURCES = ("common.cuh", "sched.cuh", "graph.cuh", "release.cuh", "lu.cuh", "lu.cu")
 
@@ -242,6 +249,9 @@ def run_batched(args, dev, rank, world, barrier, dist):
                                      "batched_value": sflops / tb / 1e9}
         torch.cuda.empty_cache()
     out["tf32_speedup_vs_fp64"] = out["fp64"]["ms"] / out["tf32"]["ms"]
+    tpk, tsrc = tf32_peak_gflops()
+    out["tf32"]["pct_of_tf32_dense_peak"] = 100.0 * out["tf32"]["value"] / world / tpk
+    out["tf32"]["tf32_peak_source"] = tsrc
     return out
 
 
@@ -591,6 +601,11 @@ def main():
                  "initial_rel_residual": infos[-1]["initial_rel_residual"],
                  "speedup_vs_fp64_factorization": (world * ops / tm / 1e9) / value,
                  "timing": "wall clock around factor+refine (the refinement synchronises), max over ranks"}
+        tpk, tsrc = tf32_peak_gflops()
+        # the factorization's LAPACK-count rate against the dense TF32 peak
+        # (each product is three TF32 MMAs, so 1/3 of it is the ceiling)
+        mixed["factor_pct_of_tf32_dense_peak"] = 100.0 * (ops / (mixed["factor_ms"] / 1e3) / 1e9) / tpk
+        mixed["tf32_peak_source"] = tsrc
         del wsm, Akd, bk, fm
 
     # ---- batched: 4096 independent matrices, m ~ U[64, 2048], n ~ U[32, m],
