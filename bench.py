@@ -411,6 +411,92 @@ def run_lu(args, dev, rank, world, barrier, dist):
             "timing": "CUDA events around the factorizations (layout conversion included), max over ranks"}
 
 
+def run_config2_sweep(args, dev, rank, world, barrier, dist):
+    """16384^2 N(0,1) factorization rate for nb in {128, 256} x ib in {16, 32}
+    with the persistent task-graph kernel, and the fork-join comparator (one
+    launch per step and task kind) at nb 128 / ib 16; one timed run each after
+    a warm-up (opt-in: about a minute)."""
+    import torch
+    from paper_0709_1272_gb300 import inputs, replicas, tileqr
+    m = n = args.n
+    A = tileqr.to_device_colmajor(inputs.normal_matrix(m, n, seed=20070709 + 1 + 1000 * rank), dev)
+    ops = lapack_opcount(m, n)
+    out = {}
+    for nb, ib, sched in [(128, 16, "dag"), (128, 32, "dag"), (256, 16, "dag"), (256, 32, "dag"),
+                          (128, 16, "bulk")]:
+        sc = tileqr.TILEQR_SCHED_DAG if sched == "dag" else tileqr.TILEQR_SCHED_BULK
+        ws = torch.empty(tileqr.tileqr_workspace_size(m, n, nb, ib), dtype=torch.uint8, device=dev)
+        tileqr.tileqr_factor(A, nb, ib, schedule=sc, workspace=ws).check()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record()
+        f = tileqr.tileqr_factor(A, nb, ib, schedule=sc, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        f.check()
+        t = replicas.max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+        out[f"{sched}_nb{nb}_ib{ib}"] = {"value": world * ops / t / 1e9, "ms": t * 1e3}
+        del ws, f
+    return {"workload": f"plain FP64 tile QR, {m}x{n} N(0,1): task graph vs fork-join, nb x ib sweep",
+            "unit": UNIT, "runs": out}
+
+
+def run_kappa_sweep(args, dev, rank, world, barrier, dist):
+    """The mixed-precision solve of A x = b (TF32 updates + FP64 refinement)
+    for cond(A) in {1e2, 1e6, 1e10}, A = (I-2uu^T) diag(s) (I-2vv^T): time,
+    refinement steps and method, the solve's relative residual, and the
+    factorization's accuracy at full size from samples: the backward error
+    ||Q^T a_j - r_j|| / ||A|| over 64 sampled columns and the orthogonality
+    ||Q^T (Q X) - X|| / ||X|| for 8 random probe vectors (opt-in)."""
+    import numpy as np
+    import torch
+    from paper_0709_1272_gb300 import inputs, replicas, tileqr
+    m = n = args.n
+    nb, ib = 128, 16
+    out = {}
+    g = torch.Generator(device=dev).manual_seed(20070709 + 5)
+    cols = torch.randperm(n, generator=g, device=dev)[:64].sort().values
+    for kappa in (1e2, 1e6, 1e10):
+        Ak, _, _, _ = inputs.kappa_matrix(n, kappa, seed=20070709 + 4 + 1000 * rank)
+        xt = inputs.normal_matrix(n, 1, seed=20070709 + 6)[:, 0]
+        bk = torch.from_numpy(Ak @ xt).to(dev)
+        Akd = tileqr.to_device_colmajor(Ak, dev)
+        del Ak
+        wsm = torch.empty(tileqr.tileqr_workspace_size(m, n, nb, ib, tileqr.TILEQR_TF32), dtype=torch.uint8,
+                          device=dev)
+        tileqr.tileqr_factor(Akd, nb, ib, precision=tileqr.TILEQR_TF32, workspace=wsm).check()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fm = tileqr.tileqr_factor(Akd, nb, ib, precision=tileqr.TILEQR_TF32, workspace=wsm)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        xk, info = fm.solve_refine(Akd, bk, max_iter=40, tol=1e-12)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        fm.check()
+        nA = torch.linalg.matrix_norm(Akd).item()
+        QtA = fm.apply_qt(Akd[:, cols].contiguous().t().contiguous().t())
+        R = fm.R()
+        back = torch.linalg.matrix_norm(QtA - R[:, cols]).item() / nA * np.sqrt(n / 64.0)
+        X = torch.randn((n, 8), generator=g, dtype=torch.float64, device=dev)
+        orth = (torch.linalg.matrix_norm(fm.apply_qt(fm.apply_q(X)) - X) / torch.linalg.matrix_norm(X)).item()
+        d = info.as_dict()
+        out[f"{kappa:.0e}"] = {"factor_ms": replicas.max_over_ranks(t1 - t0, dist, dev) * 1e3,
+                               "refine_ms": replicas.max_over_ranks(t2 - t1, dist, dev) * 1e3,
+                               "refine_iterations": d["iterations"],
+                               "refine_method": {1: "classical", 2: "flexible GMRES"}.get(d["method"], "none"),
+                               "rel_residual": d["rel_residual"], "initial_rel_residual": d["initial_rel_residual"],
+                               "backward_error_sampled": back, "orthogonality_probe": orth}
+        del wsm, Akd, bk, fm, QtA, R
+        torch.cuda.empty_cache()
+    return {"workload": f"TF32-update tile QR + FP64 refinement, {n}x{n}, A = (I-2uu^T) diag(s) (I-2vv^T)",
+            "per_kappa": out,
+            "estimates": "backward error scaled from 64 sampled columns by sqrt(n/64); orthogonality from "
+                         "8 random probes"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,7 +519,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-cholesky", action="store_true",
                     help="skip the tiled Cholesky (Algorithm 1) measurement")
-    ap.add_argument("--only", choices=["lu", "cholesky"], default=None,
+    ap.add_argument("--only", choices=["lu", "cholesky", "config2-sweep", "kappa-sweep"], default=None,
                     help="run only this secondary measurement (at --n) and print its JSON object")
     ap.add_argument("--no-lu", action="store_true",
                     help="skip the tiled LU (Algorithm 3) measurement")
@@ -472,7 +558,8 @@ def main():
         def barrier():
             if dist is not None:
                 dist.barrier()
-        section = {"lu": run_lu, "cholesky": run_cholesky}[args.only](args, dev, rank, world, barrier, dist)
+        section = {"lu": run_lu, "cholesky": run_cholesky, "config2-sweep": run_config2_sweep,
+                   "kappa-sweep": run_kappa_sweep}[args.only](args, dev, rank, world, barrier, dist)
         if rank == 0:
             print(json.dumps({"section": args.only, **section}), flush=True)
         if dist is not None:
