@@ -380,8 +380,10 @@ __device__ __forceinline__ void column_scalars(const double *x, int t0, int rows
 //
 // Critical path: column jj+1 needs H_jj applied before its norm exists.
 // Warp 0 applies H_jj to column jj+1 and at once forms column jj+1's
-// scalars, while warps 1.. apply H_jj to the remaining columns; one block
-// barrier per column.  Scalars are double-buffered in shared memory.
+// scalars, while the warps of the other three sub-partitions apply H_jj to
+// the remaining columns (the warps sharing warp 0's sub-partition stay out of
+// its FP64 pipe); one block barrier per column.  Scalars are double-buffered
+// in shared memory.
 template <int NB, int S, bool TS>
 __device__ __noinline__ void panel_factor(double *sm, double *Pt, double *Ph, int ldh, int rows)
 {
@@ -411,8 +413,13 @@ __device__ __noinline__ void panel_factor(double *sm, double *Pt, double *Ph, in
                 const int r = t0 + lane + 32 * k;
                 vs[k] = (r < rows) ? x[r] * scale : 0.0;
             }
-            const int cfirst = (warp == 0) ? jj + 1 : jj + 1 + warp;
-            const int cstep = (warp == 0) ? S : NWARP - 1;
+            // helpers: the warps on the other three sub-partitions (warp & 3
+            // != 0), so that no FP64 work queues on warp 0's FP64 pipe (one
+            // warp instruction per ~64 cycles per sub-partition on GB300)
+            constexpr int NHELP = NWARP - NWARP / 4;
+            const int h = warp - 1 - (warp >> 2);   // helper index of warp (warp & 3 != 0)
+            const int cfirst = (warp == 0) ? jj + 1 : ((warp & 3) ? jj + 2 + h : S);
+            const int cstep = (warp == 0) ? S : NHELP;
             for (int c = cfirst; c < S; c += cstep) {
                 double *y = Pt + c * LDC;
                 double d = 0.0;
