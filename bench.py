@@ -519,7 +519,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-cholesky", action="store_true",
                     help="skip the tiled Cholesky (Algorithm 1) measurement")
-    ap.add_argument("--only", choices=["lu", "cholesky", "config2-sweep", "kappa-sweep"], default=None,
+    ap.add_argument("--only", choices=["lu", "cholesky", "batched", "config2-sweep", "kappa-sweep"], default=None,
                     help="run only this secondary measurement (at --n) and print its JSON object")
     ap.add_argument("--no-lu", action="store_true",
                     help="skip the tiled LU (Algorithm 3) measurement")
@@ -558,7 +558,7 @@ def main():
         def barrier():
             if dist is not None:
                 dist.barrier()
-        section = {"lu": run_lu, "cholesky": run_cholesky, "config2-sweep": run_config2_sweep,
+        section = {"lu": run_lu, "cholesky": run_cholesky, "batched": run_batched, "config2-sweep": run_config2_sweep,
                    "kappa-sweep": run_kappa_sweep}[args.only](args, dev, rank, world, barrier, dist)
         if rank == 0:
             print(json.dumps({"section": args.only, **section}), flush=True)

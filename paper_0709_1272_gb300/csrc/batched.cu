@@ -1,6 +1,7 @@
 // batched.cu -- many independent tiled QR factorizations in one persistent
 // launch (the batched form): a per-matrix table in the workspace, one layout
 // kernel over all matrices, one task-graph kernel over all tasks.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -73,11 +74,11 @@ BatchLayout batch_layout(int count, const int64_t *m, const int64_t *n, int nb, 
         mi.steps = (m[b] > 0 && n[b] > 0) ? (mi.p < mi.q ? mi.p : mi.q) : 0;
         mi.cnt_off = cnt;
         cnt += (unsigned long long)mi.steps * mi.p * mi.q;
-        for (int k = 0; k < mi.steps; k++) {
-            B.cap[K_GEQRT] += 1;
-            B.cap[K_LARFB] += (unsigned long long)(mi.q - k - 1);
-            B.cap[K_TSQRT] += (unsigned long long)(mi.p - k - 1);
-            B.cap[K_SSRFB] += (unsigned long long)(mi.p - k - 1) * (mi.q - k - 1);
+        if (mi.steps > 0) {
+            unsigned long long lv[K_NKIND];
+            g_level_counts(make_graph(mi.p, mi.q, 0), lv);
+            for (int t = 0; t < K_NKIND; t++)
+                B.cap[t] += lv[t];
         }
         // data offsets relative to the data section: tiles then T strips
         mi.tiles = (double *)(uintptr_t)data;
@@ -108,7 +109,8 @@ BatchLayout batch_layout(int count, const int64_t *m, const int64_t *n, int nb, 
         off += align256((size_t)(B.cap[t] ? B.cap[t] : 1) * 8);
     }
     B.off_mats = off;
-    off += align256((size_t)(count ? count : 1) * sizeof(MatInfo));
+    // the per-matrix table, then the order of the first pushes (count ints)
+    off += align256((size_t)(count ? count : 1) * sizeof(MatInfo) + (size_t)(count ? count : 1) * sizeof(int));
     B.off_data = off;
     off += data;
     B.end = off;
@@ -242,8 +244,19 @@ extern "C" int tileqr_batched_prepare(int count, const int64_t *m, const int64_t
     if (count == 0)
         return 0;
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(ws + B.off_mats, infos.data(), (size_t)count * sizeof(MatInfo), cudaMemcpyHostToDevice,
-                        st) != cudaSuccess)
+    // largest matrices (by flop count) start first: their chains are the longest
+    std::vector<int> order(count);
+    for (int b = 0; b < count; b++)
+        order[b] = b;
+    auto work = [&](int b) {
+        const double mm = (double)m[b], nn = (double)n[b];
+        return m[b] >= n[b] ? nn * nn * (mm - nn / 3.0) : mm * mm * (nn - mm / 3.0);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+    std::vector<char> table((size_t)count * sizeof(MatInfo) + (size_t)count * sizeof(int));
+    std::memcpy(table.data(), infos.data(), (size_t)count * sizeof(MatInfo));
+    std::memcpy(table.data() + (size_t)count * sizeof(MatInfo), order.data(), (size_t)count * sizeof(int));
+    if (cudaMemcpyAsync(ws + B.off_mats, table.data(), table.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess)
         return TILEQR_ERR_CUDA;

@@ -252,7 +252,8 @@ __device__ static void release_batched(const Queues &Q, const FactorArgs &F, siz
             break;
         }
         const size_t idx = cnt_off + ((size_t)ks * p + is) * q + js;
-        q_signal(Q, idx, task_ndeps(is, js, ks), task_kind(is, js, ks), encode_btask(mat, ks, is, js));
+        q_signal(Q, idx, task_ndeps(is, js, ks), kind_prio(task_kind(is, js, ks), ks, js),
+                 encode_btask(mat, ks, is, js));
     }
 }
 
@@ -284,9 +285,14 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
             if (threadIdx.x == 0)
                 atomicCAS(&Q.ctrl->error, 0, TILEQR_ERR_NONFINITE);
         } else {
-            for (int b = threadIdx.x; b < count; b += NT)
+            // the matrices' first panels in the order the host stored after
+            // the table (largest first), so the longest chains start first
+            const int *order = (const int *)(mats + count);
+            for (int u = threadIdx.x; u < count; u += NT) {
+                const int b = order[u];
                 if (mats[b].steps > 0)
                     q_push(Q, K_GEQRT, encode_btask(b, 0, 0, 0));
+            }
         }
     }
     for (;;) {
