@@ -57,6 +57,7 @@ def tf32_peak_gflops():
 
 QR_SOURCES = ("common.cuh", "sched.cuh", "tile_f64.cuh", "dag.cuh", "release.cuh", "factor.cu")
 LU_SOURCES = ("common.cuh", "sched.cuh", "graph.cuh", "release.cuh", "lu.cuh", "lu.cu")
+CHOL_SOURCES = ("common.cuh", "sched.cuh", "graph.cuh", "chol.cuh", "cholesky.cu")
 
 
 def kernel_source_hash(files=QR_SOURCES):
@@ -335,9 +336,14 @@ def run_cholesky(args, dev, rank, world, barrier, dist):
     peaks = measured_peaks()
     fp64_peak = NSM * FP64_FLOP_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
     del A, ws
+    roof = {"bound": "alu", "achieved": ops / t / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
+            "frac": ops / t / 1e9 / fp64_peak,
+            "traffic": profiled_traffic(f"{n}x{n}/nb{nb}", "k_chol_dag_fp64.md", CHOL_SOURCES),
+            "kernel": f"k_chol_dag<{nb}>",
+            "achieved_flops": "n^3/3 per factorization (the algorithm's own count) / its CUDA-event time"}
     return {"workload": f"tiled Cholesky (Algorithm 1), {n}x{n} SPD (G+G^T)/2 + nI, G uniform[-1,1), nb={nb}, "
                         f"FP64 task graph", "value": world * ops / t / 1e9, "unit": UNIT, "ms_per_step": t * 1e3,
-            "steps": reps, "pct_fp64_peak": 100.0 * (ops / t / 1e9) / fp64_peak,
+            "steps": reps, "pct_fp64_peak": 100.0 * (ops / t / 1e9) / fp64_peak, "roofline": roof,
             "timing": "CUDA events around the factorizations (layout conversion included), max over ranks"}
 
 

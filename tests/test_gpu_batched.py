@@ -97,3 +97,36 @@ def test_batched_cuda_graph_replay(tq):
         assert bt.status() == 0
         for b in range(len(shapes)):
             assert np.array_equal(bt.get(b).factors()[0].cpu().numpy(), ref[b])
+
+
+@pytest.mark.parametrize("prec_name,nb,ib", [("TILEQR_FP64", 64, 16), ("TILEQR_TF32", 128, 16)])
+def test_full_batch_4096(tq, prec_name, nb, ib):
+    """The benchmarked batch at full size: 4096 matrices, m ~ U[64, 2048],
+    n ~ U[32, m], entries U[-1, 1) (the benchmark's seed), with the (nb, ib)
+    the autotuner picks for it (FP64 64/16, TF32 128/16).  Every matrix
+    finishes; sampled matrices are bit-identical to the single-matrix entry
+    point; in FP64 the smallest sampled ones also match the oracle."""
+    prec = getattr(tq, prec_name)
+    seed = 20070709 + 5
+    shapes = inputs.batch_shapes(4096, seed=seed)
+    pool, offs = inputs.batch_pool(shapes, seed=seed)
+    pool_d = torch.from_numpy(pool).to("cuda")
+    mats = [pool_d[o:o + m * n].view(n, m).t() for (m, n), o in zip(shapes, offs)]
+    bt = tq.Batch(mats, nb, ib, prec)
+    bt.run()
+    assert bt.status() == 0
+    rng = np.random.Generator(np.random.Philox(key=77))
+    sample = sorted(set(rng.integers(0, len(shapes), 10).tolist()) | {int(np.argmin([m * n for m, n in shapes]))})
+    for b in sample:
+        m, n = shapes[b]
+        AV, T = bt.get(b).factors()
+        s = tq.tileqr_factor(mats[b], nb, ib, precision=prec).check()
+        AVs, Ts = s.factors()
+        assert np.array_equal(AV.cpu().numpy(), AVs.cpu().numpy())
+        assert np.array_equal(T.cpu().numpy(), Ts.cpu().numpy())
+        if prec == tq.TILEQR_FP64 and m * n <= 400 * 400:
+            A = pool[offs[b]:offs[b] + m * n].reshape(n, m).T
+            ref = oracle.tiled_qr(A, nb, ib)
+            assert _rel(AV.cpu().numpy(), ref.A) <= TOL
+    del bt, mats, pool_d
+    torch.cuda.empty_cache()

@@ -115,3 +115,22 @@ def test_cholesky_trace_respects_dependencies(tq):
     for t in tasks:
         for pr in preds[t]:
             assert seen[pr][1] <= seen[t][0]
+
+
+def test_full_16384(tq):
+    """The benchmarked launch: 16384 x 16384 SPD (G + G^T)/2 + n I with the
+    benchmark's seed, nb 128.  Properties at full size: L is lower triangular
+    with a positive diagonal, and (L L^T)[rows, :] = A[rows, :] to rounding
+    on 64 sampled rows."""
+    n, nb = 16384, 128
+    A = inputs.spd_matrix(n, seed=20070709 + 7)
+    Ad = tq.to_device_colmajor(A)
+    f = tq.tileqr_cholesky(Ad, nb).check()
+    assert f.info() == 0
+    L = f.L()
+    assert torch.count_nonzero(torch.triu(L, 1)).item() == 0
+    assert (torch.diagonal(L) > 0).all().item()
+    rows = torch.from_numpy(np.random.Generator(np.random.Philox(key=5)).choice(n, 64, replace=False)).cuda()
+    LLt = L[rows] @ L.t()
+    err = (LLt - Ad[rows]).abs().max().item()
+    assert err <= 10 * n * EPS * np.abs(A).max()

@@ -166,14 +166,16 @@ def test_empty_and_degenerate(tq):
 
 # ---------------------------------------------------------------------------
 # full-size workloads, in the launch configuration the benchmark times
-def test_full_16384_sampled(tq):
-    """16384 x 16384 N(0,1), nb 128, ib 32, persistent kernel.  Sampled
+@pytest.mark.parametrize("ib", [16, 32])
+def test_full_16384_sampled(tq, ib):
+    """16384 x 16384 N(0,1), nb 128, ib 16 (the benchmarked launch) and 32,
+    persistent kernel.  Sampled
     against the oracle: the first tile column's R_00, V_i0, T_i0 (the oracle
     factors that 16384 x 128 panel) and the first tile row R_0j for sampled
     j (the oracle applies those reflectors to column block j).  Properties at
     full size: Q^T (A x) = R x and ||Q^T y|| = ||y||."""
     m = n = 16384
-    nb, ib = 128, 32
+    nb = 128
     A = inputs.normal_matrix(m, n, seed=20070711)
     Ad = tq.to_device_colmajor(A)
     f = tq.tileqr_factor(Ad, nb, ib).check()
@@ -201,10 +203,11 @@ def test_full_16384_sampled(tq):
 
 
 def test_full_tall_skinny_solve(tq):
-    """262144 x 512 N(0,1), nb 128, ib 32, with tileqr_solve_ls on 16 RHS.
-    Sampled: the first tile column against the oracle; properties: the
-    least-squares optimality ||A^T r|| / (||A|| ||r||) at rounding level."""
-    m, n, nb, ib = 262144, 512, 128, 32
+    """262144 x 512 N(0,1), nb 128, ib 16 (the benchmarked flat-tree launch),
+    with tileqr_solve_ls on 16 RHS.  Sampled: the first tile column against
+    the oracle; properties: the least-squares optimality ||A^T r|| / (||A||
+    ||r||) at rounding level."""
+    m, n, nb, ib = 262144, 512, 128, 16
     A = inputs.normal_matrix(m, n, seed=20070712)
     Ad = tq.to_device_colmajor(A)
     f = tq.tileqr_factor(Ad, nb, ib).check()

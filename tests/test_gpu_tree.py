@@ -151,10 +151,12 @@ def test_tree_mixed_precision(tq):
     assert _rel(Rn, oracle.sign_normalize(ref.R())) <= 1e-4
 
 
-def test_full_tall_skinny_tree(tq):
-    """262144 x 512 N(0,1), nb 128, ib 32, domain 16 (the benchmarked tree
-    configuration) with tileqr_solve_ls on 16 right-hand sides."""
-    m, n, nb, ib, h = 262144, 512, 128, 32, 16
+@pytest.mark.parametrize("ib,h", [(16, 8), (32, 16)])
+def test_full_tall_skinny_tree(tq, ib, h):
+    """262144 x 512 N(0,1), nb 128: ib 16 with domain 8 (the benchmarked FP64
+    tree launch) and ib 32 with domain 16, with tileqr_solve_ls on 16
+    right-hand sides."""
+    m, n, nb = 262144, 512, 128
     A = inputs.normal_matrix(m, n, seed=20070712)
     Ad = tq.to_device_colmajor(A)
     f = tq.tileqr_factor_tree(Ad, nb, ib, h).check()
@@ -179,6 +181,25 @@ def test_full_tall_skinny_tree(tq):
     r = Bd - Ad @ X
     ratio = (torch.linalg.matrix_norm(Ad.t() @ r) / (nA * torch.linalg.matrix_norm(r))).item()
     assert ratio <= 20 * n * EPS
+
+
+def test_full_tall_skinny_tree_mixed(tq):
+    """262144 x 512 N(0,1), nb 128, ib 16, domain 16 with TILEQR_TF32 (the
+    benchmarked mixed tree launch): backward error within the FP32
+    accumulation bound, and Q (built from FP64 reflectors) orthogonal to FP64
+    rounding on random probes."""
+    m, n, nb, ib, h = 262144, 512, 128, 16, 16
+    A = inputs.normal_matrix(m, n, seed=20070712)
+    Ad = tq.to_device_colmajor(A)
+    f = tq.tileqr_factor_tree(Ad, nb, ib, h, precision=tq.TILEQR_TF32).check()
+    R = f.R()
+    QtA = f.apply_qt(Ad.clone())
+    nA = torch.linalg.matrix_norm(Ad)
+    assert (torch.linalg.matrix_norm(QtA[:n] - R) / nA).item() <= 32 * n * 2.0 ** -24
+    assert (torch.linalg.matrix_norm(QtA[n:]) / nA).item() <= 32 * n * 2.0 ** -24
+    X = tq.to_device_colmajor(inputs.normal_matrix(m, 4, seed=20070714))
+    Y = f.apply_qt(f.apply_q(X.clone()))
+    assert (torch.linalg.matrix_norm(Y - X) / torch.linalg.matrix_norm(X)).item() <= 20 * n * EPS
 
 
 def test_tree_argument_errors(tq):
