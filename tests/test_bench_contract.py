@@ -34,8 +34,10 @@ def test_profiled_traffic_is_reported_only_for_matching_sources():
     import re
     sys.path.insert(0, ROOT)
     import bench
-    for prof, files in (("k_factor_dag_fp64.md", bench.QR_SOURCES), ("k_lu_dag_fp64.md", bench.LU_SOURCES)):
+    for prof, files, key in (("k_factor_dag_fp64.md", bench.QR_SOURCES, "16384x16384/nb128/ib16"),
+                             ("k_lu_dag_fp64.md", bench.LU_SOURCES, "16384x16384/nb128/ib16"),
+                             ("k_chol_dag_fp64.md", bench.CHOL_SOURCES, "16384x16384/nb128")):
         txt = open(os.path.join(ROOT, "profiles", prof)).read()
         match = re.search(r"source_hash:\s*([0-9a-f]+)", txt).group(1) == bench.kernel_source_hash(files)
-        t = bench.profiled_traffic("16384x16384/nb128/ib16", prof, files)
+        t = bench.profiled_traffic(key, prof, files)
         assert (t is not None and t > 0) == match
