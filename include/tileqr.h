@@ -302,9 +302,11 @@ int tileqr_refine_workspace_size(const tileqr_desc *d, size_t *bytes);
  *   A, lda   the original matrix (device, column-major, FP64)
  *   b        device, m entries;   x  device, n entries (output)
  *   max_iter refinement steps (outer iterations) at most
+ * Works on flat and tree-form factorizations (the correction solve replays
+ * the factorization's apply graph), nb 128.
  * Synchronous.  Returns 0 (also when not converged: see info), -i,
- * TILEQR_ERR_SINGULAR, TILEQR_ERR_WORKSPACE, TILEQR_ERR_UNSUPPORTED (also for a
- * tree-form factorization), TILEQR_ERR_CUDA. */
+ * TILEQR_ERR_SINGULAR, TILEQR_ERR_WORKSPACE, TILEQR_ERR_UNSUPPORTED (nb other
+ * than 128), TILEQR_ERR_CUDA. */
 int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_t lda, const double *b, double *x,
                         int max_iter, double tol, void *workspace, size_t ws_bytes, tileqr_stream_t stream,
                         tileqr_refine_info *info);

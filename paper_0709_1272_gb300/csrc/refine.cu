@@ -2,10 +2,10 @@
 // mixed-precision factorization (square or tall A, one right-hand side).
 //
 // The correction solves use an FP32 copy of the factors: M^{-1} v =
-// R^{-1} (Q^T v)(0:n) with Q^T applied as the task graph of Algorithm 2
-// restricted to one column (DLARFB / DSSRFB on vectors, single precision) and
-// R^{-1} as a tiled back substitution with precomputed inverses of R's
-// diagonal tiles.  Residuals r = b - A x, the Krylov vectors and x are FP64.
+// R^{-1} (Q^T v)(0:n) with Q^T applied as the factorization's task graph
+// restricted to one column (DLARFB / DSSRFB, and DTTMQR for the tree form, on
+// vectors, single precision; the apply graph of graph.cuh) and R^{-1} as a
+// tiled back substitution with precomputed inverses of R's diagonal tiles.  Residuals r = b - A x, the Krylov vectors and x are FP64.
 // Classical refinement (x += M^{-1} r) is tried first; if the residual stops
 // shrinking, the solve continues with restarted flexible GMRES on A d = r
 // with M^{-1} as the right preconditioner (GMRES-IR).
@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "factor.h"
+#include "graph.cuh"
 #include "sched.cuh"
 #include "tile_mixed.cuh"
 
@@ -81,10 +82,23 @@ __global__ void __launch_bounds__(128) k_inv_diag(const double *__restrict__ til
 struct Apply32Args {
     const float *tiles;   // FP32 copy of the factored tiles
     const float *T;       // FP32 copy of the T strips
+    const float *T2;      // FP32 copy of the DTTQRT T strips (tree form), else nullptr
     float *X;             // p row blocks of 128 x ncol (ld 128)
     int p, steps, ncol, S;
+    TGraph G;
 };
 
+__device__ __forceinline__ size_t apply32_cnt(const Apply32Args &A, int tt, int k, int i, int col)
+{
+    return (((size_t)tt * A.steps + k) * A.p + i) * A.ncol + col;
+}
+
+// One task: LB = DLARFB with a domain head's unit-lower V on its own block;
+// SB = DSSRFB of row i into its domain head's block (full V); TB = DTTMQR
+// merging head i into its partner's block (upper-triangular V, T2 strips).
+// TREE = false is Algorithm 2's flat graph (heads = the diagonal), with its
+// successors written out; TREE = true runs the graph functions of graph.cuh.
+template <bool TREE>
 __global__ void __launch_bounds__(128) k_apply32_dag(Apply32Args A, Queues Q)
 {
     __shared__ float Vs[128 * 33];   // V_l as [r][a], ld s+1 (s <= 32)
@@ -96,9 +110,12 @@ __global__ void __launch_bounds__(128) k_apply32_dag(Apply32Args A, Queues Q)
     __shared__ int s_cmd;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = A.S;
-    if (blockIdx.x == 0)
-        for (int c = tid; c < A.ncol; c += 128)
-            q_push(Q, 0, encode_task(0, 0, c));
+    const TGraph &G = A.G;
+    if (blockIdx.x == 0) {
+        const int nd0 = TREE ? g_ndom(G, 0) : 1;
+        for (int u = tid; u < A.ncol * nd0; u += 128)
+            q_push(Q, 0, encode_task(0, TREE ? g_head(G, 0, u / A.ncol) : 0, u % A.ncol));
+    }
     for (;;) {
         if (tid == 0)
             s_cmd = q_acquire(Q, s_code);
@@ -107,10 +124,13 @@ __global__ void __launch_bounds__(128) k_apply32_dag(Apply32Args A, Queues Q)
             break;
         int k, i, col;
         decode_task(s_code, k, i, col);
-        const bool lb = (i == k);
+        const int tt = decode_tt(s_code);
+        const int kind = TREE ? ga_kind(G, tt, k, i) : (i == k ? K_LARFB : K_SSRFB);
+        const bool lb = kind == K_LARFB, tri = TREE && kind == K_TTMQR;
+        const int top = !TREE ? k : (lb ? i : (tri ? g_partner(G, k, i) : g_head(G, k, g_dom(G, k, i))));
         const float *Vt = A.tiles + ((size_t)k * A.p + i) * 128 * 128;
-        const float *Tt = A.T + ((size_t)k * A.p + i) * (size_t)S * 128;
-        float *gxk = A.X + ((size_t)k * A.ncol + col) * 128;
+        const float *Tt = (tri ? A.T2 : A.T) + ((size_t)k * A.p + i) * (size_t)S * 128;
+        float *gxk = A.X + ((size_t)top * A.ncol + col) * 128;
         float *gxi = A.X + ((size_t)i * A.ncol + col) * 128;
         // other CTAs write these blocks in this launch: read them from L2
         xk[tid] = __ldcg(gxk + tid);
@@ -124,12 +144,14 @@ __global__ void __launch_bounds__(128) k_apply32_dag(Apply32Args A, Queues Q)
                 float v = Vt[(size_t)jj * 128 + r];
                 if (lb)
                     v = (r < jj) ? 0.0f : (r == jj ? 1.0f : v);
+                else if (tri && r > jj)
+                    v = 0.0f;
                 Vs[r * 33 + a] = v;
             }
             for (int idx = tid; idx < S * S; idx += 128)
                 Ts[idx] = Tt[(size_t)l0 * S + idx];
             __syncthreads();
-            // y(a) = [x_k(l0+a)] + sum_r V(r,a) x(r)   (x = x_i for SB, x_k for LB)
+            // y(a) = [x_top(l0+a)] + sum_r V(r,a) x(r)   (x = x_i for SB / TB, x_top for LB)
             const float *xv = lb ? xk : xi;
             float acc = 0.0f;
             if (lane < S) {
@@ -172,20 +194,27 @@ __global__ void __launch_bounds__(128) k_apply32_dag(Apply32Args A, Queues Q)
         __syncthreads();
         if (tid == 0) {
             __threadfence();
-            const size_t base = (size_t)A.ncol;
-            if (lb) {
+            if (TREE) {
+                GTask sp[2];
+                const int ns = ga_specific(G, kind, k, i, sp);
+                for (int s2 = 0; s2 < ns; s2++) {
+                    const int sk = ga_kind(G, sp[s2].tt, sp[s2].k, sp[s2].i);
+                    q_signal(Q, apply32_cnt(A, sp[s2].tt, sp[s2].k, sp[s2].i, col), ga_ndeps(sk, sp[s2].k),
+                             sk == K_LARFB ? 0 : 1, encode_task(sp[s2].k, sp[s2].i, col, sp[s2].tt));
+                }
+            } else if (lb) {
+                // LB(k) -> SB(k+1, k)
                 if (k + 1 < A.p)
-                    q_signal(Q, ((size_t)k * A.p + k + 1) * base + col, 1 + (k > 0 ? 1 : 0), 1,
-                             encode_task(k, k + 1, col));
+                    q_signal(Q, apply32_cnt(A, 0, k, k + 1, col), 1 + (k > 0 ? 1 : 0), 1, encode_task(k, k + 1, col));
             } else {
+                // SB(i, k) -> SB(i+1, k); the step-(k+1) task on row i (LB if i == k+1)
                 if (i + 1 < A.p)
-                    q_signal(Q, ((size_t)k * A.p + i + 1) * base + col, 1 + (k > 0 ? 1 : 0), 1,
-                             encode_task(k, i + 1, col));
+                    q_signal(Q, apply32_cnt(A, 0, k, i + 1, col), 1 + (k > 0 ? 1 : 0), 1, encode_task(k, i + 1, col));
                 if (k + 1 < A.steps) {
                     if (i == k + 1)
-                        q_signal(Q, ((size_t)(k + 1) * A.p + i) * base + col, 1, 0, encode_task(k + 1, i, col));
+                        q_signal(Q, apply32_cnt(A, 0, k + 1, i, col), 1, 0, encode_task(k + 1, i, col));
                     else
-                        q_signal(Q, ((size_t)(k + 1) * A.p + i) * base + col, 2, 1, encode_task(k + 1, i, col));
+                        q_signal(Q, apply32_cnt(A, 0, k + 1, i, col), 2, 1, encode_task(k + 1, i, col));
                 }
             }
             __threadfence();
@@ -340,10 +369,12 @@ constexpr int DOT_BLOCKS = 152;
 constexpr int GMRES_RESTART = 40;
 
 struct RefineLayout {
-    size_t tiles32, T32, rinv, X, sched, vecs, dots, flag, end;
-    size_t sched_bytes;
+    size_t tiles32, T32, T2_32, rinv, X, sched, vecs, dots, flag, end;
+    size_t sched_bytes, cnt_bytes;
+    unsigned long long nlb, nsb;   // queue capacities: DLARFB; DSSRFB + DTTMQR
     int64_t m, n;
     int p, q, steps, S;
+    TGraph G;
 };
 
 RefineLayout refine_layout(const tileqr_desc *d)
@@ -360,18 +391,23 @@ RefineLayout refine_layout(const tileqr_desc *d)
     off += align256((size_t)d->p * d->q * 128 * 128 * 4);
     R.T32 = off;
     off += align256((size_t)d->p * d->q * d->ib * 128 * 4);
+    R.T2_32 = off;
+    if (d->T2 != nullptr)
+        off += align256((size_t)d->p * d->q * d->ib * 128 * 4);
     R.rinv = off;
     off += align256((size_t)d->q * 128 * 128 * 4);
     R.X = off;
     off += align256((size_t)d->p * 128 * 4);
-    // scheduler of the one-column FP32 apply: control block, counters, 2 queues
-    const unsigned long long nlb = (unsigned long long)R.steps;
-    unsigned long long nsb = 0;
-    for (int k = 0; k < R.steps; k++)
-        nsb += (unsigned long long)(d->p - k - 1);
+    // scheduler of the one-column FP32 apply: control block, counters (a
+    // second bank for the tree's merges), 2 queues
+    R.G = make_graph(d->p, d->q, d->T2 != nullptr ? d->domain : 0);
+    unsigned long long cnt[2];
+    ga_count(R.G, cnt);
+    R.nlb = cnt[0];
+    R.nsb = cnt[1];
+    R.cnt_bytes = align256((size_t)(R.G.H < R.G.p ? 2 : 1) * R.steps * d->p * 4);
     R.sched = off;
-    R.sched_bytes = 256 + align256((size_t)R.steps * d->p * 4) + align256((nlb ? nlb : 1) * 8) +
-                    align256((nsb ? nsb : 1) * 8);
+    R.sched_bytes = 256 + R.cnt_bytes + align256((R.nlb ? R.nlb : 1) * 8) + align256((R.nsb ? R.nsb : 1) * 8);
     off += R.sched_bytes;
     // FP64 vectors: r (m), b copy (m), d (n), w (m), V (m x (restart+1)), Z (n x restart)
     const int64_t mm = d->m > d->n ? d->m : d->n;
@@ -439,16 +475,15 @@ struct Refiner {
         Apply32Args a;
         a.tiles = (const float *)(ws + L.tiles32);
         a.T = (const float *)(ws + L.T32);
+        a.T2 = d->T2 != nullptr ? (const float *)(ws + L.T2_32) : nullptr;
         a.X = X;
         a.p = L.p;
         a.steps = L.steps;
         a.ncol = 1;
         a.S = L.S;
-        const size_t cnt_bytes = align256((size_t)L.steps * L.p * 4);
-        const unsigned long long nlb = (unsigned long long)L.steps;
-        unsigned long long nsb = 0;
-        for (int k = 0; k < L.steps; k++)
-            nsb += (unsigned long long)(L.p - k - 1);
+        a.G = L.G;
+        const size_t cnt_bytes = L.cnt_bytes;
+        const unsigned long long nlb = L.nlb, nsb = L.nsb;
         Queues Q;
         Q.ctrl = (SchedCtrl *)sched;
         Q.cnt = (unsigned int *)(sched + 256);
@@ -467,7 +502,10 @@ struct Refiner {
         if ((unsigned)grid > Q.total)
             grid = (int)Q.total;
         if (grid > 0) {
-            k_apply32_dag<<<grid, 128, 0, st>>>(a, Q);
+            if (L.G.H < L.G.p)
+                k_apply32_dag<true><<<grid, 128, 0, st>>>(a, Q);
+            else
+                k_apply32_dag<false><<<grid, 128, 0, st>>>(a, Q);
             count_launch();
         }
         // R^{-1} on the first q blocks
@@ -522,8 +560,7 @@ extern "C" int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_
         return -6;
     if (!(tol > 0.0))
         return -7;
-    // the FP32 correction solve replays Algorithm 2's flat graph only
-    if (d->nb != 128 || d->T2 != nullptr)
+    if (d->nb != 128)
         return TILEQR_ERR_UNSUPPORTED;
     const RefineLayout L = refine_layout(d);
     if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < L.end)
@@ -557,7 +594,7 @@ extern "C" int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_
             int dev = 0, nsm = 0, per = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply32_dag, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply32_dag<true>, 128, 0);
             grid = nsm * (per > 0 ? per : 1);
             cudaFuncSetAttribute(k_inv_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (128 * 129 + 128) * 8);
         }
@@ -569,6 +606,10 @@ extern "C" int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_
     const size_t ntile = (size_t)d->p * d->q * 128 * 128, nT = (size_t)d->p * d->q * d->ib * 128;
     k_to_f32<<<4 * DOT_BLOCKS, 256, 0, st>>>(d->tiles, (float *)(R.ws + L.tiles32), ntile);
     k_to_f32<<<DOT_BLOCKS, 256, 0, st>>>(d->T, (float *)(R.ws + L.T32), nT);
+    if (d->T2 != nullptr) {
+        k_to_f32<<<DOT_BLOCKS, 256, 0, st>>>(d->T2, (float *)(R.ws + L.T2_32), nT);
+        count_launch();
+    }
     k_inv_diag<<<d->q, 128, (128 * 129 + 128) * 8, st>>>(d->tiles, d->p, d->q, d->n, (float *)(R.ws + L.rinv), flag);
     count_launch(3);
     if (cudaGetLastError() != cudaSuccess)

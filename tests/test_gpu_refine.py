@@ -66,3 +66,23 @@ def test_refine_full_size_16384(tq):
     relres = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
     assert info.converged == 1 and relres <= 1e-12, (info.as_dict(), relres)
     assert np.linalg.norm(x - xt) / np.linalg.norm(xt) <= kappa * 1e-12
+
+
+@pytest.mark.parametrize("m,n,h", [(8192, 512, 4), (16384, 384, 8), (4096, 512, 0)])
+def test_refine_tall_tree_mixed(tq, m, n, h):
+    """Tall A with TF32 updates, tree form (domain h; 0 = Algorithm 2's flat
+    tree) and a consistent right-hand side b = A x_true: the FP32 correction
+    solve replays the tree's apply graph (DLARFB, DSSRFB, DTTMQR) and the
+    refinement reaches the FP64 bar."""
+    A = inputs.normal_matrix(m, n, seed=40 + h)
+    xt = inputs.normal_matrix(n, 1, seed=41).reshape(-1)
+    b = A @ xt
+    Ad = tq.to_device_colmajor(A)
+    f = (tq.tileqr_factor_tree(Ad, 128, 16, h, precision=tq.TILEQR_TF32) if h
+         else tq.tileqr_factor(Ad, 128, 16, precision=tq.TILEQR_TF32)).check()
+    x, info = f.solve_refine(Ad, torch.from_numpy(b).cuda(), max_iter=40, tol=1e-12)
+    x = x.cpu().numpy()
+    relres = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    assert info.converged == 1 and relres <= 1e-12, (info.as_dict(), relres)
+    assert info.initial_rel_residual > 1e-9
+    assert np.linalg.norm(x - xt) / np.linalg.norm(xt) <= 1e-11

@@ -210,8 +210,9 @@ def test_tree_argument_errors(tq):
     assert rc == -7
     rc = lib.tileqr_factor_tree(10, 10, ctypes.c_void_p(1), 10, 64, 16, 2, 9, 0, None, 0, None, ctypes.byref(d))
     assert rc == -8
+    # refinement needs nb 128 (its FP32 correction solve), any domain size
     A = tq.to_device_colmajor(inputs.normal_matrix(600, 128, seed=1))
-    f = tq.tileqr_factor_tree(A, 128, 16, 2).check()
+    f = tq.tileqr_factor_tree(A, 64, 16, 2).check()
     with pytest.raises(tq.TileQRError) as e:
         f.solve_refine(A, A[:, 0].contiguous())
     assert e.value.code == tq.TILEQR_ERR_UNSUPPORTED
