@@ -1,5 +1,6 @@
-// refine.cu -- least-squares solve with FP64 iterative refinement for the
-// mixed-precision factorization (square or tall A, one right-hand side).
+// refine.cu -- solve of A x = b with FP64 iterative refinement for the
+// mixed-precision factorization (square A, or tall A with b in its range; one
+// right-hand side).  The stopping test is the FP64 residual ||b - A x||.
 //
 // The correction solves use an FP32 copy of the factors: M^{-1} v =
 // R^{-1} (Q^T v)(0:n) with Q^T applied as the factorization's task graph
