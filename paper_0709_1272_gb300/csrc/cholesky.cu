@@ -76,7 +76,7 @@ __global__ void k_tile2cm_lower(const double *__restrict__ tiles, int nb, int p,
 }
 
 template <int NB>
-__global__ void __launch_bounds__(NT, 1) k_chol_dag(CholArgs C, Queues Q)
+__global__ void __launch_bounds__(NT, 2) k_chol_dag(CholArgs C, Queues Q)
 {
     extern __shared__ double sm[];
     __shared__ unsigned long long s_code;
@@ -198,7 +198,12 @@ static int launch_chol_t(const CholLayout &L, char *ws, cudaStream_t st, unsigne
     Q.withheld = ~0ull;
     Q.trace = trace;
     Q.trace_cap = trace_cap;
-    int g = grid;
+    // two task CTAs per SM pay when the graph has the parallelism for them
+    // (average about p^2 / 9 ready tasks); below 64 tile rows the critical
+    // path rules, and a task alone on its SM finishes sooner
+    int g = L.p >= 64 ? grid : grid / 2;
+    if (g < 1)
+        g = 1;
     if ((unsigned)g > L.total)
         g = (int)L.total;
     k_chol_dag<NB><<<g, NT, smem, st>>>(C, Q);
