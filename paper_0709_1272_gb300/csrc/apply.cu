@@ -65,9 +65,10 @@ __global__ void __launch_bounds__(NT, 1) k_apply_dag(ApplyArgs A, Queues Q)
             }
         }
     }
+    unsigned int ticket = NO_TICKET;   // thread 0's bulk-level claim
     for (;;) {
         if (threadIdx.x == 0)
-            s_cmd = q_acquire(Q, s_code);
+            s_cmd = q_acquire(Q, s_code, ticket);
         __syncthreads();
         if (s_cmd != CMD_RUN)
             break;

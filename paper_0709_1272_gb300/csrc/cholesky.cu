@@ -88,9 +88,10 @@ __global__ void __launch_bounds__(NT, 2) k_chol_dag(CholArgs C, Queues Q)
         else
             q_push(Q, 0, encode_task(0, 0, 0));
     }
+    unsigned int ticket = NO_TICKET;   // thread 0's bulk-level claim
     for (;;) {
         if (threadIdx.x == 0)
-            s_cmd = q_acquire(Q, s_code);
+            s_cmd = q_acquire(Q, s_code, ticket);
         __syncthreads();
         if (s_cmd != CMD_RUN)
             break;

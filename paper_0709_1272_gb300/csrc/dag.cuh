@@ -156,25 +156,35 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_fac
                 q_push(Q, kind_prio(K_GEQRT), encode_task(0, g_head(F.G, 0, d), 0));
         }
     }
+    // Thread ACQ claims the tasks; after each task it claims the next one
+    // while warp 0 signals the finished task's successors, so the claim's
+    // round trips to L2 overlap the release.
+    constexpr int ACQ = 32;
+    unsigned int ticket = NO_TICKET;   // thread ACQ's bulk-level claim
+    if (threadIdx.x == ACQ)
+        s_cmd = q_acquire(Q, s_code, ticket);
     for (;;) {
-        if (threadIdx.x == 0)
-            s_cmd = q_acquire(Q, s_code);
         __syncthreads();
         if (s_cmd != CMD_RUN)
             break;
+        const unsigned long long code = s_code;
         int k, i, j;
-        decode_task(s_code, k, i, j);
-        const int kind = g_kind(F.G, decode_tt(s_code), k, i, j);
+        decode_task(code, k, i, j);
+        const int kind = g_kind(F.G, decode_tt(code), k, i, j);
         const unsigned long long t0 = Q.trace ? globaltimer_ns() : 0ull;
         run_task<NB, S, MIXED>(sm, F, kind, k, i, j, tmem, s_mbar, mphase, &Q.ctrl->error);
         __syncthreads();
-        release_graph(Q, F.G, kind, k, i, j);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (Q.trace)
-                trace_record(Q, s_code, t0, globaltimer_ns());
-            __threadfence();
-            atomicAdd(&Q.ctrl->completed, 1u);
+        if (threadIdx.x < 32) {
+            release_graph(Q, F.G, kind, k, i, j, threadIdx.x, 32);
+            __syncwarp();
+            if (threadIdx.x == 0) {
+                if (Q.trace)
+                    trace_record(Q, code, t0, globaltimer_ns());
+                __threadfence();
+                atomicAdd(&Q.ctrl->completed, 1u);
+            }
+        } else if (threadIdx.x == ACQ) {
+            s_cmd = q_acquire(Q, s_code, ticket);
         }
     }
     if (MIXED) {
@@ -221,7 +231,7 @@ __host__ __device__ inline void decode_btask(unsigned long long c, int &mat, int
 // Successors of task (k, i, j) of matrix `mat` in the graph of Algorithm 2
 // (the flat tree: release_graph with one domain per step).
 __device__ static void release_batched(const Queues &Q, const FactorArgs &F, size_t cnt_off, int mat, int k, int i,
-                                       int j)
+                                       int j, int first, int stride)
 {
     const int p = F.p, q = F.q;
     const int kind = task_kind(i, j, k);
@@ -232,7 +242,7 @@ __device__ static void release_batched(const Queues &Q, const FactorArgs &F, siz
     case K_TSQRT: nsucc = (q - k - 1) + (i + 1 < p ? 1 : 0); break;
     default: nsucc = (i + 1 < p ? 1 : 0) + 1; break;
     }
-    for (int s = threadIdx.x; s < nsucc; s += NT) {
+    for (int s = first; s < nsucc; s += stride) {
         int ks, is, js;
         switch (kind) {
         case K_GEQRT:
@@ -295,42 +305,53 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
             }
         }
     }
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_cmd = q_acquire(Q, s_code);
-            if (s_cmd == CMD_RUN) {
-                int mat, k, i, j;
-                decode_btask(s_code, mat, k, i, j);
-                const MatInfo &mi = mats[mat];
-                s_F.tiles = mi.tiles;
-                s_F.T = mi.T;
-                s_F.T2 = nullptr;
-                s_F.TF = mi.TF;
-                s_F.TF2 = nullptr;
-                s_F.p = mi.p;
-                s_F.q = mi.q;
-                s_F.steps = mi.steps;
-                s_F.G = make_graph(mi.p, mi.q, 0);
-                s_cnt = mi.cnt_off;
-            }
+    // as in k_factor_dag: thread ACQ claims the next task (and loads its
+    // matrix's descriptor) while warp 0 releases the finished one
+    constexpr int ACQ = 32;
+    unsigned int ticket = NO_TICKET;   // thread ACQ's bulk-level claim
+    auto claim = [&]() {
+        s_cmd = q_acquire(Q, s_code, ticket);
+        if (s_cmd == CMD_RUN) {
+            int mat, k, i, j;
+            decode_btask(s_code, mat, k, i, j);
+            const MatInfo &mi = mats[mat];
+            s_F.tiles = mi.tiles;
+            s_F.T = mi.T;
+            s_F.T2 = nullptr;
+            s_F.TF = mi.TF;
+            s_F.TF2 = nullptr;
+            s_F.p = mi.p;
+            s_F.q = mi.q;
+            s_F.steps = mi.steps;
+            s_F.G = make_graph(mi.p, mi.q, 0);
+            s_cnt = mi.cnt_off;
         }
+    };
+    if (threadIdx.x == ACQ)
+        claim();
+    for (;;) {
         __syncthreads();
         if (s_cmd != CMD_RUN)
             break;
+        const unsigned long long code = s_code;
         int mat, k, i, j;
-        decode_btask(s_code, mat, k, i, j);
+        decode_btask(code, mat, k, i, j);
         const FactorArgs F = s_F;
         const size_t cnt_off = s_cnt;
         const unsigned long long t0 = Q.trace ? globaltimer_ns() : 0ull;
         run_task<NB, S, MIXED>(sm, F, task_kind(i, j, k), k, i, j, tmem, s_mbar, mphase, &Q.ctrl->error);
         __syncthreads();
-        release_batched(Q, F, cnt_off, mat, k, i, j);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (Q.trace)
-                trace_record(Q, s_code, t0, globaltimer_ns());
-            __threadfence();
-            atomicAdd(&Q.ctrl->completed, 1u);
+        if (threadIdx.x < 32) {
+            release_batched(Q, F, cnt_off, mat, k, i, j, threadIdx.x, 32);
+            __syncwarp();
+            if (threadIdx.x == 0) {
+                if (Q.trace)
+                    trace_record(Q, code, t0, globaltimer_ns());
+                __threadfence();
+                atomicAdd(&Q.ctrl->completed, 1u);
+            }
+        } else if (threadIdx.x == ACQ) {
+            claim();
         }
     }
     if (MIXED) {

@@ -148,9 +148,10 @@ __global__ void __launch_bounds__(NT, (LuCfg<NB, S>::CTAS_PER_SM)) k_lu_dag(LuAr
         else
             q_push(Q, kind_prio(K_GEQRT), encode_task(0, 0, 0));
     }
+    unsigned int ticket = NO_TICKET;   // thread 0's bulk-level claim
     for (;;) {
         if (threadIdx.x == 0)
-            s_cmd = q_acquire(Q, s_code);
+            s_cmd = q_acquire(Q, s_code, ticket);
         __syncthreads();
         if (s_cmd != CMD_RUN)
             break;
@@ -269,9 +270,10 @@ __global__ void __launch_bounds__(NT, 1) k_lu_apply_dag(LuApplyArgs A, Queues Q)
     if (blockIdx.x == 0)
         for (int u = threadIdx.x; u < A.nchunk; u += NT)
             q_push(Q, 0, encode_task(0, 0, u));
+    unsigned int ticket = NO_TICKET;   // thread 0's bulk-level claim
     for (;;) {
         if (threadIdx.x == 0)
-            s_cmd = q_acquire(Q, s_code);
+            s_cmd = q_acquire(Q, s_code, ticket);
         __syncthreads();
         if (s_cmd != CMD_RUN)
             break;

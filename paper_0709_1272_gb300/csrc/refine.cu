@@ -117,9 +117,10 @@ __global__ void __launch_bounds__(128) k_apply32_dag(Apply32Args A, Queues Q)
         for (int u = tid; u < A.ncol * nd0; u += 128)
             q_push(Q, 0, encode_task(0, TREE ? g_head(G, 0, u / A.ncol) : 0, u % A.ncol));
     }
+    unsigned int ticket = NO_TICKET;   // thread 0's bulk-level claim
     for (;;) {
         if (tid == 0)
-            s_cmd = q_acquire(Q, s_code);
+            s_cmd = q_acquire(Q, s_code, ticket);
         __syncthreads();
         if (s_cmd != CMD_RUN)
             break;

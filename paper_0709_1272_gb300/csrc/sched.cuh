@@ -4,7 +4,8 @@
 // onto one of four ready queues, one per priority level of Sec. 4 (DGEQRT >
 // DTSQRT > DLARFB > DSSRFB).  Workers (one CTA each) pop the highest-priority
 // ready task.  Queues are write-once arrays sized to the exact number of tasks
-// of their kind, so a slot is never reused and a pop is a CAS on the head.
+// of their kind, so a slot is never reused and a pop only advances the head
+// (a CAS, or on the bulk level an atomicAdd, see q_try_pop).
 //
 // Progress does not depend on CTA co-residency: a CTA only ever waits while
 // idle (never while holding a task), and every wait is bounded by a
@@ -60,9 +61,55 @@ __device__ __forceinline__ void q_push(const Queues &Q, int level, unsigned long
         atomicCAS(&Q.ctrl->error, 0, TILEQR_ERR_CUDA);  // cannot happen: capacities are exact
 }
 
-__device__ __forceinline__ bool q_try_pop(const Queues &Q, unsigned long long &code)
+// The last level holds the bulk of every graph (the DSSRFB-class updates),
+// and with short tasks (the tensor-core updates run in tens of microseconds)
+// the CTAs pop it several times per microsecond.  A compare-and-swap on its
+// head then fails and retries under contention, so while that level has more
+// than TICKET_MARGIN tasks queued a CTA claims the next slot with one
+// atomicAdd instead.  A claimed slot that has not been filled yet (the head
+// ran past the tail between the loads and the add) stays the CTA's "ticket":
+// its task will be this CTA's next bulk task, and until it is pushed the CTA
+// keeps popping the higher levels.  Every slot below the head is owned by
+// some CTA that runs its task once it is filled, so no ready task is ever
+// stranded; a ticket at or beyond the capacity claims nothing.
+constexpr int Q_BULK = K_NKIND - 1;
+constexpr unsigned int NO_TICKET = 0xFFFFFFFFu;
+constexpr unsigned int TICKET_MARGIN = 8;
+
+__device__ __forceinline__ bool q_try_pop(const Queues &Q, unsigned long long &code, unsigned int &ticket)
 {
+    unsigned int hd[K_NKIND], tl[K_NKIND];
+#pragma unroll
+    for (int l = 0; l < K_NKIND; l++) {
+        hd[l] = ld_relaxed_u32(&Q.ctrl->head[l]);
+        tl[l] = ld_relaxed_u32(&Q.ctrl->tail[l]);
+    }
     for (int lvl = 0; lvl < K_NKIND; lvl++) {
+        if (lvl == Q_BULK && ticket != NO_TICKET) {
+            const unsigned long long v = ld_acquire_u64(&Q.slot[lvl][ticket]);
+            if (v == 0ull)
+                return false;
+            code = v - 1ull;
+            ticket = NO_TICKET;
+            return true;
+        }
+        if (hd[lvl] >= Q.cap[lvl] || hd[lvl] >= tl[lvl])
+            continue;   // empty as of the loads
+        if (lvl == Q_BULK && tl[lvl] - hd[lvl] > TICKET_MARGIN) {
+            const unsigned int t = atomicAdd(&Q.ctrl->head[lvl], 1u);
+            if (t >= Q.cap[lvl])
+                return false;
+            // the slot is this CTA's; its push may still be in flight
+            for (int spin = 0; spin < 4; spin++) {
+                const unsigned long long v = ld_acquire_u64(&Q.slot[lvl][t]);
+                if (v != 0ull) {
+                    code = v - 1ull;
+                    return true;
+                }
+            }
+            ticket = t;
+            return false;
+        }
         for (;;) {
             const unsigned int h = ld_relaxed_u32(&Q.ctrl->head[lvl]);
             if (h >= Q.cap[lvl])
@@ -81,8 +128,10 @@ __device__ __forceinline__ bool q_try_pop(const Queues &Q, unsigned long long &c
 
 enum { CMD_RUN = 1, CMD_EXIT = 2 };
 
-// Thread 0 of a worker CTA: wait (bounded) for a ready task.
-__device__ __noinline__ static int q_acquire(const Queues &Q, unsigned long long &code)
+// Thread 0 of a worker CTA: wait (bounded) for a ready task.  `ticket` is
+// the CTA's claim on a bulk-level slot (NO_TICKET: none), kept by the caller
+// across calls.
+__device__ __noinline__ static int q_acquire(const Queues &Q, unsigned long long &code, unsigned int &ticket)
 {
     unsigned long long t_last = globaltimer_ns();
     unsigned int last_done = ld_relaxed_u32(&Q.ctrl->completed);
@@ -91,7 +140,7 @@ __device__ __noinline__ static int q_acquire(const Queues &Q, unsigned long long
     for (unsigned long long it = 0; it < max_iter; it++) {
         if (ld_relaxed_s32(&Q.ctrl->error) != 0)
             return CMD_EXIT;
-        if (q_try_pop(Q, code)) {
+        if (q_try_pop(Q, code, ticket)) {
             __threadfence();
             return CMD_RUN;
         }
