@@ -34,12 +34,15 @@ extern "C" {
 
 typedef struct CUstream_st *tileqr_stream_t; /* identical to cudaStream_t */
 
-/* Arithmetic of the trailing updates (DLARFB/DSSRFB).  Panels (DGEQRT,
- * DTSQRT: norms, tau, T factors) are always FP64. */
+/* Arithmetic of the trailing updates (DLARFB/DSSRFB, and DTTMQR in the tree
+ * form).  Panels (DGEQRT, DTSQRT, DTTQRT: norms, tau, T factors) are always
+ * FP64; with TILEQR_TF32 their in-tile trailing updates run in FP32. */
 enum {
     TILEQR_FP64 = 0,       /* every task in FP64 */
-    TILEQR_TF32 = 1,       /* updates as TF32 products, FP32 accumulation (reserved) */
-    TILEQR_SPLIT_BF16 = 2  /* updates as split-BF16 products, FP32 accumulation (reserved) */
+    TILEQR_TF32 = 1,       /* updates as 3xTF32 tensor-core products (tcgen05),
+                              FP32 accumulation; nb 128, ib 16 or 32, task graph only */
+    TILEQR_SPLIT_BF16 = 2  /* updates as split-BF16 products (declared, not built:
+                              TILEQR_ERR_UNSUPPORTED) */
 };
 
 /* How the task graph is executed. */
@@ -117,7 +120,8 @@ int tileqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int precision, s
  *   A, lda    device, column-major, lda >= max(1,m); read only
  *   nb, ib    tile size b and inner block size s; ib must divide nb.  Built
  *             combinations: nb in {64,128,256}, ib in {16,32}
- *   precision TILEQR_FP64 (others: TILEQR_ERR_UNSUPPORTED in this build)
+ *   precision TILEQR_FP64, or TILEQR_TF32 (nb 128, TILEQR_SCHED_DAG);
+ *             TILEQR_SPLIT_BF16 and other combinations: TILEQR_ERR_UNSUPPORTED
  *   schedule  TILEQR_SCHED_DAG or TILEQR_SCHED_BULK
  *   flags     TILEQR_FLAG_*
  *   workspace device, 256-byte aligned, >= tileqr_workspace_size() bytes

@@ -289,6 +289,54 @@ def test_solve_ls_consistent_and_inconsistent():
     assert np.linalg.norm(A.T @ r) / (np.linalg.norm(A) * np.linalg.norm(r)) <= 20 * n * EPS
 
 
+def _cholesky_solve_longdouble(G, c):
+    """G x = c for SPD G by Cholesky in np.longdouble (plain loops, small n)."""
+    n = G.shape[0]
+    L = np.zeros((n, n), dtype=np.longdouble)
+    for j in range(n):
+        d = G[j, j] - np.sum(L[j, :j] * L[j, :j])
+        L[j, j] = np.sqrt(d)
+        for i in range(j + 1, n):
+            L[i, j] = (G[i, j] - np.sum(L[i, :j] * L[j, :j])) / L[j, j]
+    y = np.zeros((n, c.shape[1]), dtype=np.longdouble)
+    for i in range(n):
+        y[i] = (c[i] - L[i, :i] @ y[:i]) / L[i, i]
+    x = np.zeros_like(y)
+    for i in reversed(range(n)):
+        x[i] = (y[i] - L[i + 1:, i] @ x[i + 1:]) / L[i, i]
+    return x
+
+
+def test_solve_ls_matches_long_double_normal_equations():
+    # the least-squares solution of a well-conditioned inconsistent system is
+    # the solution of A^T A x = A^T b; formed and solved in extended precision
+    # it is an independent check of solve_ls (Q^T b, then R x = (Q^T b)(0:n))
+    m, n = 60, 14
+    A = inputs.uniform_matrix(m, n, seed=61)
+    B = inputs.normal_matrix(m, 2, seed=62)
+    Al, Bl = A.astype(np.longdouble), B.astype(np.longdouble)
+    Xl = _cholesky_solve_longdouble(Al.T @ Al, Al.T @ Bl).astype(np.float64)
+    f = oracle.tiled_qr(A, 8, 4)
+    X = oracle.solve_ls(f, B.copy())
+    assert _rel(X, Xl) <= 50 * n * EPS * np.linalg.cond(A)
+
+
+@pytest.mark.parametrize("e", [-1000, -900, -600, 600, 1000])
+def test_extreme_magnitudes_scale_exactly(e):
+    # scaling A by 2^e is exact, and so is R(2^e A) = 2^e R(A) in exact
+    # arithmetic; at |e| = 900..1000 the squares of the entries under- or
+    # overflow, so a plain sum of squares would give a zero or infinite norm
+    # (the scaled accumulation of the Householder step must keep R finite and
+    # accurate)
+    m, n, nb, ib = 70, 45, 16, 4
+    A = inputs.uniform_matrix(m, n, seed=63)
+    c = np.ldexp(1.0, e)
+    R = oracle.tiled_qr(A, nb, ib).R()
+    Rc = oracle.tiled_qr(A * c, nb, ib).R()
+    assert np.all(np.isfinite(Rc))
+    assert _rel(Rc / c, R) <= 20 * n * EPS
+
+
 def test_solve_ls_singular_reports_zero_pivot():
     A = np.zeros((6, 3), order="F")
     A[:, 0] = 1.0
