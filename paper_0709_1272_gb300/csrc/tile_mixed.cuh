@@ -74,6 +74,27 @@ __device__ __forceinline__ double mixed_v_elem(const double *Vt, int trow, int t
     return ldcg(Vt + (size_t)tcol * 128 + trow);
 }
 
+// Four consecutive entries V(trow..trow+3, tcol) of a reflector tile (trow a
+// multiple of 4), read as two 16-byte loads and masked like mixed_v_elem.
+template <int VK>
+__device__ __forceinline__ void mixed_v_elem4(const double *Vt, int trow, int tcol, double (&v)[4])
+{
+    const double2 *p = (const double2 *)(Vt + (size_t)tcol * 128 + trow);
+    const double2 a = __ldcg(p), b = __ldcg(p + 1);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        const int r = trow + e;
+        if (VK == VK_UNIT)
+            v[e] = (r < tcol) ? 0.0 : (r == tcol ? 1.0 : v[e]);
+        if (VK == VK_UPPER && r > tcol)
+            v[e] = 0.0;
+    }
+}
+
 // Split four FP32 values (consecutive K of one operand row) and store them
 // as one 16-byte vector in each of the hi and lo operand buffers.
 __device__ __forceinline__ void store_split4(unsigned char *sm, int off_hi, int off_lo, uint32_t byte_off,
@@ -376,12 +397,15 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         double v[4][4], c[4][4];
 #pragma unroll
         for (int x = 0; x < 4; x++) {
+            // four consecutive rows of column m of V and C: two 16-byte loads each
             const int m = p_row(x), j = p_kgrp(x), r = r0 + 4 * j;
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                v[x][e] = mixed_v_elem<VK>(Vt, r + e, m);
-                c[x][e] = ldcg(Ct + (size_t)m * NB + r + e);
-            }
+            mixed_v_elem4<VK>(Vt, r, m, v[x]);
+            const double2 *cp = (const double2 *)(Ct + (size_t)m * NB + r);
+            const double2 c01 = __ldcg(cp), c23 = __ldcg(cp + 1);
+            c[x][0] = c01.x;
+            c[x][1] = c01.y;
+            c[x][2] = c23.x;
+            c[x][3] = c23.y;
         }
 #pragma unroll
         for (int x = 0; x < 4; x++) {
