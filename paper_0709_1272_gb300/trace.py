@@ -27,19 +27,73 @@ def decode(records: np.ndarray, domain: int = 0):
     return {"k": k, "i": i, "j": j, "kind": kind, "t0": t0, "t1": t1, "sm": r[:, 3].astype(np.int64)}
 
 
+def slots_per_sm(d) -> np.ndarray:
+    """Most tasks in flight at once on each SM (the worker CTAs it held)."""
+    nsm = int(d["sm"].max()) + 1
+    out = np.zeros(nsm, dtype=np.int64)
+    for sm in np.unique(d["sm"]):
+        sel = d["sm"] == sm
+        t = np.concatenate([d["t0"][sel], d["t1"][sel]])
+        step = np.concatenate([np.ones(int(sel.sum()), np.int64), -np.ones(int(sel.sum()), np.int64)])
+        order = np.lexsort((step, t))   # at equal times an end before a start
+        out[sm] = int(np.cumsum(step[order]).max())
+    return out
+
+
 def summary(records: np.ndarray, domain: int = 0) -> dict:
+    """Per-kind task counts and mean durations, and the occupancy of the
+    worker slots: busy_fraction = task time / (wall x slots), slots = the
+    tasks in flight at once summed over the SMs (one or two CTAs per SM)."""
     d = decode(records, domain)
     t_begin, t_end = int(d["t0"].min()), int(d["t1"].max())
     wall = (t_end - t_begin) * 1e-9
     dur = (d["t1"] - d["t0"]) * 1e-9
-    nsm = int(d["sm"].max()) + 1
-    out = {"tasks": int(len(dur)), "wall_s": wall, "busy_fraction": float(dur.sum() / (wall * nsm)),
-           "per_kind": {}}
+    slots = int(slots_per_sm(d).sum())
+    out = {"tasks": int(len(dur)), "wall_s": wall, "slots": slots,
+           "busy_fraction": float(dur.sum() / (wall * slots)) if wall > 0 else 1.0,
+           "idle_per_task_us": float((wall * slots - dur.sum()) / len(dur) * 1e6), "per_kind": {}}
     for kd, name in enumerate(KINDS):
         sel = d["kind"] == kd
         if sel.any():
             out["per_kind"][name] = {"count": int(sel.sum()), "mean_us": float(dur[sel].mean() * 1e6),
                                      "total_sm_s": float(dur[sel].sum())}
+    return out
+
+
+def ready_waits(records: np.ndarray, graph, domain: int = 0) -> dict:
+    """Time from a task's readiness (the end of its last predecessor; the
+    first task's start for tasks without one) to its start, per kind.
+    `graph` = (tasks, ndeps, succ_ptr, succ) of tileqr_task_graph (what = 0,
+    the QR factorization) for the same shape, nb and domain.  Long waits with idle slots point at the scheduler;
+    long waits with busy slots at a shortage of workers."""
+    d = decode(records, domain)
+    tasks, _, ptr, succ = graph
+    index = {}
+    for g in range(len(tasks)):
+        kind, i, j, k = (int(x) for x in tasks[g])
+        index[(1 if kind >= 4 else 0, k, i, j)] = g
+    tt = np.where(d["kind"] >= 4, 1, 0)
+    gid = np.array([index[(int(tt[n]), int(d["k"][n]), int(d["i"][n]), int(d["j"][n]))]
+                    for n in range(len(d["t0"]))], dtype=np.int64)
+    if len(set(gid.tolist())) != len(tasks) or len(gid) != len(tasks):
+        raise ValueError("the trace does not hold every task of the graph exactly once")
+    start = np.empty(len(tasks), np.int64)
+    end = np.empty(len(tasks), np.int64)
+    start[gid] = d["t0"]
+    end[gid] = d["t1"]
+    ready = np.full(len(tasks), int(d["t0"].min()), np.int64)
+    src = np.repeat(np.arange(len(tasks)), np.diff(ptr))
+    np.maximum.at(ready, np.asarray(succ, dtype=np.int64), end[src])
+    wait = (start - ready) * 1e-3   # us
+    kind_of = tasks[:, 0]
+    out = {}
+    for kd, name in enumerate(KINDS):
+        sel = kind_of == kd
+        if sel.any():
+            w = wait[sel]
+            out[name] = {"count": int(sel.sum()), "mean_us": float(w.mean()),
+                         "median_us": float(np.median(w)), "p90_us": float(np.percentile(w, 90)),
+                         "min_us": float(w.min())}
     return out
 
 

@@ -1,0 +1,102 @@
+"""Host-side trace analysis (paper_0709_1272_gb300/trace.py) on synthetic
+traces of the QR task graph: a list schedule simulated here on the CPU, so
+every start, end and readiness time is known."""
+import heapq
+
+import numpy as np
+import pytest
+
+from paper_0709_1272_gb300 import trace
+
+DUR_NS = {0: 5000, 1: 4000, 2: 2000, 3: 3000, 4: 2500, 5: 1500}   # per kind
+
+
+@pytest.fixture(scope="module")
+def tq():
+    from paper_0709_1272_gb300 import build
+    build.build()
+    from paper_0709_1272_gb300 import tileqr
+    tileqr.load()
+    return tileqr
+
+
+def _simulate(graph, nsm, per_sm, claim_ns):
+    """Greedy FIFO list schedule of the graph on nsm x per_sm workers; a
+    worker spends claim_ns between two tasks.  Returns the trace records and
+    the readiness time of every task."""
+    tasks, ndeps, ptr, succ = graph
+    nt = len(tasks)
+    left = ndeps.astype(np.int64).copy()
+    ready_t = np.zeros(nt, np.int64)
+    queue = [g for g in range(nt) if left[g] == 0]
+    free = [(0, w) for w in range(nsm * per_sm)]   # (time the worker is free, worker)
+    heapq.heapify(free)
+    running = []                                  # (end, task, worker)
+    rec = np.zeros((nt, 4), np.int64)
+    n = 0
+    while n < nt:
+        if queue and free:
+            t_free, w = heapq.heappop(free)
+            g = queue.pop(0)
+            t0 = max(t_free + claim_ns, ready_t[g])
+            t1 = t0 + DUR_NS[int(tasks[g, 0])]
+            kind, i, j, k = (int(x) for x in tasks[g])
+            code = (np.uint64(1 if kind >= 4 else 0) << np.uint64(63)) | (np.uint64(k) << np.uint64(42)) | \
+                (np.uint64(i) << np.uint64(21)) | np.uint64(j)
+            rec[n] = [np.int64(code.astype(np.int64)), t0, t1, w // per_sm]
+            n += 1
+            heapq.heappush(running, (t1, g, w))
+            continue
+        t1, g, w = heapq.heappop(running)
+        heapq.heappush(free, (t1, w))
+        for v in succ[ptr[g]:ptr[g + 1]]:
+            left[v] -= 1
+            ready_t[v] = max(ready_t[v], t1)
+            if left[v] == 0:
+                queue.append(int(v))
+    return rec, ready_t
+
+
+@pytest.mark.parametrize("m,n,nb,domain,per_sm", [(1280, 1280, 128, 0, 2), (2560, 512, 128, 4, 1),
+                                                  (640, 900, 64, 0, 1)])
+def test_summary_and_ready_waits(tq, m, n, nb, domain, per_sm):
+    graph = tq.tileqr_task_graph(m, n, nb, domain)
+    rec, ready_t = _simulate(graph, nsm=3, per_sm=per_sm, claim_ns=700)
+    s = trace.summary(rec, domain)
+    assert s["tasks"] == len(graph[0])
+    d = trace.decode(rec, domain)
+    # the kinds decoded from the codes are the graph's own
+    tasks = graph[0]
+    lookup = {(int(t[3]), int(t[1]), int(t[2])): int(t[0]) for t in tasks if t[0] < 4}
+    for n_ in range(len(rec)):
+        if d["kind"][n_] < 4:
+            assert lookup[(int(d["k"][n_]), int(d["i"][n_]), int(d["j"][n_]))] == d["kind"][n_]
+    # slots: the simulated workers (every SM ran per_sm tasks at once at some time)
+    assert s["slots"] == 3 * per_sm
+    wall = (rec[:, 2].max() - rec[:, 1].min()) * 1e-9
+    busy = ((rec[:, 2] - rec[:, 1]) * 1e-9).sum()
+    assert s["busy_fraction"] == pytest.approx(busy / (wall * 3 * per_sm))
+    assert 0 < s["busy_fraction"] <= 1
+    # ready waits against the simulator's own readiness times
+    w = trace.ready_waits(rec, graph, domain)
+    start = {}
+    for n_ in range(len(rec)):
+        start[(int(d["kind"][n_]) >= 4, int(d["k"][n_]), int(d["i"][n_]), int(d["j"][n_]))] = rec[n_, 1]
+    t_first = rec[:, 1].min()
+    for kd, name in enumerate(trace.KINDS):
+        sel = [g for g in range(len(tasks)) if tasks[g, 0] == kd]
+        if not sel:
+            assert name not in w
+            continue
+        ref = [(start[(kd >= 4, int(tasks[g, 3]), int(tasks[g, 1]), int(tasks[g, 2]))] -
+                max(ready_t[g], t_first)) * 1e-3 for g in sel]
+        assert w[name]["count"] == len(sel)
+        assert w[name]["mean_us"] == pytest.approx(np.mean(ref))
+        assert w[name]["min_us"] >= 0
+
+
+def test_ready_waits_rejects_an_incomplete_trace(tq):
+    graph = tq.tileqr_task_graph(512, 512, 128)
+    rec, _ = _simulate(graph, nsm=2, per_sm=1, claim_ns=0)
+    with pytest.raises(ValueError):
+        trace.ready_waits(rec[:-1], graph)
