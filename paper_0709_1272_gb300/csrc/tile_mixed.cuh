@@ -388,6 +388,17 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         __syncwarp();
     };
 
+    // One thread asks L2 for the task's tiles and T^T operand at once: the
+    // first phase streams V and C from HBM at full rate instead of one
+    // 32-row round at a time, and the later phases (B, T^T, the second reads
+    // of V and C) find them in L2.
+    if (tid == 0) {
+        tc::prefetch_l2(Vt, NB * NB * 8);
+        tc::prefetch_l2(Ct, NB * NB * 8);
+        if (Bt)
+            tc::prefetch_l2(Bt, NB * NB * 8);
+        tc::prefetch_l2(TFg, TF_BYTES);
+    }
     // ---- P = V^T C: A = V^T (row = reflector, K = tile row), B = C^T (row =
     // column); sets at 0 and 4 OPB
     for (int rr = 0; rr < NB / KC; rr++) {
