@@ -97,6 +97,37 @@ def ready_waits(records: np.ndarray, graph, domain: int = 0) -> dict:
     return out
 
 
+def span_bounds(graph, dur_by_kind: dict, slots: int) -> dict:
+    """Lower bounds on the span of the task graph `graph` (tileqr_task_graph
+    output) with a duration per task kind (seconds, keyed by the kind codes
+    0..5) on `slots` workers: the critical path (longest chain of dependent
+    tasks) and the work divided by the slots.  A list schedule never beats the
+    larger of the two; comparing a trace's span with them tells whether the
+    run was bound by the graph, by the work or by the scheduler."""
+    tasks, ndeps, ptr, succ = graph
+    nt = len(tasks)
+    dur = np.array([dur_by_kind[int(k)] for k in tasks[:, 0]], dtype=np.float64)
+    # longest path by Kahn's order over the successor lists
+    left = ndeps.astype(np.int64).copy()
+    finish = np.zeros(nt)
+    start = np.zeros(nt)
+    order = [g for g in range(nt) if left[g] == 0]
+    head = 0
+    while head < len(order):
+        u = order[head]
+        head += 1
+        finish[u] = start[u] + dur[u]
+        for v in succ[ptr[u]:ptr[u + 1]]:
+            start[v] = max(start[v], finish[u])
+            left[v] -= 1
+            if left[v] == 0:
+                order.append(int(v))
+    if len(order) != nt:
+        raise ValueError("the graph has a cycle or a task that is never released")
+    return {"critical_path_s": float(finish.max()) if nt else 0.0, "work_s": float(dur.sum()),
+            "work_per_slot_s": float(dur.sum() / slots)}
+
+
 def to_chrome(records: np.ndarray, path: str, domain: int = 0) -> None:
     d = decode(records, domain)
     base = int(d["t0"].min())

@@ -100,3 +100,41 @@ def test_ready_waits_rejects_an_incomplete_trace(tq):
     rec, _ = _simulate(graph, nsm=2, per_sm=1, claim_ns=0)
     with pytest.raises(ValueError):
         trace.ready_waits(rec[:-1], graph)
+
+
+def test_span_bounds_closed_forms(tq):
+    # one tile column: DGEQRT then the chain of p - 1 DTSQRTs (Algorithm 2's
+    # flat tree), nothing else
+    p, nb = 9, 64
+    graph = tq.tileqr_task_graph(p * nb, nb, nb)
+    dur = {0: 5.0, 1: 3.0, 2: 1.0, 3: 2.0, 4: 1.0, 5: 1.0}
+    b = trace.span_bounds(graph, dur, slots=4)
+    assert b["critical_path_s"] == pytest.approx(5.0 + (p - 1) * 3.0)
+    assert b["work_s"] == pytest.approx(5.0 + (p - 1) * 3.0)
+    # square flat graph with updates of zero duration: the longest chain of
+    # panel tasks, against a brute-force longest path over the same edges
+    q = 6
+    graph = tq.tileqr_task_graph(q * nb, q * nb, nb)
+    dur0 = {0: 5.0, 1: 3.0, 2: 0.0, 3: 0.0, 4: 0.0, 5: 0.0}
+    b = trace.span_bounds(graph, dur0, slots=4)
+    # brute force over the dependency table (longest path by recursion)
+    tasks, ndeps, ptr, succ = graph
+    preds = {g: [] for g in range(len(tasks))}
+    for u in range(len(tasks)):
+        for v in succ[ptr[u]:ptr[u + 1]]:
+            preds[int(v)].append(u)
+    memo = {}
+
+    def fin(g):
+        if g not in memo:
+            memo[g] = max((fin(u) for u in preds[g]), default=0.0) + dur0[int(tasks[g, 0])]
+        return memo[g]
+
+    assert b["critical_path_s"] == pytest.approx(max(fin(g) for g in range(len(tasks))))
+    # the simulated list schedule is never shorter than either bound
+    rec, _ = _simulate(graph, nsm=2, per_sm=2, claim_ns=0)
+    durs = {k: v * 1e-9 for k, v in DUR_NS.items()}
+    b = trace.span_bounds(graph, durs, slots=4)
+    span = (rec[:, 2].max() - rec[:, 1].min()) * 1e-9
+    assert span >= b["critical_path_s"] - 1e-12
+    assert span >= b["work_per_slot_s"] - 1e-12
