@@ -21,6 +21,17 @@
  *    tileqr_status(), which synchronises the stream.
  *  - Return codes follow LAPACK: 0 = success, -i = argument i is illegal,
  *    positive = one of the TILEQR_ERR_* codes below.
+ *  - Every scheduler wait is bounded: a persistent kernel that sees no
+ *    progress for 10 s (or TILEQR_WATCHDOG_MS milliseconds, if that
+ *    environment variable is set when a call is made) gives up and records
+ *    TILEQR_ERR_TIMEOUT.
+ *  - Threads and devices: calls work on the device current in the calling
+ *    thread.  The one-time launch set-up (shared-memory opt-in, persistent
+ *    grid size) is made per device and kernel under a lock, so several host
+ *    threads and several devices may use the library at once; calls that
+ *    share a workspace (or tileqr_factor_noalloc's scratch) must not overlap
+ *    on the GPU.  The instrumentation hooks below (trace buffer, profile
+ *    events) are process-wide settings.
  */
 #ifndef TILEQR_H
 #define TILEQR_H
@@ -182,8 +193,14 @@ int tileqr_factor_tree(int64_t m, int64_t n, const double *A, int64_t lda, int n
  * call clears it on its stream before use.  Calls whose executions overlap on
  * the GPU (other streams, other host threads) race on it, and the device-side
  * status read by tileqr_status(out) is only valid until the next call of this
- * entry point on the same device.  Asynchronous; returns 0, -i,
- * TILEQR_ERR_UNSUPPORTED, TILEQR_ERR_SCRATCH_LIMIT or TILEQR_ERR_CUDA. */
+ * entry point on the same device.  The looked-up address is kept for the
+ * life of the process: do not call this entry point on a device after
+ * cudaDeviceReset (or any other reset of its primary context), which reloads
+ * the library's module at another address.  The scheduler watchdog honours
+ * TILEQR_WATCHDOG_MS like tileqr_factor; the task trace (tileqr_set_trace)
+ * and the profile events (tileqr_set_profile_events) are not recorded by this
+ * entry point.  Asynchronous; returns 0, -i, TILEQR_ERR_UNSUPPORTED,
+ * TILEQR_ERR_SCRATCH_LIMIT or TILEQR_ERR_CUDA. */
 int tileqr_factor_noalloc(int64_t m, int64_t n, const double *A, int64_t lda, int nb, int ib,
                           double *tiles, size_t tiles_bytes, double *T, size_t T_bytes,
                           tileqr_stream_t stream, tileqr_desc *out);

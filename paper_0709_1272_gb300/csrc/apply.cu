@@ -134,17 +134,10 @@ static int launch_apply_t(const WsLayout &L, const double *tiles, const double *
                           int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns)
 {
     constexpr size_t smem = F64Cfg<NB, S, APPLY_W>::SMEM;
-    static int grid_max = 0;
-    if (grid_max == 0) {
-        cudaFuncSetAttribute(k_apply_dag<NB, S, NOTRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0, nsm = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_dag<NB, S, NOTRANS>, NT, smem);
-        if (per_sm < 1)
-            return TILEQR_ERR_CUDA;
-        grid_max = nsm * per_sm;
-    }
+    int grid_max = 0;
+    const int rc = kernel_grid((const void *)k_apply_dag<NB, S, NOTRANS>, NT, smem, &grid_max);
+    if (rc)
+        return rc;
     ApplyArgs A;
     A.tiles = tiles;
     A.T = T;
@@ -272,12 +265,9 @@ int launch_trsm(const WsLayout &L, const double *tiles, double *Bt, int64_t ncp,
 {
     const int nchunk = (int)(ncp / 32);
     const size_t smem = (size_t)L.nb * 33 * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_trsm_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 33 * 8);
-        cudaFuncSetAttribute(k_trsm_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 33 * 8);
-        attr = true;
-    }
+    if (kernel_smem_optin((const void *)k_trsm_diag, 256 * 33 * 8) != 0 ||
+        kernel_smem_optin((const void *)k_trsm_update, 256 * 33 * 8) != 0)
+        return TILEQR_ERR_CUDA;
     for (int j = L.q - 1; j >= 0; j--) {
         k_trsm_diag<<<nchunk, NT, smem, st>>>(tiles, Bt, L.nb, L.p, ncp, j, L.n, flag);
         count_launch();

@@ -123,18 +123,13 @@ template <int NB, int S, bool MIXED>
 int launch_batched_t(const tileqr_batch *bt, cudaStream_t st)
 {
     constexpr size_t smem = DagCfg<NB, S, MIXED>::SMEM;
-    static int grid_dag = 0;
-    if (grid_dag == 0) {
-        cudaFuncSetAttribute(k_factor_dag_batched<NB, S, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        int dev = 0, nsm = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_dag_batched<NB, S, MIXED>, NT, smem);
-        if (per_sm < 1 || cudaGetLastError() != cudaSuccess)
-            return TILEQR_ERR_CUDA;
-        grid_dag = MIXED ? nsm : nsm * per_sm;
-    }
+    int grid_dag = 0;
+    int rc = kernel_grid((const void *)k_factor_dag_batched<NB, S, MIXED>, NT, smem, &grid_dag);
+    if (rc)
+        return rc;
+    // the mixed kernel runs one CTA per SM (256 of the 512 tensor-memory columns each)
+    if (MIXED && (rc = device_sm_count(&grid_dag)) != 0)
+        return rc;
     char *ws = (char *)bt->workspace;
     Queues Q;
     Q.ctrl = (SchedCtrl *)(ws + bt->off_ctrl);
@@ -144,9 +139,7 @@ int launch_batched_t(const tileqr_batch *bt, cudaStream_t st)
         Q.cap[t] = bt->cap[t];
     }
     Q.total = (unsigned int)bt->total_tasks;
-    const char *e = std::getenv("TILEQR_WATCHDOG_MS");
-    long ms = e ? std::atol(e) : 0;
-    Q.watchdog_ns = (unsigned long long)(ms > 0 ? ms : 10000) * 1000000ull;
+    Q.watchdog_ns = watchdog_ns_default();
     Q.withheld = ~0ull;
     Q.trace = nullptr;
     Q.trace_cap = 0;

@@ -173,17 +173,10 @@ static int launch_chol_t(const CholLayout &L, char *ws, cudaStream_t st, unsigne
                          unsigned long long *trace, unsigned int trace_cap)
 {
     constexpr size_t smem = CholCfg<NB>::SMEM;
-    static int grid = 0;
-    if (grid == 0) {
-        cudaFuncSetAttribute(k_chol_dag<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0, nsm = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_dag<NB>, NT, smem);
-        if (per_sm < 1 || cudaGetLastError() != cudaSuccess)
-            return TILEQR_ERR_CUDA;
-        grid = nsm * per_sm;
-    }
+    int grid = 0;
+    const int rc = kernel_grid((const void *)k_chol_dag<NB>, NT, smem, &grid);
+    if (rc)
+        return rc;
     CholArgs C;
     C.tiles = (double *)(ws + L.off_tiles);
     C.p = L.p;
@@ -267,9 +260,9 @@ extern "C" int tileqr_cholesky(int64_t n, const double *A, int64_t lda, int nb, 
     if (n == 0)
         return 0;
     {
-        int dev = 0, nsm = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        int nsm = 1;
+        if (device_sm_count(&nsm) != 0)
+            return TILEQR_ERR_CUDA;
         size_t warps = (size_t)L.p * L.p * nb;
         int ctas = (int)((warps + 7) / 8);
         if (ctas > nsm * 16)
@@ -280,7 +273,7 @@ extern "C" int tileqr_cholesky(int64_t n, const double *A, int64_t lda, int nb, 
         if (cudaGetLastError() != cudaSuccess)
             return TILEQR_ERR_CUDA;
     }
-    unsigned long long wd = 10000ull * 1000000ull;
+    const unsigned long long wd = watchdog_ns_default();
     unsigned long long *trace = nullptr;
     unsigned int tcap = 0;
     trace_target(&trace, &tcap);
@@ -302,9 +295,9 @@ extern "C" int tileqr_cholesky_get_L(const tileqr_desc *d, double *L, int64_t ld
         return -3;
     if (d->n == 0)
         return 0;
-    int dev = 0, nsm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int nsm = 1;
+    if (device_sm_count(&nsm) != 0)
+        return TILEQR_ERR_CUDA;
     size_t warps = (size_t)d->p * d->n;
     int ctas = (int)((warps + 7) / 8);
     if (ctas > nsm * 16)

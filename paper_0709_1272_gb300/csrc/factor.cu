@@ -56,24 +56,16 @@ static int launch_factor_t(const WsLayout &L, char *ws, int schedule, int flags,
                            unsigned int trace_cap)
 {
     constexpr size_t smem = F64Cfg<NB, S>::SMEM;
-    static bool attr_done = false;
-    static int grid_dag = 0;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_factor_dag<NB, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_bulk_geqrt<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_bulk_larfb<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_bulk_tsqrt<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_bulk_ssrfb<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0, nsm = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_dag<NB, S, false>, NT, smem);
-        if (per_sm < 1)
-            return TILEQR_ERR_CUDA;
-        grid_dag = nsm * per_sm;
-        if (cudaGetLastError() != cudaSuccess)
-            return TILEQR_ERR_CUDA;
-        attr_done = true;
+    int grid_dag = 0;
+    int rc = kernel_grid((const void *)k_factor_dag<NB, S, false>, NT, smem, &grid_dag);
+    if (rc)
+        return rc;
+    if (schedule != TILEQR_SCHED_DAG) {
+        const void *bulk[4] = {(const void *)k_bulk_geqrt<NB, S>, (const void *)k_bulk_larfb<NB, S>,
+                               (const void *)k_bulk_tsqrt<NB, S>, (const void *)k_bulk_ssrfb<NB, S>};
+        for (const void *fn : bulk)
+            if ((rc = kernel_smem_optin(fn, smem)) != 0)
+                return rc;
     }
     FactorArgs F;
     F.tiles = (double *)(ws + L.off_tiles);
@@ -155,17 +147,10 @@ static int launch_factor_dag_at_t(const WsLayout &L, double *tiles, double *T, c
                                   cudaStream_t st, unsigned long long watchdog_ns)
 {
     constexpr size_t smem = F64Cfg<NB, S>::SMEM;
-    static int grid_dag = 0;
-    if (grid_dag == 0) {
-        cudaFuncSetAttribute(k_factor_dag<NB, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0, nsm = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_dag<NB, S, false>, NT, smem);
-        if (per_sm < 1 || cudaGetLastError() != cudaSuccess)
-            return TILEQR_ERR_CUDA;
-        grid_dag = nsm * per_sm;
-    }
+    int grid_dag = 0;
+    const int rc = kernel_grid((const void *)k_factor_dag<NB, S, false>, NT, smem, &grid_dag);
+    if (rc)
+        return rc;
     FactorArgs F;
     F.tiles = tiles;
     F.T = T;

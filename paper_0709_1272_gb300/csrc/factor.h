@@ -6,6 +6,15 @@
 
 namespace tqr {
 
+// Per-device launch set-up (launch_cfg.cu), made once per (device, kernel)
+// under a mutex, on the current device.  kernel_grid opts `func` into `smem`
+// bytes of dynamic shared memory and returns SMs x resident CTAs in *grid;
+// kernel_smem_optin only opts in; device_sm_count returns the SM count.
+// Each returns 0 or TILEQR_ERR_CUDA.
+int kernel_grid(const void *func, int threads, size_t smem, int *grid);
+int kernel_smem_optin(const void *func, size_t smem);
+int device_sm_count(int *nsm);
+
 bool factor_supported(int nb, int ib);
 // The scheduler watchdog limit (TILEQR_WATCHDOG_MS, default 10 s), in ns.
 unsigned long long watchdog_ns_default();

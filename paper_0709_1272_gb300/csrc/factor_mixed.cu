@@ -13,18 +13,13 @@ static int launch_factor_mixed_t(const WsLayout &L, char *ws, int flags, cudaStr
 {
     constexpr int NB = 128;
     constexpr size_t smem = DagCfg<NB, S, true>::SMEM;
-    static int grid_dag = 0;
-    if (grid_dag == 0) {
-        cudaFuncSetAttribute(k_factor_dag<NB, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0, nsm = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_dag<NB, S, true>, NT, smem);
-        if (per_sm < 1 || cudaGetLastError() != cudaSuccess)
-            return TILEQR_ERR_CUDA;
-        // one CTA per SM: each holds 256 of the SM's 512 tensor-memory columns
-        grid_dag = nsm;
-    }
+    int grid_dag = 0;
+    int rc = kernel_grid((const void *)k_factor_dag<NB, S, true>, NT, smem, &grid_dag);
+    if (rc)
+        return rc;
+    // one CTA per SM: each holds 256 of the SM's 512 tensor-memory columns
+    if ((rc = device_sm_count(&grid_dag)) != 0)
+        return rc;
     FactorArgs F;
     F.tiles = (double *)(ws + L.off_tiles);
     F.T = (double *)(ws + L.off_T);

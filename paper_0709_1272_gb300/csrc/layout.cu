@@ -9,14 +9,9 @@ namespace tqr {
 
 static int grid_for(size_t warps_needed)
 {
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (nsm <= 0)
-            nsm = 1;
-    }
+    int nsm = 1;
+    if (device_sm_count(&nsm) != 0)
+        nsm = 1;   // a failed query only shrinks the grid; the launch reports the error
     const size_t per_cta = 8;  // 256 threads
     size_t ctas = (warps_needed + per_cta - 1) / per_cta;
     const size_t cap = (size_t)nsm * 16;

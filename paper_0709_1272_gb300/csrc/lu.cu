@@ -216,17 +216,10 @@ static int launch_lu_t(const LuLayout &L, char *ws, int flags, cudaStream_t st, 
                        unsigned long long *trace, unsigned int trace_cap)
 {
     constexpr size_t smem = LuCfg<NB, S>::SMEM;
-    static int grid = 0;
-    if (grid == 0) {
-        cudaFuncSetAttribute(k_lu_dag<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0, nsm = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_dag<NB, S>, NT, smem);
-        if (per_sm < 1 || cudaGetLastError() != cudaSuccess)
-            return TILEQR_ERR_CUDA;
-        grid = nsm * per_sm;
-    }
+    int grid = 0;
+    const int rc = kernel_grid((const void *)k_lu_dag<NB, S>, NT, smem, &grid);
+    if (rc)
+        return rc;
     LuArgs F;
     F.tiles = (double *)(ws + L.off_tiles);
     F.L = (double *)(ws + L.off_L);
@@ -328,17 +321,10 @@ static int launch_lu_apply_t(const LuLayout &L, const char *ws, double *Bt, int6
                              cudaStream_t st, unsigned long long watchdog_ns)
 {
     constexpr size_t smem = LuCfg<NB, S, APPLY_W>::SMEM;
-    static int grid_max = 0;
-    if (grid_max == 0) {
-        cudaFuncSetAttribute(k_lu_apply_dag<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0, nsm = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_apply_dag<NB, S>, NT, smem);
-        if (per_sm < 1 || cudaGetLastError() != cudaSuccess)
-            return TILEQR_ERR_CUDA;
-        grid_max = nsm * per_sm;
-    }
+    int grid_max = 0;
+    const int rc = kernel_grid((const void *)k_lu_apply_dag<NB, S>, NT, smem, &grid_max);
+    if (rc)
+        return rc;
     LuApplyArgs A;
     A.tiles = (const double *)(ws + L.off_tiles);
     A.L = (const double *)(ws + L.off_L);
@@ -458,9 +444,9 @@ extern "C" int tileqr_lu(int64_t n, const double *A, int64_t lda, int nb, int ib
     if (n == 0)
         return 0;
     {
-        int dev = 0, nsm = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        int nsm = 1;
+        if (device_sm_count(&nsm) != 0)
+            return TILEQR_ERR_CUDA;
         const size_t warps = (size_t)L.p * L.p * nb;
         int ctas = (int)((warps + 7) / 8);
         if (ctas > nsm * 16)
@@ -472,7 +458,7 @@ extern "C" int tileqr_lu(int64_t n, const double *A, int64_t lda, int nb, int ib
             return TILEQR_ERR_CUDA;
     }
     const unsigned long long wd = (flags & TILEQR_FLAG_TEST_WITHHOLD_LAST_TASK) ? 200ull * 1000000ull
-                                                                               : 10000ull * 1000000ull;
+                                                                               : watchdog_ns_default();
     unsigned long long *trace = nullptr;
     unsigned int tcap = 0;
     trace_target(&trace, &tcap);

@@ -120,5 +120,5 @@ extern "C" int tileqr_factor_noalloc(int64_t m, int64_t n, const double *A, int6
     rc = launch_cm2tile(A, lda, m, n, tiles, nb, L.p, L.q, (SchedCtrl *)sched, st);
     if (rc)
         return rc;
-    return launch_factor_dag_at(L, tiles, T, sched, st, 10000ull * 1000000ull);
+    return launch_factor_dag_at(L, tiles, T, sched, st, watchdog_ns_default());
 }

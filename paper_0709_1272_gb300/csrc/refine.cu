@@ -496,7 +496,7 @@ struct Refiner {
         Q.cap[1] = (unsigned int)nsb;
         Q.cap[2] = Q.cap[3] = 0;
         Q.total = (unsigned int)(nlb + nsb);
-        Q.watchdog_ns = 10000ull * 1000000ull;
+        Q.watchdog_ns = watchdog_ns_default();
         Q.withheld = ~0ull;
         Q.trace = nullptr;
         Q.trace_cap = 0;
@@ -591,15 +591,10 @@ extern "C" int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_
     R.dots = (double *)(R.ws + L.dots);
     cudaStream_t st = R.st;
     {
-        static int grid = 0;
-        if (grid == 0) {
-            int dev = 0, nsm = 0, per = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply32_dag<true>, 128, 0);
-            grid = nsm * (per > 0 ? per : 1);
-            cudaFuncSetAttribute(k_inv_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (128 * 129 + 128) * 8);
-        }
+        int grid = 0;
+        if (kernel_grid((const void *)k_apply32_dag<true>, 128, 0, &grid) != 0 ||
+            kernel_smem_optin((const void *)k_inv_diag, (128 * 129 + 128) * 8) != 0)
+            return TILEQR_ERR_CUDA;
         R.grid_apply = grid;
     }
     // FP32 factors and inverted diagonal tiles of R
