@@ -138,47 +138,139 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(nb, ib, n_sample=3072):
-    """The oracle as it stands, one thread, on a bounded sample of the workload."""
+CPU_SAMPLE_N = 4096
+
+
+def _oracle_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(nb, ib, n_sample=CPU_SAMPLE_N):
+    """The oracle as it stands on a bounded sample of the workload: Algorithm
+    2's tasks run level by level of the task graph, each level spread over
+    all host cores with OpenMP (oracle.tiled_qr_levels, identical bits to the
+    sequential oracle)."""
     import oracle
     from paper_0709_1272_gb300 import inputs
+    threads = _oracle_threads()
     A = inputs.normal_matrix(n_sample, n_sample, seed=20070709 + 2)
     t0 = time.perf_counter()
-    oracle.tiled_qr(A, nb, ib)
+    _, nlev = oracle.tiled_qr_levels(A, nb, ib, threads)
     dt = time.perf_counter() - t0
-    return {"value": lapack_opcount(n_sample, n_sample) / dt / 1e9, "unit": UNIT, "cores": 1,
+    return {"value": lapack_opcount(n_sample, n_sample) / dt / 1e9, "unit": UNIT, "cores": threads,
             "kind": "oracle",
-            "sample": f"oracle tiled QR (Algorithm 2, plain C, -O2, one thread) of one "
-                      f"{n_sample}x{n_sample} N(0,1) matrix, nb={nb}, ib={ib}: {dt:.1f} s"}
+            "sample": f"oracle tiled QR (Algorithm 2, plain C -O2, the {nlev} levels of its task graph in turn, "
+                      f"tasks of a level on {threads} OpenMP threads) of one {n_sample}x{n_sample} N(0,1) "
+                      f"matrix, nb={nb}, ib={ib}: {dt:.1f} s"}
 
 
 def run_reference(args, rank):
+    """The reference arm: the oracle (there is no other implementation of
+    this paper) on the host cores, one CPU_SAMPLE_N^2 sample per step --
+    the same sample and build as the cpu_baseline of our arm."""
     if rank != 0:
         return 0
     import oracle
     from paper_0709_1272_gb300 import inputs
     n = args.ref_n
+    threads = _oracle_threads()
     A = inputs.normal_matrix(n, n, seed=20070709 + 2)
     for _ in range(args.warmup):
-        oracle.tiled_qr(A, args.nb, args.ib)
+        oracle.tiled_qr_levels(A, args.nb, args.ib, threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.tiled_qr(A, args.nb, args.ib)
+        _, nlev = oracle.tiled_qr_levels(A, args.nb, args.ib, threads)
     dt = time.perf_counter() - t0
     value = args.steps * lapack_opcount(n, n) / dt / 1e9
-    sample = (f"oracle tiled QR (Algorithm 2, plain C, -O2, one thread) of a {n}x{n} N(0,1) "
-              f"matrix per step, nb={args.nb}, ib={args.ib} (bounded sample of the "
-              f"{args.n}x{args.n} workload)")
+    sample = (f"oracle tiled QR (Algorithm 2, plain C -O2, the {nlev} levels of its task graph in turn, tasks "
+              f"of a level on {threads} OpenMP threads) of a {n}x{n} N(0,1) matrix per step, nb={args.nb}, "
+              f"ib={args.ib} (bounded sample of the {args.n}x{args.n} workload)")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": f"plain FP64 tile QR, {n}x{n} N(0,1), nb={args.nb}, ib={args.ib} "
-                                  f"(sample of {args.n}x{args.n})", "parallelism": "none (host)"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                                  f"(sample of {args.n}x{args.n})", "parallelism": f"{threads} host threads"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
+
+
+def run_e2e(args, A_host, m, n, nb, ib, sched, ws, stream, dev, barrier, dist, world, ops):
+    """The headline metric end to end through the C ABI with host buffers:
+    per step, pinned host A -> device (cudaMemcpyAsync), tileqr_factor,
+    tileqr_get_R, R -> pinned host.  Copies run on their own streams and
+    overlap the previous / next step's factorization; the timed region spans
+    the first input copy to the last result copy.  Also reports the copy
+    rates measured alone."""
+    import numpy as np
+    import torch
+    from paper_0709_1272_gb300 import replicas, tileqr
+    k = min(m, n)
+    A_pin = torch.from_numpy(np.ascontiguousarray(A_host.T)).pin_memory()   # (n, m) row-major == A col-major
+    R_pin = [torch.empty((n, k), dtype=torch.float64).pin_memory() for _ in range(2)]
+    A_dev = [torch.empty((n, m), dtype=torch.float64, device=dev) for _ in range(2)]
+    R_dev = [torch.empty((n, k), dtype=torch.float64, device=dev) for _ in range(2)]
+    h2d, d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def copy_rate(dst, src, s):
+        e0, e1 = ev(), ev()
+        torch.cuda.synchronize()
+        e0.record(s)
+        with torch.cuda.stream(s):
+            dst.copy_(src, non_blocking=True)
+        e1.record(s)
+        torch.cuda.synchronize()
+        return src.numel() * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+    h2d_gbs = copy_rate(A_dev[0], A_pin, h2d)
+    d2h_gbs = copy_rate(R_pin[0], R_dev[0], d2h)
+    lib = tileqr.load()
+    in_ready = [ev() for _ in range(2)]
+    a_free = [ev() for _ in range(2)]
+    r_ready = [ev() for _ in range(2)]
+    r_free = [ev() for _ in range(2)]
+    e0, e1 = ev(), ev()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(h2d)
+    for st in range(args.e2e_steps):
+        b = st % 2
+        if st >= 2:
+            h2d.wait_event(a_free[b])        # step st-2 has read A_dev[b]
+        with torch.cuda.stream(h2d):
+            A_dev[b].copy_(A_pin, non_blocking=True)
+        in_ready[b].record(h2d)
+        stream.wait_event(in_ready[b])
+        if st >= 2:
+            stream.wait_event(r_free[b])     # R_dev[b] of step st-2 is on the host
+        g = tileqr.tileqr_factor(A_dev[b].t(), nb, ib, schedule=sched, workspace=ws)
+        a_free[b].record(stream)
+        rc = lib.tileqr_get_R(tileqr.ctypes.byref(g.desc), tileqr.ctypes.c_void_p(R_dev[b].data_ptr()),
+                              max(k, 1), tileqr.ctypes.c_void_p(stream.cuda_stream))
+        assert rc == 0
+        r_ready[b].record(stream)
+        d2h.wait_event(r_ready[b])
+        with torch.cuda.stream(d2h):
+            R_pin[b].copy_(R_dev[b], non_blocking=True)
+        r_free[b].record(d2h)
+    stream.wait_event(r_free[(args.e2e_steps - 1) % 2])
+    if args.e2e_steps >= 2:
+        stream.wait_event(r_free[(args.e2e_steps - 2) % 2])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    et = replicas.max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+    assert g.status() == 0
+    return {"value": world * args.e2e_steps * ops / et / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": k * n * 8, "steps": args.e2e_steps,
+            "h2d_gbs_alone": round(h2d_gbs, 1), "d2h_gbs_alone": round(d2h_gbs, 1),
+            "path": "pinned host A -> cudaMemcpyAsync (copy stream) -> tileqr_factor -> tileqr_get_R -> "
+                    "pinned host R (second copy stream); copies overlap the neighbouring steps' factorizations"}
 
 
 def run_batched(args, dev, rank, world, barrier, dist):
@@ -448,59 +540,97 @@ def run_config2_sweep(args, dev, rank, world, barrier, dist):
             "unit": UNIT, "runs": out}
 
 
-def run_kappa_sweep(args, dev, rank, world, barrier, dist):
-    """The mixed-precision solve of A x = b (TF32 updates + FP64 refinement)
-    for cond(A) in {1e2, 1e6, 1e10}, A = (I-2uu^T) diag(s) (I-2vv^T): time,
-    refinement steps and method, the solve's relative residual, and the
-    factorization's accuracy at full size from samples: the backward error
-    ||Q^T a_j - r_j|| / ||A|| over 64 sampled columns and the orthogonality
-    ||Q^T (Q X) - X|| / ||X|| for 8 random probe vectors (opt-in)."""
+def kappa_device_matrix(n, kappa, seed, dev):
+    """inputs.kappa_matrix formed on the device from the same (s, u, v):
+    A = (I-2uu^T) diag(s) (I-2vv^T) = D - 2 u (Du)^T - 2 (Dv) v^T + 4 c u v^T
+    with c = u^T D v, built as its transpose in row-major memory, which is A
+    in column-major order (the layout the library reads)."""
+    import torch
+    from paper_0709_1272_gb300 import inputs
+    s, u, v = inputs.kappa_factors(n, kappa, seed)
+    c = float(u @ (s * v))
+    st, ut, vt = (torch.from_numpy(x).to(dev) for x in (s, u, v))
+    At = torch.diag(st)
+    At.addr_(st * ut, ut, alpha=-2.0)
+    At.addr_(vt, st * vt, alpha=-2.0)
+    At.addr_(vt, ut, alpha=4.0 * c)
+    return At.t()
+
+
+def run_kappa_sweep(args, dev, rank, world, barrier, dist, fp64_factor_ms=None):
+    """The mixed-precision solve of A x = b (TF32 tensor-core updates + FP64
+    refinement) for cond(A) in {1e2, 1e6, 1e10}, A = (I-2uu^T) diag(s)
+    (I-2vv^T) at --n, against the plain FP64 factorization + solve of the
+    same system.  Per kappa: factorization and refinement time, steps,
+    method, the solve's relative residual and forward error, the
+    factorization's backward error ||Q^T a_j - r_j|| / ||A|| over 64 sampled
+    columns, and R's first two tile columns against the CPU oracle (FP64
+    Algorithm 2 of A's first 256 columns)."""
     import numpy as np
     import torch
+    import oracle
     from paper_0709_1272_gb300 import inputs, replicas, tileqr
-    m = n = args.n
+    n = args.n
     nb, ib = 128, 16
-    out = {}
     g = torch.Generator(device=dev).manual_seed(20070709 + 5)
     cols = torch.randperm(n, generator=g, device=dev)[:64].sort().values
-    for kappa in (1e2, 1e6, 1e10):
-        Ak, _, _, _ = inputs.kappa_matrix(n, kappa, seed=20070709 + 4 + 1000 * rank)
-        xt = inputs.normal_matrix(n, 1, seed=20070709 + 6)[:, 0]
-        bk = torch.from_numpy(Ak @ xt).to(dev)
-        Akd = tileqr.to_device_colmajor(Ak, dev)
-        del Ak
-        wsm = torch.empty(tileqr.tileqr_workspace_size(m, n, nb, ib, tileqr.TILEQR_TF32), dtype=torch.uint8,
-                          device=dev)
-        tileqr.tileqr_factor(Akd, nb, ib, precision=tileqr.TILEQR_TF32, workspace=wsm).check()
+    xt = torch.from_numpy(inputs.normal_matrix(n, 1, seed=20070709 + 6)).to(dev).reshape(-1)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        fm = tileqr.tileqr_factor(Akd, nb, ib, precision=tileqr.TILEQR_TF32, workspace=wsm)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
         torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        xk, info = fm.solve_refine(Akd, bk, max_iter=40, tol=1e-12)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
+        return replicas.max_over_ranks(e0.elapsed_time(e1), dist, dev), out
+
+    wsm = torch.empty(tileqr.tileqr_workspace_size(n, n, nb, ib, tileqr.TILEQR_TF32), dtype=torch.uint8,
+                      device=dev)
+    per, fp64 = [], {}
+    for kappa in (1e2, 1e6, 1e10):
+        seed = 20070709 + 4 + 1000 * rank
+        A = kappa_device_matrix(n, kappa, seed, dev)
+        b = A @ xt
+        if not per:
+            tileqr.tileqr_factor(A, nb, ib, precision=tileqr.TILEQR_TF32, workspace=wsm).check()   # warm-up
+        t_f, fm = timed(lambda: tileqr.tileqr_factor(A, nb, ib, precision=tileqr.TILEQR_TF32, workspace=wsm))
         fm.check()
-        nA = torch.linalg.matrix_norm(Akd).item()
-        QtA = fm.apply_qt(Akd[:, cols].contiguous().t().contiguous().t())
+        t_r, (x, info) = timed(lambda: fm.solve_refine(A, b, max_iter=40, tol=1e-12))
+        d = info.as_dict()
+        nA = torch.linalg.matrix_norm(A).item()
+        QtA = fm.apply_qt(A[:, cols].contiguous().t().contiguous().t())
         R = fm.R()
         back = torch.linalg.matrix_norm(QtA - R[:, cols]).item() / nA * np.sqrt(n / 64.0)
-        X = torch.randn((n, 8), generator=g, dtype=torch.float64, device=dev)
-        orth = (torch.linalg.matrix_norm(fm.apply_qt(fm.apply_q(X)) - X) / torch.linalg.matrix_norm(X)).item()
-        d = info.as_dict()
-        out[f"{kappa:.0e}"] = {"factor_ms": replicas.max_over_ranks(t1 - t0, dist, dev) * 1e3,
-                               "refine_ms": replicas.max_over_ranks(t2 - t1, dist, dev) * 1e3,
-                               "refine_iterations": d["iterations"],
-                               "refine_method": {1: "classical", 2: "flexible GMRES"}.get(d["method"], "none"),
-                               "rel_residual": d["rel_residual"], "initial_rel_residual": d["initial_rel_residual"],
-                               "backward_error_sampled": back, "orthogonality_probe": orth}
-        del wsm, Akd, bk, fm, QtA, R
+        fwd = (torch.linalg.vector_norm(x - xt) / torch.linalg.vector_norm(xt)).item()
+        r_gpu = R[:256, :256].cpu().numpy()
+        ref = oracle.tiled_qr(inputs.kappa_columns(n, kappa, seed, 0, 256), nb, ib)
+        r_err = float(np.linalg.norm(oracle.sign_normalize(r_gpu) - oracle.sign_normalize(ref.R())) /
+                      np.linalg.norm(ref.R()))
+        per.append({"kappa": f"{kappa:.0e}", "factor_ms": round(t_f, 2), "refine_ms": round(t_r, 2),
+                    "steps": d["iterations"], "method": {1: "classical", 2: "fgmres"}.get(d["method"], "none"),
+                    "rel_res": d["rel_residual"], "fwd_err": fwd, "back_err": back, "r256_vs_oracle": r_err})
+        if kappa == 1e10:
+            # the plain FP64 path on the hardest system: factorization + solve
+            del fm, wsm, QtA
+            torch.cuda.empty_cache()
+            ws64 = torch.empty(tileqr.tileqr_workspace_size(n, n, nb, ib), dtype=torch.uint8, device=dev)
+            t64, f64 = timed(lambda: tileqr.tileqr_factor(A, nb, ib, workspace=ws64))
+            f64.check()
+            ts, X = timed(lambda: f64.solve_ls(b.reshape(-1, 1).clone()))
+            rr = (torch.linalg.vector_norm(b - A @ X[:n, 0]) / torch.linalg.vector_norm(b)).item()
+            fp64 = {"factor_ms": round(t64, 1), "solve_ms": round(ts, 2), "rel_res": rr}
+            del f64, ws64, X
+        del A, b, x, R
         torch.cuda.empty_cache()
-    return {"workload": f"TF32-update tile QR + FP64 refinement, {n}x{n}, A = (I-2uu^T) diag(s) (I-2vv^T)",
-            "per_kappa": out,
-            "estimates": "backward error scaled from 64 sampled columns by sqrt(n/64); orthogonality from "
-                         "8 random probes"}
+    t64_total = fp64["factor_ms"] + fp64["solve_ms"]
+    for e in per:
+        e["speedup_vs_fp64"] = round(t64_total / (e["factor_ms"] + e["refine_ms"]), 2)
+    return {"workload": f"A x = b, {n}x{n}, A = (I-2uu^T)diag(s)(I-2vv^T), s geometric 1..1/kappa; "
+                        f"TF32 updates + FP64 refinement to 1e-12 vs FP64 factor + solve",
+            "fp64_kappa1e10": fp64, "per_kappa": per}
 
 
 def main():
@@ -514,12 +644,11 @@ def main():
     ap.add_argument("--nb", type=int, default=128)
     ap.add_argument("--ib", type=int, default=16)
     ap.add_argument("--schedule", default="dag", choices=["dag", "bulk"])
-    ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--ref-n", type=int, default=2048)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-n", type=int, default=CPU_SAMPLE_N)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision + FP64 refinement measurement")
-    ap.add_argument("--kappa", type=float, default=1e6)
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched (4096 ragged matrices) measurement")
     ap.add_argument("--batch-count", type=int, default=4096)
@@ -622,84 +751,21 @@ def main():
     ops = lapack_opcount(m, n)
     value = world * args.steps * ops / elapsed / 1e9
 
-    # ---- end to end through the public API: pinned host A in, R out
+    # ---- end to end through the public API: pinned host A in, R out.  Two
+    # device buffers each for A and R and two copy streams, so the copy of
+    # step k+1's input and of step k-1's R run while step k factors.
     e2e = None
     if args.e2e_steps > 0:
-        A_pin = torch.from_numpy(np.ascontiguousarray(A_host.T)).pin_memory()   # (n, m) row-major == A col-major
-        k = min(m, n)
-        R_pin = torch.empty((n, k), dtype=torch.float64).pin_memory()
-        A_dev = torch.empty((n, m), dtype=torch.float64, device=dev)
-        R_dev = torch.empty((n, k), dtype=torch.float64, device=dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.e2e_steps):
-            A_dev.copy_(A_pin, non_blocking=True)
-            g = tileqr.tileqr_factor(A_dev.t(), nb, ib, schedule=sched, workspace=ws)
-            rc = tileqr.load().tileqr_get_R(tileqr.ctypes.byref(g.desc),
-                                            tileqr.ctypes.c_void_p(R_dev.data_ptr()), max(k, 1),
-                                            tileqr.ctypes.c_void_p(stream.cuda_stream))
-            assert rc == 0
-            R_pin.copy_(R_dev, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        et = e0.elapsed_time(e1) / 1e3
-        et = replicas.max_over_ranks(et, dist, dev)
-        assert g.status() == 0
-        e2e = {"value": world * args.e2e_steps * ops / et / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": k * n * 8,
-               "steps": args.e2e_steps,
-               "path": "pinned host A -> cudaMemcpyAsync -> tileqr_factor -> tileqr_get_R -> pinned host R"}
+        e2e = run_e2e(args, A_host, m, n, nb, ib, sched, ws, stream, dev, barrier, dist, world, ops)
 
     # ---- mixed precision (tcgen05 updates) + FP64 iterative refinement of the
-    # solve A x = b, A = (I-2uu^T) diag(s) (I-2vv^T), cond(A) = kappa, same size
+    # solve A x = b for cond(A) 1e2 / 1e6 / 1e10 at the same order, against
+    # the plain FP64 factorization + solve of the same system
     mixed = None
     if not args.no_mixed and m == n and nb == 128:
         del ws
         torch.cuda.empty_cache()
-        Ak, _, _, _ = inputs.kappa_matrix(n, args.kappa, seed=20070709 + 4 + 1000 * rank)
-        xt = inputs.normal_matrix(n, 1, seed=20070709 + 5).reshape(-1)
-        bk = torch.from_numpy(Ak @ xt).to(dev)
-        Akd = tileqr.to_device_colmajor(Ak, dev)
-        del Ak
-        wsm = torch.empty(tileqr.tileqr_workspace_size(m, n, nb, ib, tileqr.TILEQR_TF32), dtype=torch.uint8,
-                          device=dev)
-        steps_m = max(2, min(args.steps, 3))
-        fac_t, ref_t, infos = [], [], []
-        for it in range(1 + steps_m):
-            barrier()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            fm = tileqr.tileqr_factor(Akd, nb, ib, precision=tileqr.TILEQR_TF32, workspace=wsm)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            xk, info = fm.solve_refine(Akd, bk, max_iter=40, tol=1e-12)
-            torch.cuda.synchronize()
-            t2 = time.perf_counter()
-            if it > 0:
-                fac_t.append(t1 - t0)
-                ref_t.append(t2 - t1)
-                infos.append(info.as_dict())
-        assert fm.status() == 0
-        tm = statistics.mean([a + b for a, b in zip(fac_t, ref_t)])
-        tm = replicas.max_over_ranks(tm, dist, dev)
-        mixed = {"workload": f"TF32-update tile QR + FP64 refinement of A x = b, {m}x{n}, "
-                             f"A = (I-2uu^T) diag(s) (I-2vv^T), cond {args.kappa:.0e}, nb={nb}, ib={ib}",
-                 "value": world * ops / tm / 1e9, "unit": UNIT, "ms_per_step": tm * 1e3,
-                 "factor_ms": statistics.mean(fac_t) * 1e3, "refine_ms": statistics.mean(ref_t) * 1e3,
-                 "steps": steps_m, "rel_residual": max(i["rel_residual"] for i in infos),
-                 "refine_iterations": infos[-1]["iterations"], "refine_method":
-                     {1: "classical", 2: "flexible GMRES"}.get(infos[-1]["method"], "none"),
-                 "initial_rel_residual": infos[-1]["initial_rel_residual"],
-                 "speedup_vs_fp64_factorization": (world * ops / tm / 1e9) / value,
-                 "timing": "wall clock around factor+refine (the refinement synchronises), max over ranks"}
-        tpk, tsrc = tf32_peak_gflops()
-        # the factorization's LAPACK-count rate against the dense TF32 peak
-        # (each product is three TF32 MMAs, so 1/3 of it is the ceiling)
-        mixed["factor_pct_of_tf32_dense_peak"] = 100.0 * (ops / (mixed["factor_ms"] / 1e3) / 1e9) / tpk
-        mixed["tf32_peak_source"] = tsrc
-        del wsm, Akd, bk, fm
+        mixed = run_kappa_sweep(args, dev, rank, world, barrier, dist)
 
     # ---- batched: 4096 independent matrices, m ~ U[64, 2048], n ~ U[32, m],
     # entries U[-1, 1), one persistent launch replayed from a CUDA graph
@@ -760,18 +826,20 @@ def main():
     }
     if e2e:
         out["e2e"] = e2e
-    if mixed:
-        out["mixed_ls"] = mixed
-    if batched:
-        out["batched"] = batched
-    if tall:
-        out["tall_skinny"] = tall
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(nb, ib)
+    # the secondary workloads, the mixed-precision sweep last: a reader that
+    # keeps only the end of the line still sees it
     if chol:
         out["cholesky"] = chol
     if lu:
         out["lu"] = lu
-    if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(nb, ib)
+    if tall:
+        out["tall_skinny"] = tall
+    if batched:
+        out["batched"] = batched
+    if mixed:
+        out["mixed_ls"] = mixed
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -51,9 +51,14 @@ typedef struct CUstream_st *tileqr_stream_t; /* identical to cudaStream_t */
 enum {
     TILEQR_FP64 = 0,       /* every task in FP64 */
     TILEQR_TF32 = 1,       /* updates as 3xTF32 tensor-core products (tcgen05),
-                              FP32 accumulation; nb 128, ib 16 or 32, task graph only */
-    TILEQR_SPLIT_BF16 = 2  /* updates as split-BF16 products (declared, not built:
-                              TILEQR_ERR_UNSUPPORTED) */
+                              FP32 accumulation; nb 128, ib 16 or 32, task graph only.
+                              The FP32 operands are scaled per matrix column by a
+                              power of two taken from the column's largest entry,
+                              so any magnitude of A is handled (column norms in
+                              [2^-1000, 2^1000]); each update's output column is
+                              within ~2^-21 of its norm (tileqr_mixed_update_tile) */
+    TILEQR_SPLIT_BF16 = 2  /* split-BF16 updates: NOT BUILT in this library; every
+                              call that asks for it returns TILEQR_ERR_UNSUPPORTED */
 };
 
 /* How the task graph is executed. */
@@ -205,6 +210,30 @@ int tileqr_factor_noalloc(int64_t m, int64_t n, const double *A, int64_t lda, in
                           double *tiles, size_t tiles_bytes, double *T, size_t T_bytes,
                           tileqr_stream_t stream, tileqr_desc *out);
 
+/* One update task of the TILEQR_TF32 factorization on caller tiles, for
+ * checking the accuracy of a single DLARFB or DSSRFB (Sec. 3.2.1) against
+ * FP64 tile kernels.  It runs the code the factorization runs for that task:
+ * the panel's full T built from V and its T strip, then three 3xTF32 tcgen05
+ * products with FP32 accumulation, tiles FP64, columns scaled by powers of
+ * two from the largest exponent of each column of [B; C].
+ *   kind  TILEQR_UPDATE_LARFB: C <- (I - V T V^T)^T C, V the unit lower part
+ *         of a DGEQRT tile (the entries on and above its diagonal, R, are
+ *         not read);
+ *         TILEQR_UPDATE_SSRFB: [B; C] <- (I - V T V^T)^T [B; C] with the
+ *         reflectors [I; V], V a full DTSQRT reflector tile
+ *   ib    16 or 32 (nb is 128)
+ *   V, T  device: the 128 x 128 reflector tile (column-major) and its
+ *         ib x 128 T strip (column-major, ld ib), as in tileqr_desc
+ *   B, C  device 128 x 128 column-major tiles, updated in place (B is not
+ *         read for TILEQR_UPDATE_LARFB and may be NULL)
+ *   workspace  device, 256-byte aligned, >= TILEQR_MIXED_UPDATE_WS_BYTES
+ * Synchronous.  Returns 0, -i, TILEQR_ERR_UNSUPPORTED, TILEQR_ERR_WORKSPACE,
+ * TILEQR_ERR_TIMEOUT (a tensor-core wait gave up) or TILEQR_ERR_CUDA. */
+enum { TILEQR_UPDATE_LARFB = 0, TILEQR_UPDATE_SSRFB = 1 };
+#define TILEQR_MIXED_UPDATE_WS_BYTES (132u * 1024u)
+int tileqr_mixed_update_tile(int kind, int ib, const double *V, const double *T, double *B, double *C,
+                             void *workspace, size_t ws_bytes, tileqr_stream_t stream);
+
 /* Synchronises `stream` and returns the device-side status of the last
  * factorization run on `d`: 0, TILEQR_ERR_TIMEOUT or TILEQR_ERR_NONFINITE
  * (or TILEQR_ERR_CUDA if the stream reports an error). */
@@ -324,7 +353,9 @@ int tileqr_refine_workspace_size(const tileqr_desc *d, size_t *bytes);
  *   b        device, m entries;   x  device, n entries (output)
  *   max_iter refinement steps (outer iterations) at most
  * Works on flat and tree-form factorizations (the correction solve replays
- * the factorization's apply graph), nb 128.
+ * the factorization's apply graph), nb 128.  The FP32 correction solve works
+ * on power-of-two scaled quantities (b, each corrected residual, and R's
+ * columns), so any magnitude of A and b is handled.
  * Synchronous.  Returns 0 (also when not converged: see info), -i,
  * TILEQR_ERR_SINGULAR, TILEQR_ERR_WORKSPACE, TILEQR_ERR_UNSUPPORTED (nb other
  * than 128), TILEQR_ERR_CUDA. */

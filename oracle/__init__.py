@@ -30,20 +30,32 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 TASK_GEQRT, TASK_TSQRT, TASK_LARFB, TASK_SSRFB = 0, 1, 2, 3
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no FMA contraction, no -march)."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(x) for x in _SRCS)):
-        return _LIB
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp] + _SRCS + ["-lm"]
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def _compile(lib: str, extra, force: bool) -> str:
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= max(os.path.getmtime(x) for x in _SRCS)):
+        return lib
+    tmp = lib + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC"] + extra + \
+        ["-shared", "-o", tmp] + _SRCS + ["-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no FMA contraction, no -march):
+    the single-threaded library the tests use, and the same sources built
+    with OpenMP (liboracle_omp.so), whose only parallel code is the level-by-
+    level driver of tiled_qr_levels (the CPU baseline)."""
+    _compile(_LIB_OMP, ["-fopenmp"], force)
+    return _compile(_LIB, [], force)
 
 
 _lib = None
+_lib_omp = None
 
 
 def _load():
@@ -146,6 +158,32 @@ def tiled_qr(A, nb: int, ib: int) -> Factored:
     if rc:
         raise ValueError(f"oracle_tiled_qr: illegal argument {rc}")
     return Factored(A, T, m, n, nb, ib)
+
+
+def tiled_qr_levels(A, nb: int, ib: int, threads: int = 1):
+    """Algorithm 2 run level by level of its task graph, the tasks of a level
+    spread over `threads` OpenMP threads (the same tile kernels; identical
+    bits to tiled_qr).  Returns (Factored, number of levels)."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        lib = ctypes.CDLL(_LIB_OMP)
+        lib.oracle_tiled_qr_levels.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int)]
+        lib.oracle_tiled_qr_levels.restype = ctypes.c_int
+        _lib_omp = lib
+    A = _fortran(A)
+    m, n = A.shape
+    p = -(-m // nb) if m else 0
+    T = np.zeros((max(p * ib, 1), max(n, 1)), dtype=np.float64, order="F")
+    nlev = ctypes.c_int(0)
+    rc = _lib_omp.oracle_tiled_qr_levels(m, n, _dp(A), max(m, 1), nb, ib, _dp(T), T.shape[0], int(threads),
+                                         ctypes.byref(nlev))
+    if rc:
+        raise ValueError(f"oracle_tiled_qr_levels: error {rc}")
+    return Factored(A, T, m, n, nb, ib), nlev.value
 
 
 def tiled_qr_ordered(A, nb: int, ib: int, tasks) -> Factored:

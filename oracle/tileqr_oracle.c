@@ -44,7 +44,12 @@
 
 /* Flop tally: incremented by every loop nest with the exact number of
  * floating-point operations it performs (multiply-add = 2). */
-static double g_flops = 0.0;
+#ifdef _OPENMP
+#define ORACLE_TLS __thread   /* the level-parallel build: one tally per thread */
+#else
+#define ORACLE_TLS
+#endif
+static ORACLE_TLS double g_flops = 0.0;
 
 /* Deliberate-mistake switch used only by the test that checks the pins catch
  * plausible errors.  0 = correct arithmetic.  1 = apply T instead of T^T in
@@ -657,6 +662,134 @@ int oracle_tiled_qr_ordered(int64_t m, int64_t n, double *A, int64_t lda, int nb
         run_task(&g, A, lda, T, ldt, NULL, tk[0], tk[1], tk[2], tk[3], work);
     }
     free(work);
+    return 0;
+}
+
+/* Algorithm 2 executed level by level: a task's level is one more than the
+ * highest level of the tasks it must follow, found from the tile parts each
+ * task reads and writes (Sec. 3.2.1; the R part, on and above the diagonal,
+ * and the V part, below it, of a diagonal tile counted apart) -- after the
+ * last writer of every part it touches, and after the readers of every part
+ * it writes.  Tasks of one level touch disjoint data, so they may run in any
+ * order or at the same time; built with OpenMP (the baseline build), each
+ * level is spread over `nthreads` threads.  Any topological order gives the
+ * same bits (Sec. 4), so the result equals oracle_tiled_qr's exactly.
+ * *nlevels (if not NULL) receives the number of levels.  Returns 0, a
+ * negative argument index, or -99 if memory for the schedule is lacking. */
+int oracle_tiled_qr_levels(int64_t m, int64_t n, double *A, int64_t lda, int nb, int ib, double *T,
+                           int64_t ldt, int nthreads, int *nlevels)
+{
+    int rc = check_args(m, n, lda, nb, ib, ldt);
+    if (rc)
+        return rc;
+    geom g = make_geom(m, n, nb, ib);
+    if (ldt < (int64_t)g.p * ib)
+        return -8;
+    for (int64_t c = 0; c < n; c++)
+        for (int64_t r = 0; r < ldt; r++)
+            T[c * ldt + r] = 0.0;
+    int kmax = g.p < g.q ? g.p : g.q;
+    int64_t ntask = 0;
+    for (int k = 0; k < kmax; k++)
+        ntask += (int64_t)(g.p - k) * (g.q - k);
+    /* per tile part: level of its last writer and highest level of a reader since */
+    size_t nparts = (size_t)g.p * g.q * 2;
+    int *wlev = calloc(nparts ? nparts : 1, sizeof(int));
+    int *rlev = calloc(nparts ? nparts : 1, sizeof(int));
+    int32_t *task = malloc(sizeof(int32_t) * 4 * (size_t)(ntask ? ntask : 1));
+    int *lev = malloc(sizeof(int) * (size_t)(ntask ? ntask : 1));
+    if (!wlev || !rlev || !task || !lev) {
+        free(wlev);
+        free(rlev);
+        free(task);
+        free(lev);
+        return -99;
+    }
+#define PART(i, j, v) (((size_t)(j) * g.p + (size_t)(i)) * 2 + (size_t)(v))
+    int64_t t = 0;
+    int top = 0;
+    for (int k = 0; k < kmax; k++) {
+        for (int i = k; i < g.p; i++) {
+            for (int j = k; j < g.q; j++) {
+                int kind = (i == k) ? (j == k ? TASK_GEQRT : TASK_LARFB) : (j == k ? TASK_TSQRT : TASK_SSRFB);
+                /* reads (rd) and writes (wr) of the task, as tile parts */
+                size_t rd[2], wr[3];
+                int nrd = 0, nwr = 0;
+                switch (kind) {
+                case TASK_GEQRT: wr[nwr++] = PART(k, k, 0); wr[nwr++] = PART(k, k, 1); break;
+                case TASK_LARFB: rd[nrd++] = PART(k, k, 1); wr[nwr++] = PART(k, j, 0); break;
+                case TASK_TSQRT: wr[nwr++] = PART(k, k, 0); wr[nwr++] = PART(i, k, 0); break;
+                default: rd[nrd++] = PART(i, k, 0); wr[nwr++] = PART(k, j, 0); wr[nwr++] = PART(i, j, 0); break;
+                }
+                int l = 0;
+                for (int a = 0; a < nrd; a++)
+                    l = wlev[rd[a]] > l ? wlev[rd[a]] : l;
+                for (int a = 0; a < nwr; a++) {
+                    l = wlev[wr[a]] > l ? wlev[wr[a]] : l;
+                    l = rlev[wr[a]] > l ? rlev[wr[a]] : l;
+                }
+                l += 1;
+                for (int a = 0; a < nrd; a++)
+                    rlev[rd[a]] = l > rlev[rd[a]] ? l : rlev[rd[a]];
+                for (int a = 0; a < nwr; a++) {
+                    wlev[wr[a]] = l;
+                    rlev[wr[a]] = 0;
+                }
+                task[4 * t + 0] = kind;
+                task[4 * t + 1] = i;
+                task[4 * t + 2] = j;
+                task[4 * t + 3] = k;
+                lev[t] = l;
+                top = l > top ? l : top;
+                t++;
+            }
+        }
+    }
+#undef PART
+    /* bucket the tasks by level (counting sort, stable) */
+    int64_t *start = calloc((size_t)top + 2, sizeof(int64_t));
+    int64_t *order = malloc(sizeof(int64_t) * (size_t)(ntask ? ntask : 1));
+    if (!start || !order) {
+        free(wlev);
+        free(rlev);
+        free(task);
+        free(lev);
+        free(start);
+        free(order);
+        return -99;
+    }
+    for (int64_t u = 0; u < ntask; u++)
+        start[lev[u] + 1]++;
+    for (int l = 1; l <= top + 1; l++)
+        start[l] += start[l - 1];
+    {
+        int64_t *fill = calloc((size_t)top + 2, sizeof(int64_t));
+        for (int64_t u = 0; u < ntask; u++)
+            order[start[lev[u]] + fill[lev[u]]++] = u;
+        free(fill);
+    }
+    if (nthreads < 1)
+        nthreads = 1;
+#pragma omp parallel num_threads(nthreads)
+    {
+        double *work = malloc(sizeof(double) * (size_t)ib * nb);
+        for (int l = 1; l <= top; l++) {
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t u = start[l]; u < start[l + 1]; u++) {
+                const int32_t *tk = &task[4 * order[u]];
+                run_task(&g, A, lda, T, ldt, NULL, tk[0], tk[1], tk[2], tk[3], work);
+            }
+        }
+        free(work);
+    }
+    if (nlevels)
+        *nlevels = top;
+    free(wlev);
+    free(rlev);
+    free(task);
+    free(lev);
+    free(start);
+    free(order);
     return 0;
 }
 

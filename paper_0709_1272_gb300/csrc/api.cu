@@ -70,6 +70,13 @@ WsLayout make_layout(int64_t m, int64_t n, int nb, int ib, int h, int precision)
         off += align256((size_t)(caps[t] ? caps[t] : 1) * sizeof(unsigned long long));
     }
     L.total = (unsigned int)tot;
+    // per-column exponents of the mixed-precision path, in the range that is
+    // cleared with the scheduler state before every factorization
+    L.off_cexp = 0;
+    if (tfb > 0) {
+        L.off_cexp = off;
+        off += align256((size_t)(n > 0 ? n : 1) * sizeof(int));
+    }
     L.end = off;
     return L;
 }
@@ -190,7 +197,8 @@ static int factor_impl(int64_t m, int64_t n, const double *A, int64_t lda, int n
         return TILEQR_ERR_CUDA;
     if (m == 0 || n == 0)
         return 0;
-    rc = launch_cm2tile(A, lda, m, n, out->tiles, nb, L.p, L.q, (SchedCtrl *)(ws + L.off_ctrl), st);
+    rc = launch_cm2tile(A, lda, m, n, out->tiles, nb, L.p, L.q, (SchedCtrl *)(ws + L.off_ctrl),
+                        L.off_cexp ? (int *)(ws + L.off_cexp) : nullptr, st);
     if (rc)
         return rc;
     unsigned long long wd = watchdog_ns_default();

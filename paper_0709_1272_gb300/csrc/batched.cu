@@ -35,13 +35,21 @@ __global__ void k_cm2tile_batched(const MatInfo *__restrict__ mats, int count, i
             }
             const double *src = mi.A + col * mi.lda + row0;
             double *dst = mi.tiles + (t * nb + c) * nb;
+            unsigned int emax = 0;
             for (int r = lane; r < nb; r += 32) {
                 double v = 0.0;
                 if (r < valid) {
                     v = __ldg(src + r);
                     bad |= !isfinite(v);
+                    emax = max(emax, (unsigned int)(__double2hiint(v) >> 20) & 0x7FFu);
                 }
                 dst[r] = v;
+            }
+            // mixed precision: the column's largest exponent (column scaling)
+            if (mi.cexp != nullptr) {
+                emax = __reduce_max_sync(0xffffffffu, emax);
+                if (lane == 0 && emax > 0 && col < mi.n)
+                    atomicMax(mi.cexp + col, (int)emax);
             }
         }
     }
@@ -52,7 +60,7 @@ __global__ void k_cm2tile_batched(const MatInfo *__restrict__ mats, int count, i
 namespace {
 
 struct BatchLayout {
-    size_t off_ctrl, off_mats, off_cnt, off_q[K_NKIND], off_data, end;
+    size_t off_ctrl, off_mats, off_cnt, off_q[K_NKIND], off_cexp, off_data, end;
     unsigned long long cap[K_NKIND], total, counters;
     double flops;
 };
@@ -62,7 +70,7 @@ BatchLayout batch_layout(int count, const int64_t *m, const int64_t *n, int nb, 
 {
     BatchLayout B{};
     unsigned long long cnt = 0;
-    size_t data = 0;
+    size_t data = 0, ncols = 0;
     std::vector<MatInfo> infos(count);
     for (int b = 0; b < count; b++) {
         MatInfo &mi = infos[b];
@@ -88,6 +96,10 @@ BatchLayout batch_layout(int count, const int64_t *m, const int64_t *n, int nb, 
         if (precision == TILEQR_TF32 && mi.steps > 0) {
             mi.TF = (unsigned char *)(uintptr_t)data;
             data += align256(tf_pairs(mi.p, mi.steps) * TF_BYTES);
+            // column exponents: offset (in ints) into the cleared cexp region
+            mi.cexp = (int *)(uintptr_t)ncols;
+            ncols += (size_t)n[b];
+            mi.lm = ceil_log2_sqrt(m[b]);
         }
         const double mm = (double)m[b], nn = (double)n[b];
         if (m[b] >= n[b])
@@ -108,6 +120,10 @@ BatchLayout batch_layout(int count, const int64_t *m, const int64_t *n, int nb, 
         B.off_q[t] = off;
         off += align256((size_t)(B.cap[t] ? B.cap[t] : 1) * 8);
     }
+    // mixed precision: the column exponents of every matrix, cleared with
+    // the scheduler state before each factorization
+    B.off_cexp = off;
+    off += ncols ? align256(ncols * sizeof(int)) : 0;
     B.off_mats = off;
     // the per-matrix table, then the order of the first pushes (count ints)
     off += align256((size_t)(count ? count : 1) * sizeof(MatInfo) + (size_t)(count ? count : 1) * sizeof(int));
@@ -214,8 +230,10 @@ extern "C" int tileqr_batched_prepare(int count, const int64_t *m, const int64_t
         infos[b].lda = lda[b];
         infos[b].tiles = (double *)(ws + B.off_data + (uintptr_t)infos[b].tiles);
         infos[b].T = (double *)(ws + B.off_data + (uintptr_t)infos[b].T);
-        if (precision == TILEQR_TF32 && infos[b].steps > 0)
+        if (precision == TILEQR_TF32 && infos[b].steps > 0) {
             infos[b].TF = (unsigned char *)(ws + B.off_data + (uintptr_t)infos[b].TF);
+            infos[b].cexp = (int *)(ws + B.off_cexp) + (uintptr_t)infos[b].cexp;
+        }
     }
     std::memset(out, 0, sizeof(*out));
     out->count = count;

@@ -71,6 +71,7 @@ struct WsLayout {
     int64_t m, n;
     int nb, ib, p, q, steps, H;
     size_t off_tiles, off_T, off_T2, off_TF, off_TF2, off_ctrl, off_cnt, off_q[K_NKIND], end;
+    size_t off_cexp;   // TILEQR_TF32: per-column largest exponent (n ints, cleared with the scheduler state); else 0
     unsigned int cap[K_NKIND];
     unsigned int total;
 };
@@ -108,6 +109,66 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
+}
+
+// ---------------------------------------------------------------------------
+// Column scaling of the FP32 operands of the mixed-precision (TILEQR_TF32)
+// updates.  The layout conversion records, per matrix column c, the largest
+// biased FP64 exponent cexp[c] of its entries; with lm = ceil(log2 sqrt(m)),
+// s_c = cexp[c] - 1022 + lm gives 2^s_c >= sqrt(m) max|a_ic| >= ||a_c||_2.
+// An orthogonal transformation keeps every column's 2-norm, so at every stage
+// of the factorization the entries of column c, and the products the updates
+// form from them, stay below a small multiple of 2^s_c: scaled by 2^-s_c they
+// fit FP32 whatever the magnitude of A, and what FP32 flushes is below
+// 2^-115 ||a_c||.  s_c is clamped to [-1000, 1000] (columns whose norm lies
+// in [2^-1000, 2^1000] are handled).  The scaling is exact (a power of two).
+constexpr int MIX_SHIFT_MAX = 1000;
+
+__host__ __device__ inline int ceil_log2_sqrt(int64_t m)
+{
+    int l = 0;
+    while (l < 40 && ((int64_t)1 << (2 * l)) < m)
+        l++;
+    return l;
+}
+__device__ __forceinline__ int col_shift(int cexp, int lm)
+{
+    const int s = cexp - 1022 + lm;
+    return s < -MIX_SHIFT_MAX ? -MIX_SHIFT_MAX : (s > MIX_SHIFT_MAX ? MIX_SHIFT_MAX : s);
+}
+// x * 2^-s rounded to FP32 with integer operations (exponent rebias,
+// mantissa funnel shift, round half away from zero).  Zeros and results
+// below the FP32 normal range give a signed zero, results above it a signed
+// infinity (not reached with the column shifts above).
+__device__ __forceinline__ float f64_to_f32_sc(double x, int s)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    const uint32_t sgn = hi & 0x80000000u;
+    uint32_t f = __funnelshift_l(lo, hi - ((uint32_t)(896 + s) << 20), 3);
+    f = (f & 0x7FFFFFFFu) | sgn;
+    f += (lo >> 28) & 1u;
+    const int es = e - s;
+    f = (e == 0 || es < 897) ? sgn : f;
+    f = (es > 1150) ? (sgn | 0x7F800000u) : f;
+    return __uint_as_float(f);
+}
+// v * 2^s as FP64 (exact) with integer operations; FP32 zeros and denormals,
+// and results below the FP64 normal range, give a signed zero, results
+// above it a signed infinity (finite v).
+__device__ __forceinline__ double f32_to_f64_sc(float v, int s)
+{
+    const uint32_t f = __float_as_uint(v);
+    const uint32_t sgn = f & 0x80000000u;
+    const int e32 = (int)((f >> 23) & 0xFFu);
+    uint32_t hi = sgn | (((f & 0x7FFFFFFFu) >> 3) + ((uint32_t)(896 + s) << 20));
+    uint32_t lo = f << 29;
+    const int eo = e32 + 896 + s;
+    const bool zero = e32 == 0 || eo < 1;
+    hi = zero ? sgn : (eo > 2046 ? (sgn | 0x7FF00000u) : hi);
+    lo = (zero || eo > 2046) ? 0u : lo;
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
 }
 
 // Library-wide launch counter (host side), for the benchmark's launch count.

@@ -18,6 +18,11 @@ struct FactorArgs {
     // mixed precision: the panels' full T^T as pre-split tf32 operands
     // (TF_BYTES per tile pair; TF2 for DTTQRT); unused in FP64
     unsigned char *TF, *TF2;
+    // mixed precision: the largest biased exponent of every matrix column
+    // and ceil(log2 sqrt(m)), for the column scaling of the FP32 operands
+    // (common.cuh); unused in FP64
+    const int *cexp;
+    int lm;
     int p, q, steps;
     TGraph G;
 };
@@ -38,6 +43,13 @@ __device__ __forceinline__ double *strip2_ptr(const FactorArgs &F, int i, int k)
     return F.T2 + ((size_t)k * F.p + i) * (size_t)S * NB;
 }
 
+// The column exponents of tile column j (nullptr in FP64).
+template <int NB>
+__device__ __forceinline__ const int *cexp_ptr(const FactorArgs &F, int j)
+{
+    return F.cexp ? F.cexp + (size_t)j * NB : nullptr;
+}
+
 __device__ __forceinline__ unsigned char *tf_ptr(unsigned char *base, int p, int i, int k)
 {
     return base + tf_index(p, i, k) * (size_t)TF_BYTES;
@@ -55,7 +67,7 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
     unsigned char *smb = (unsigned char *)sm;
     switch (kind) {
     case K_GEQRT:
-        task_geqrt<NB, S, MIXED>(sm, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
+        task_geqrt<NB, S, MIXED>(sm, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), cexp_ptr<NB>(F, k), F.lm);
         if constexpr (MIXED)
             {
                 __syncthreads();
@@ -65,7 +77,8 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
         break;
     case K_TSQRT:
         task_tsqrt<NB, S, MIXED, false>(sm, tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), k),
-                                        tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
+                                        tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), cexp_ptr<NB>(F, k),
+                                        F.lm);
         if constexpr (MIXED)
             {
                 __syncthreads();
@@ -75,7 +88,7 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
         break;
     case K_TTQRT:
         task_tsqrt<NB, S, MIXED, true>(sm, tile_ptr<NB, S>(F, g_partner(G, k, i), k), tile_ptr<NB, S>(F, i, k),
-                                       strip2_ptr<NB, S>(F, i, k));
+                                       strip2_ptr<NB, S>(F, i, k), cexp_ptr<NB>(F, k), F.lm);
         if constexpr (MIXED)
             {
                 __syncthreads();
@@ -86,7 +99,8 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
     case K_LARFB:
         if constexpr (MIXED) {
             task_update_mixed_tf<S, VK_UNIT>(smb, nullptr, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                             tf_ptr(F.TF, F.p, i, k), tmem, mbar, mphase, err);
+                                             tf_ptr(F.TF, F.p, i, k), cexp_ptr<NB>(F, j), F.lm, tmem, mbar, mphase,
+                                             err);
         } else {
             task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
         }
@@ -95,7 +109,8 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
         double *top = tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), j);
         if constexpr (MIXED) {
             task_update_mixed_tf<S, VK_FULL>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                             tf_ptr(F.TF, F.p, i, k), tmem, mbar, mphase, err);
+                                             tf_ptr(F.TF, F.p, i, k), cexp_ptr<NB>(F, j), F.lm, tmem, mbar, mphase,
+                                             err);
         } else {
             task_ssrfb<NB, S>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
                               strip_ptr<NB, S>(F, i, k));
@@ -106,7 +121,8 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
         double *top = tile_ptr<NB, S>(F, g_partner(G, k, i), j);
         if constexpr (MIXED) {
             task_update_mixed_tf<S, VK_UPPER>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                              tf_ptr(F.TF2, F.p, i, k), tmem, mbar, mphase, err);
+                                              tf_ptr(F.TF2, F.p, i, k), cexp_ptr<NB>(F, j), F.lm, tmem, mbar,
+                                              mphase, err);
         } else
             task_ssrfb<NB, S, FactorW<NB>::value, true>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
                                                         strip2_ptr<NB, S>(F, i, k));
@@ -118,7 +134,7 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
 // Dynamic shared memory and CTAs per SM of the persistent kernel.
 template <int NB, int S, bool MIXED>
 struct DagCfg {
-    static constexpr size_t MIX = TF_BUILD_SMEM > TF_UPDATE_SMEM ? TF_BUILD_SMEM : TF_UPDATE_SMEM;
+    static constexpr size_t MIX = TF_BUILD_SMEM > TF_UPDATE_SMEM_TOTAL ? TF_BUILD_SMEM : TF_UPDATE_SMEM_TOTAL;
     static constexpr size_t SMEM = MIXED ? (F64Cfg<NB, S>::SMEM > MIX ? F64Cfg<NB, S>::SMEM : MIX)
                                          : F64Cfg<NB, S>::SMEM;
     static_assert(SMEM <= 232448, "shared memory budget");
@@ -208,9 +224,10 @@ struct MatInfo {
     double *tiles;
     double *T;
     unsigned char *TF;   // mixed precision: the panels' pre-split T^T operands (else nullptr)
+    int *cexp;           // mixed precision: largest biased exponent per column (else nullptr)
     const double *A;
     int64_t m, n, lda;
-    int p, q, steps, pad;
+    int p, q, steps, lm;  // lm = ceil(log2 sqrt(m)) (column scaling)
     size_t cnt_off;   // first task counter of this matrix
 };
 
@@ -320,6 +337,8 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
             s_F.T2 = nullptr;
             s_F.TF = mi.TF;
             s_F.TF2 = nullptr;
+            s_F.cexp = mi.cexp;
+            s_F.lm = mi.lm;
             s_F.p = mi.p;
             s_F.q = mi.q;
             s_F.steps = mi.steps;

@@ -72,6 +72,8 @@ static int launch_factor_t(const WsLayout &L, char *ws, int schedule, int flags,
     F.T = (double *)(ws + L.off_T);
     F.T2 = (L.H < L.p) ? (double *)(ws + L.off_T2) : nullptr;
     F.TF = F.TF2 = nullptr;
+    F.cexp = nullptr;
+    F.lm = 0;
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;
@@ -156,6 +158,8 @@ static int launch_factor_dag_at_t(const WsLayout &L, double *tiles, double *T, c
     F.T = T;
     F.T2 = nullptr;
     F.TF = F.TF2 = nullptr;
+    F.cexp = nullptr;
+    F.lm = 0;
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;

@@ -31,9 +31,11 @@ int launch_factor_mixed(const WsLayout &L, char *ws, int flags, cudaStream_t st,
 int launch_factor(const WsLayout &L, char *ws, int schedule, int flags, cudaStream_t st,
                   unsigned long long watchdog_ns, unsigned long long *trace, unsigned int trace_cap);
 
-// Column-major <-> tile layout (K1); cm2tile also flags non-finite input in ctrl.
+// Column-major <-> tile layout (K1); cm2tile also flags non-finite input in
+// ctrl and, if cexp is not NULL, raises cexp[c] (cleared beforehand) to the
+// largest biased FP64 exponent of column c (the mixed path's column scaling).
 int launch_cm2tile(const double *A, int64_t lda, int64_t m, int64_t n, double *tiles, int nb, int p,
-                   int q, SchedCtrl *ctrl, cudaStream_t st);
+                   int q, SchedCtrl *ctrl, int *cexp, cudaStream_t st);
 int launch_tile2cm(const double *tiles, int nb, int p, int q, int64_t m, int64_t n, double *A,
                    int64_t lda, int upper_only, int64_t rows_out, cudaStream_t st);
 int launch_strips2cm(const double *T, int nb, int ib, int p, int q, int64_t n, double *Tout,

@@ -29,6 +29,10 @@ static int launch_factor_mixed_t(const WsLayout &L, char *ws, int flags, cudaStr
     // the tensor-core updates need the panels' T^T operands (a TILEQR_TF32 layout)
     if (F.TF == nullptr || (F.T2 != nullptr && F.TF2 == nullptr))
         return TILEQR_ERR_WORKSPACE;
+    if (L.off_cexp == 0)
+        return TILEQR_ERR_WORKSPACE;
+    F.cexp = (const int *)(ws + L.off_cexp);
+    F.lm = ceil_log2_sqrt(L.m);
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;

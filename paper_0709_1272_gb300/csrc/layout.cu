@@ -20,8 +20,11 @@ static int grid_for(size_t warps_needed)
     return (int)(ctas ? ctas : 1);
 }
 
+// One warp per tile column segment (nb contiguous doubles on both sides).
+// With cexp, also the largest biased exponent of every matrix column
+// (integer atomicMax per segment; cexp cleared beforehand).
 __global__ void k_cm2tile(const double *__restrict__ A, int64_t lda, int64_t m, int64_t n,
-                          double *__restrict__ tiles, int nb, int p, int q, int *nonfinite)
+                          double *__restrict__ tiles, int nb, int p, int q, int *nonfinite, int *cexp)
 {
     const int lane = threadIdx.x & 31;
     const size_t nseg = (size_t)p * q * nb;
@@ -39,13 +42,20 @@ __global__ void k_cm2tile(const double *__restrict__ A, int64_t lda, int64_t m, 
         }
         const double *src = A + col * lda + row0;
         double *dst = tiles + (t * nb + c) * nb;
+        unsigned int emax = 0;
         for (int r = lane; r < nb; r += 32) {
             double v = 0.0;
             if (r < valid) {
                 v = __ldg(src + r);
                 bad |= !isfinite(v);
+                emax = max(emax, (unsigned int)(__double2hiint(v) >> 20) & 0x7FFu);
             }
             dst[r] = v;
+        }
+        if (cexp != nullptr) {
+            emax = __reduce_max_sync(0xffffffffu, emax);
+            if (lane == 0 && emax > 0 && col < n)
+                atomicMax(cexp + col, (int)emax);
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0)
@@ -132,10 +142,10 @@ __global__ void k_rows2cm(const double *__restrict__ Bt, int nb, int p, int64_t 
 }
 
 int launch_cm2tile(const double *A, int64_t lda, int64_t m, int64_t n, double *tiles, int nb, int p,
-                   int q, SchedCtrl *ctrl, cudaStream_t st)
+                   int q, SchedCtrl *ctrl, int *cexp, cudaStream_t st)
 {
     const size_t segs = (size_t)p * q * nb;
-    k_cm2tile<<<grid_for(segs), 256, 0, st>>>(A, lda, m, n, tiles, nb, p, q, &ctrl->nonfinite);
+    k_cm2tile<<<grid_for(segs), 256, 0, st>>>(A, lda, m, n, tiles, nb, p, q, &ctrl->nonfinite, cexp);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
 }

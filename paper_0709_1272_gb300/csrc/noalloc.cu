@@ -117,7 +117,7 @@ extern "C" int tileqr_factor_noalloc(int64_t m, int64_t n, const double *A, int6
         return TILEQR_ERR_CUDA;
     if (m == 0 || n == 0)
         return 0;
-    rc = launch_cm2tile(A, lda, m, n, tiles, nb, L.p, L.q, (SchedCtrl *)sched, st);
+    rc = launch_cm2tile(A, lda, m, n, tiles, nb, L.p, L.q, (SchedCtrl *)sched, nullptr, st);
     if (rc)
         return rc;
     return launch_factor_dag_at(L, tiles, T, sched, st, watchdog_ns_default());

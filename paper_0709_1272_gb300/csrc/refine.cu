@@ -22,11 +22,83 @@
 namespace tqr {
 
 // ---------------------------------------------------------------------------
-// FP64 -> FP32 copies of the tiles and T strips (integer conversion).
+// Range: the correction solve runs in FP32, whose range (1e-38 .. 3e38) is
+// far narrower than FP64's.  So it works on scaled quantities, every scaling
+// a power of two (exact):
+//  - b enters as b' = b 2^-sb (largest entry in [1, 2)), x' solves A x' = b'
+//    and x = x' 2^sb at the end;
+//  - each vector v handed to M^{-1} is scaled by 2^-sv the same way;
+//  - the FP32 copy of R is R' = R D^-1, D = diag(2^s_c) with s_c from the
+//    largest exponent of column c of R (||R(:,c)|| = ||a_c|| <= 2^s_c, see
+//    col_shift), and its diagonal-tile inverses are D_j U_j^{-1};
+// so M^{-1} v = 2^sv D^-1 R'^{-1} (Q^T v 2^-sv)(0:n) with every FP32
+// quantity of moderate size.  The reflectors and T are scale-free.
+
+// FP64 -> FP32 copy (integer conversion), for the T strips.
 __global__ void k_to_f32(const double *__restrict__ src, float *__restrict__ dst, size_t n)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         dst[i] = f64_to_f32_bits(src[i]);
+}
+
+// Largest biased exponent of the entries of R's column c (the tiles on and
+// above the diagonal, rows <= c in the diagonal tile), into cexp[c] (cleared
+// beforehand); one warp per tile column segment.
+__global__ void k_r_colexp(const double *__restrict__ tiles, int p, int q, int *cexp)
+{
+    const int lane = threadIdx.x & 31;
+    const size_t nseg = (size_t)q * 128 * q;   // (column, tile row i < q)
+    for (size_t s = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nseg;
+         s += (size_t)gridDim.x * (blockDim.x >> 5)) {
+        const int i = (int)(s % q);
+        const int col = (int)(s / q), j = col >> 7, c = col & 127;
+        if (i > j)
+            continue;
+        const double *src = tiles + (((size_t)j * p + i) * 128 + c) * 128;
+        unsigned int e = 0;
+        for (int r = lane; r < 128; r += 32)
+            if (i < j || r <= c)
+                e = max(e, (unsigned int)(__double2hiint(ldcg(src + r)) >> 20) & 0x7FFu);
+        e = __reduce_max_sync(0xffffffffu, e);
+        if (lane == 0 && e > 0)
+            atomicMax(cexp + col, (int)e);
+    }
+}
+
+// FP32 copy of the factored tiles: R' = R D^-1 (tiles i < j, and rows <= c
+// of diagonal tile j), the reflectors as they are.
+__global__ void k_tiles_to_f32(const double *__restrict__ tiles, int p, int q, const int *__restrict__ cexp,
+                               int lm, float *__restrict__ dst)
+{
+    const size_t n = (size_t)p * q * 128 * 128;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t t = e >> 14;
+        const int i = (int)(t % p), j = (int)(t / p), c = (int)((e >> 7) & 127), r = (int)(e & 127);
+        const bool is_r = i < j || (i == j && r <= c);
+        dst[e] = f64_to_f32_sc(tiles[e], is_r ? col_shift(cexp[j * 128 + c], lm) : 0);
+    }
+}
+
+// Largest biased exponent of a vector's entries, into *out (cleared
+// beforehand).
+__global__ void k_vec_maxexp(const double *__restrict__ v, int64_t n, int *out)
+{
+    unsigned int e = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        e = max(e, (unsigned int)(__double2hiint(v[i]) >> 20) & 0x7FFu);
+    e = __reduce_max_sync(0xffffffffu, e);
+    if ((threadIdx.x & 31) == 0 && e > 0)
+        atomicMax(out, (int)e);
+}
+// The power-of-two exponent that brings a largest biased exponent e to [1, 2).
+__device__ __forceinline__ int unit_shift(int e) { return e > 0 ? e - 1023 : 0; }
+
+// y = x 2^(sign * unit_shift(*e))  (exact)
+__global__ void k_scale_pow2(const double *__restrict__ x, double *y, int64_t n, const int *e, int sign)
+{
+    const int k = sign * unit_shift(*e);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = ldexp(x[i], k);
 }
 
 // Inverse of the upper triangle of diagonal tile j (nb = 128), written as
@@ -34,7 +106,8 @@ __global__ void k_to_f32(const double *__restrict__ src, float *__restrict__ dst
 // column and row.  One CTA per tile, thread c computes column c of the
 // inverse by back substitution in FP64.
 __global__ void __launch_bounds__(128) k_inv_diag(const double *__restrict__ tiles, int p, int q, int64_t n,
-                                                  float *__restrict__ rinv, int *singular)
+                                                  const int *__restrict__ cexp, int lm, float *__restrict__ rinv,
+                                                  int *singular)
 {
     extern __shared__ double U[];   // 128 x 129, [r][c] row-major padded
     double *rcp = U + 128 * 129;
@@ -72,9 +145,11 @@ __global__ void __launch_bounds__(128) k_inv_diag(const double *__restrict__ til
             x[r] = -acc * rcp[r];
         }
     }
+    // the inverse of the column-scaled tile U D_j^-1 is D_j U^-1: row r
+    // scaled by 2^s_r
 #pragma unroll 1
     for (int r = 0; r < 128; r++)
-        out[r] = f64_to_f32_bits(x[r]);
+        out[r] = r < nvalid ? f64_to_f32_sc(x[r], -col_shift(cexp[j * 128 + r], lm)) : 0.0f;
 }
 
 // ---------------------------------------------------------------------------
@@ -312,17 +387,22 @@ __global__ void k_scale_copy(double alpha, const double *__restrict__ x, double 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = alpha * x[i];
 }
-// FP64 vector (length m) -> FP32 row blocks X (p x 128, zero-padded), and back (first n rows)
-__global__ void k_vec_to_blocks(const double *__restrict__ v, int64_t m, float *X, int p)
+// FP64 vector (length m) scaled by 2^-sv -> FP32 row blocks X (p x 128,
+// zero-padded); and back (first n rows): v_c = X_c 2^(sv - s_c), undoing the
+// vector's scaling and R's column scaling (sv = unit_shift(*vexp)).
+__global__ void k_vec_to_blocks(const double *__restrict__ v, int64_t m, float *X, int p, const int *vexp)
 {
+    const int sv = unit_shift(*vexp);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)p * 128;
          i += (int64_t)gridDim.x * blockDim.x)
-        X[i] = i < m ? f64_to_f32_bits(v[i]) : 0.0f;
+        X[i] = i < m ? f64_to_f32_sc(v[i], sv) : 0.0f;
 }
-__global__ void k_blocks_to_vec(const float *__restrict__ X, int64_t n, double *v)
+__global__ void k_blocks_to_vec(const float *__restrict__ X, int64_t n, double *v, const int *vexp,
+                                const int *__restrict__ cexp, int lm)
 {
+    const int sv = unit_shift(*vexp);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v[i] = f32_to_f64_bits(X[i]);
+        v[i] = f32_to_f64_sc(X[i], sv - col_shift(cexp[i], lm));
 }
 
 }  // namespace tqr
@@ -371,7 +451,7 @@ constexpr int DOT_BLOCKS = 152;
 constexpr int GMRES_RESTART = 40;
 
 struct RefineLayout {
-    size_t tiles32, T32, T2_32, rinv, X, sched, vecs, dots, flag, end;
+    size_t tiles32, T32, T2_32, rinv, X, sched, vecs, dots, flag, cexp, end;
     size_t sched_bytes, cnt_bytes;
     unsigned long long nlb, nsb;   // queue capacities: DLARFB; DSSRFB + DTTMQR
     int64_t m, n;
@@ -417,8 +497,10 @@ RefineLayout refine_layout(const tileqr_desc *d)
     off += align256((size_t)mm * 8 * (4 + (GMRES_RESTART + 1) + GMRES_RESTART));
     R.dots = off;
     off += align256((size_t)(GMRES_RESTART + 2) * DOT_BLOCKS * 8);
-    R.flag = off;
+    R.flag = off;   // [0] singular column + 1, [1] exponent of b, [2] exponent of the preconditioned vector
     off += 256;
+    R.cexp = off;   // largest exponent per column of R (q * 128 ints)
+    off += align256((size_t)d->q * 128 * 4);
     R.end = off;
     return R;
 }
@@ -468,8 +550,12 @@ struct Refiner {
     int precond(const double *v, double *z)
     {
         float *X = (float *)(ws + L.X);
-        k_vec_to_blocks<<<DOT_BLOCKS, 256, 0, st>>>(v, L.m, X, L.p);
-        count_launch();
+        int *vexp = (int *)(ws + L.flag) + 2;
+        if (cudaMemsetAsync(vexp, 0, sizeof(int), st) != cudaSuccess)
+            return TILEQR_ERR_CUDA;
+        k_vec_maxexp<<<DOT_BLOCKS, 256, 0, st>>>(v, L.m, vexp);
+        k_vec_to_blocks<<<DOT_BLOCKS, 256, 0, st>>>(v, L.m, X, L.p, vexp);
+        count_launch(2);
         // Q^T on one column
         char *sched = ws + L.sched;
         if (cudaMemsetAsync(sched, 0, L.sched_bytes, st) != cudaSuccess)
@@ -521,7 +607,8 @@ struct Refiner {
                 count_launch();
             }
         }
-        k_blocks_to_vec<<<DOT_BLOCKS, 256, 0, st>>>(X, L.n, z);
+        k_blocks_to_vec<<<DOT_BLOCKS, 256, 0, st>>>(X, L.n, z, vexp, (const int *)(ws + L.cexp),
+                                                    ceil_log2_sqrt(L.n));
         count_launch();
         return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
     }
@@ -597,18 +684,23 @@ extern "C" int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_
             return TILEQR_ERR_CUDA;
         R.grid_apply = grid;
     }
-    // FP32 factors and inverted diagonal tiles of R
+    // FP32 factors (R column-scaled) and inverted diagonal tiles of R
     int *flag = (int *)(R.ws + L.flag);
+    int *cexp = (int *)(R.ws + L.cexp);
+    const int lm = ceil_log2_sqrt(d->n);
     cudaMemsetAsync(flag, 0, 256, st);
-    const size_t ntile = (size_t)d->p * d->q * 128 * 128, nT = (size_t)d->p * d->q * d->ib * 128;
-    k_to_f32<<<4 * DOT_BLOCKS, 256, 0, st>>>(d->tiles, (float *)(R.ws + L.tiles32), ntile);
+    cudaMemsetAsync(cexp, 0, (size_t)d->q * 128 * 4, st);
+    const size_t nT = (size_t)d->p * d->q * d->ib * 128;
+    k_r_colexp<<<4 * DOT_BLOCKS, 256, 0, st>>>(d->tiles, d->p, d->q, cexp);
+    k_tiles_to_f32<<<4 * DOT_BLOCKS, 256, 0, st>>>(d->tiles, d->p, d->q, cexp, lm, (float *)(R.ws + L.tiles32));
     k_to_f32<<<DOT_BLOCKS, 256, 0, st>>>(d->T, (float *)(R.ws + L.T32), nT);
     if (d->T2 != nullptr) {
         k_to_f32<<<DOT_BLOCKS, 256, 0, st>>>(d->T2, (float *)(R.ws + L.T2_32), nT);
         count_launch();
     }
-    k_inv_diag<<<d->q, 128, (128 * 129 + 128) * 8, st>>>(d->tiles, d->p, d->q, d->n, (float *)(R.ws + L.rinv), flag);
-    count_launch(3);
+    k_inv_diag<<<d->q, 128, (128 * 129 + 128) * 8, st>>>(d->tiles, d->p, d->q, d->n, cexp, lm,
+                                                        (float *)(R.ws + L.rinv), flag);
+    count_launch(4);
     if (cudaGetLastError() != cudaSuccess)
         return TILEQR_ERR_CUDA;
     int hflag = 0;
@@ -617,17 +709,23 @@ extern "C" int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_
     if (hflag)
         return TILEQR_ERR_SINGULAR;
 
-    const double bnorm = std::sqrt(R.dot(b, b, d->m));
+    // b' = b 2^-sb (largest entry in [1, 2)); the loop solves A x' = b'
+    int *bexp = flag + 1;
+    k_vec_maxexp<<<DOT_BLOCKS, 256, 0, st>>>(b, d->m, bexp);
+    k_scale_pow2<<<DOT_BLOCKS, 256, 0, st>>>(b, R.bc, d->m, bexp, -1);
+    count_launch(2);
+    const double *bs = R.bc;
+    const double bnorm = std::sqrt(R.dot(bs, bs, d->m));
     if (bnorm == 0.0) {
         cudaMemsetAsync(x, 0, (size_t)d->n * 8, st);
         info->converged = 1;
         return 0;
     }
-    // x0 = M^{-1} b
-    int rc = R.precond(b, x);
+    // x0 = M^{-1} b'
+    int rc = R.precond(bs, x);
     if (rc)
         return rc;
-    rc = R.gemv_residual(x, R.r, b, false);
+    rc = R.gemv_residual(x, R.r, bs, false);
     if (rc)
         return rc;
     double rnorm = std::sqrt(R.dot(R.r, R.r, d->m));
@@ -722,7 +820,7 @@ extern "C" int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_
             k_multiaxpy<<<DOT_BLOCKS, 256, 0, st>>>(R.Z, R.mm, jdone, hdev, x, d->n, 1.0);
             count_launch();
         }
-        rc = R.gemv_residual(x, R.r, b, false);
+        rc = R.gemv_residual(x, R.r, bs, false);
         if (rc)
             return rc;
         const double rn = std::sqrt(R.dot(R.r, R.r, d->m));
@@ -733,5 +831,10 @@ extern "C" int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_
     info->iterations = outer;
     info->rel_residual = rnorm / bnorm;
     info->converged = rnorm / bnorm <= tol;
+    // x = x' 2^sb
+    k_scale_pow2<<<DOT_BLOCKS, 256, 0, st>>>(x, x, d->n, bexp, 1);
+    count_launch();
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
 }

@@ -305,13 +305,19 @@ __device__ __noinline__ void task_larfb(double *sm, double *Ct, const double *Vt
 
 // ---------------------------------------------------------------------------
 // Sum of squares of x[t0:rows) for extreme magnitudes (rare path, one
-// thread): returns s2 and scl with ||x|| = scl * sqrt(s2), scl = max |x|.
+// thread): returns s2 and scl with ||x|| = scl * sqrt(s2), scl = max |x|
+// (s2 = 0, scl = 1 for an exactly zero x).
 __device__ __noinline__ static void rescaled_sumsq(const double *x, int t0, int rows, double *s2,
                                                    double *scl)
 {
     double mx = 0.0;
     for (int r = t0; r < rows; r++)
         mx = fmax(mx, fabs(x[r]));
+    if (mx == 0.0) {
+        *s2 = 0.0;
+        *scl = 1.0;
+        return;
+    }
     const double inv = 1.0 / mx;
     double acc = 0.0;
     for (int r = t0; r < rows; r++)
@@ -339,8 +345,15 @@ __device__ __forceinline__ void column_scalars(const double *x, int t0, int rows
     double s2 = warp_allsum(part0 + part1);
     if (lane == 0) {
         double beta = alpha, tau = 0.0, scale = 0.0;
+        // a sum of squares outside [1e-280, 1e280] may have under- or
+        // overflowed (entries below ~1e-162 square to zero): recompute it
+        // scaled, so that s2 == 0 means an exactly zero tail
+        double scl = 1.0;
+        const bool s2_in_range = s2 > 1e-280 && s2 < 1e280;
+        if (!s2_in_range)
+            rescaled_sumsq(x, t0, rows, &s2, &scl);
         if (s2 != 0.0) {
-            if (s2 > 1e-280 && s2 < 1e280 && fabs(alpha) < 1e140) {
+            if (s2_in_range && fabs(alpha) < 1e140) {
                 // common case: alpha^2 + sigma^2 (and beta * d below) stay in
                 // range, so one sqrt and one reciprocal suffice:
                 // tau = (beta - alpha) / beta = -d^2 / (beta d), scale = 1/d = beta / (beta d)
@@ -352,9 +365,6 @@ __device__ __forceinline__ void column_scalars(const double *x, int t0, int rows
                 scale = beta * inv;
             } else {
                 // extreme magnitudes (rare): rescaled norm, hypot, two divisions
-                double scl = 1.0;
-                if (!(s2 > 1e-280 && s2 < 1e280))
-                    rescaled_sumsq(x, t0, rows, &s2, &scl);
                 const double h = hypot(alpha, scl * sqrt(s2));
                 beta = (alpha >= 0.0) ? -h : h;
                 tau = (beta - alpha) / beta;
@@ -567,9 +577,10 @@ __device__ __noinline__ void trailing_update(double *sm, double *At, double *Rt,
     }
 }
 
-// FP64 <-> FP32 by integer operations (the F2F instructions run at the FP64
-// rate on GB300): see tile_mixed.cuh for the same conversions on the tensor-
-// core path.
+// FP64 -> FP32 by integer operations (the F2F instructions run at the FP64
+// rate on GB300), for the reflectors and T (entries of magnitude <= 2 by
+// construction); the tile's values use the column-scaled conversions of
+// common.cuh.
 __device__ __forceinline__ float panel_f64_to_f32(double x)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -583,25 +594,17 @@ __device__ __forceinline__ float panel_f64_to_f32(double x)
     f = (e > 1150u) ? (sgn | 0x7F800000u) : f;
     return __uint_as_float(f);
 }
-__device__ __forceinline__ double panel_f32_to_f64(float v)
-{
-    const uint32_t f = __float_as_uint(v);
-    const uint32_t sgn = f & 0x80000000u;
-    uint32_t hi = sgn | (((f & 0x7FFFFFFFu) >> 3) + 0x38000000u);
-    uint32_t lo = f << 29;
-    const bool zero = (f & 0x7F800000u) == 0u;
-    hi = zero ? sgn : hi;
-    lo = zero ? 0u : lo;
-    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
-}
 
 // Mixed-precision form of trailing_update (TILEQR_TF32 builds): the block
 // product Y = B_l + V_l^T C, W = T_l^T Y and the delta V_l W are formed in
 // FP32 on the CUDA cores; the FP64 tile then receives C -= delta and
 // B_l -= W with one FP64 subtraction per element.  The reflectors, tau and
 // T_l were formed in FP64 by the panel and are only read here.
+// The tile's column values are scaled by 2^-s_c into FP32 (s_c from the
+// column exponents cex, common.cuh), so any magnitude of A stays in range.
 template <int NB, int S, bool TRI = false>
-__device__ __noinline__ void trailing_update_mixed(double *sm, double *At, double *Rt, int l0, int r0)
+__device__ __noinline__ void trailing_update_mixed(double *sm, double *At, double *Rt, int l0, int r0,
+                                                   const int *cex, int lm)
 {
     using C_ = F64Cfg<NB, S>;
     constexpr int W = C_::W, LDF = NB + 1, LDVF = S + 1;
@@ -611,10 +614,13 @@ __device__ __noinline__ void trailing_update_mixed(double *sm, double *At, doubl
     float *Vf = Cf + W * LDF;                         // NB x (S+1), [r][a]
     float *Yf = Vf + NB * LDVF;                       // S x W, [a][c]
     float *Tf = Yf + S * W;                           // S x S, T(b,a) at b + a*S
-    static_assert((W * LDF + NB * LDVF + S * W + S * S) * 4 <= W * (NB + 1) * 8, "fits the chunk area");
+    int *sh = (int *)(Tf + S * S);                    // NB column shifts
+    static_assert((W * LDF + NB * LDVF + S * W + S * S + NB) * 4 <= W * (NB + 1) * 8, "fits the chunk area");
     const double *Vs = sm + C_::OFF_V;
     const double *Ts = sm + C_::OFF_T;
     const int tid = threadIdx.x;
+    for (int c = tid; c < NB; c += NT)
+        sh[c] = cex ? col_shift(__ldg(cex + c), lm) : 0;
     for (int idx = tid; idx < NB * S; idx += NT) {
         const int r = idx / S, a = idx - r * S;
         Vf[r * LDVF + a] = panel_f64_to_f32(Vs[r * C_::LDV + a]);
@@ -627,12 +633,13 @@ __device__ __noinline__ void trailing_update_mixed(double *sm, double *At, doubl
         for (int idx = tid; idx < W * NB; idx += NT) {
             const int c = idx / NB, r = idx - c * NB;
             const bool in = c < nc && r >= r0 && (!TRI || r <= c0 + c);
-            Cf[c * LDF + r] = in ? panel_f64_to_f32(ldcg(At + (size_t)(c0 + c) * NB + r)) : 0.0f;
+            Cf[c * LDF + r] = in ? f64_to_f32_sc(ldcg(At + (size_t)(c0 + c) * NB + r), sh[c0 + c]) : 0.0f;
         }
         __syncthreads();
         // Y = B_l + V^T C: thread (c, quarter of the block rows)
         {
             const int c = tid & (W - 1), ag = tid >> 6;
+            const int sc = c < nc ? sh[c0 + c] : 0;
             constexpr int AQ = S / 4;
             float y[AQ];
             double bv[AQ];
@@ -640,7 +647,7 @@ __device__ __noinline__ void trailing_update_mixed(double *sm, double *At, doubl
             for (int i = 0; i < AQ; i++) {
                 const int a = ag * AQ + i;
                 bv[i] = (Rt != nullptr && c < nc) ? ldcg(Rt + (size_t)(c0 + c) * NB + l0 + a) : 0.0;
-                y[i] = panel_f64_to_f32(bv[i]);
+                y[i] = f64_to_f32_sc(bv[i], sc);
             }
             for (int r = r0; r < (TRI ? l0 + S : NB); r++) {
                 const float cv = Cf[c * LDF + r];
@@ -667,7 +674,7 @@ __device__ __noinline__ void trailing_update_mixed(double *sm, double *At, doubl
                 const int a = ag * AQ + i;
                 Yf[a * W + c] = w[i];
                 if (Rt != nullptr && c < nc)
-                    stcg(Rt + (size_t)(c0 + c) * NB + l0 + a, bv[i] - panel_f32_to_f64(w[i]));
+                    stcg(Rt + (size_t)(c0 + c) * NB + l0 + a, bv[i] - f32_to_f64_sc(w[i], sc));
             }
             __syncthreads();
         }
@@ -691,7 +698,7 @@ __device__ __noinline__ void trailing_update_mixed(double *sm, double *At, doubl
                     const int c = half * CH + j;
                     if (c < nc) {
                         double *p = At + (size_t)(c0 + c) * NB + r;
-                        stcg(p, ldcg(p) - panel_f32_to_f64(d[j]));
+                        stcg(p, ldcg(p) - f32_to_f64_sc(d[j], sh[c0 + c]));
                     }
                 }
             }
@@ -704,7 +711,7 @@ __device__ __noinline__ void trailing_update_mixed(double *sm, double *At, doubl
 // the diagonal, V below), T strip to Tt.  Inner blocks l in order: panel
 // factorization, T_l, then the block applied to the trailing tile columns.
 template <int NB, int S, bool MIXED = false>
-__device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt)
+__device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt, const int *cex = nullptr, int lm = 0)
 {
     using C_ = F64Cfg<NB, S>;
     constexpr int LDC = C_::LDC, LDV = C_::LDV;
@@ -732,7 +739,7 @@ __device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt)
         __syncthreads();
         build_t<NB, S>(sm, l0, Tt, l0);
         if constexpr (MIXED)
-            trailing_update_mixed<NB, S>(sm, At, nullptr, l0, l0);
+            trailing_update_mixed<NB, S>(sm, At, nullptr, l0, l0, cex, lm);
         else
             trailing_update<NB, S>(sm, At, nullptr, l0, l0);
     }
@@ -747,7 +754,8 @@ __device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt)
 // j then has nonzeros in rows 0..j only, so inner block l works on rows
 // < l0 + S.
 template <int NB, int S, bool MIXED = false, bool TRI = false>
-__device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, double *Tt)
+__device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, double *Tt, const int *cex = nullptr,
+                                        int lm = 0)
 {
     using C_ = F64Cfg<NB, S>;
     constexpr int LDC = C_::LDC, LDV = C_::LDV;
@@ -782,7 +790,7 @@ __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, doub
         __syncthreads();
         build_t<NB, S>(sm, 0, Tt, l0, TRI ? l0 + S : NB);
         if constexpr (MIXED)
-            trailing_update_mixed<NB, S, TRI>(sm, At, Rt, l0, 0);
+            trailing_update_mixed<NB, S, TRI>(sm, At, Rt, l0, 0, cex, lm);
         else
             trailing_update<NB, S, TRI>(sm, At, Rt, l0, 0);
     }

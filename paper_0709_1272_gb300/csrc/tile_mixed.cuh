@@ -326,12 +326,16 @@ __device__ __noinline__ void mixed_build_tfull(unsigned char *smb, const double 
 // double-buffered A operand of those (T^T chunks, then V chunks), and before
 // each a per-warp transpose scratch for staging Y and W^T.  Returns
 // false on a tensor-core wait timeout (an error is recorded).
+// B and C enter the products scaled per column by 2^-s_c (the column
+// shifts of common.cuh, staged after the operand areas), and W and D leave
+// them scaled back, so any magnitude of A stays within FP32's range.
 constexpr size_t TF_UPDATE_SMEM = 192 * 1024;
+constexpr size_t TF_UPDATE_SMEM_TOTAL = TF_UPDATE_SMEM + 128 * sizeof(int);
 
 template <int S, int VK>
 __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt, double *Ct, const double *Vt,
-                                                  const unsigned char *TFg, uint32_t tmem, uint64_t *mbar,
-                                                  uint32_t &phase, int *err)
+                                                  const unsigned char *TFg, const int *cex, int lm, uint32_t tmem,
+                                                  uint64_t *mbar, uint32_t &phase, int *err)
 {
     constexpr int NB = 128, KC = 32, OPB = NB * KC * 4, R2 = 8 * OPB;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -399,6 +403,10 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
             tc::prefetch_l2(Bt, NB * NB * 8);
         tc::prefetch_l2(TFg, TF_BYTES);
     }
+    int *sh = (int *)(sm + TF_UPDATE_SMEM);   // column shifts of the updated tile column
+    if (tid < NB)
+        sh[tid] = cex ? col_shift(__ldg(cex + tid), lm) : 0;
+    __syncthreads();
     // ---- P = V^T C: A = V^T (row = reflector, K = tile row), B = C^T (row =
     // column); sets at 0 and 4 OPB
     for (int rr = 0; rr < NB / KC; rr++) {
@@ -423,8 +431,9 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
             const uint32_t off = tc::kmajor_off(p_row(x), 4 * p_kgrp(x), KC);
             store_split4(sm, so, so + OPB, off, f64_to_f32_bits(v[x][0]), f64_to_f32_bits(v[x][1]),
                          f64_to_f32_bits(v[x][2]), f64_to_f32_bits(v[x][3]));
-            store_split4(sm, so + 2 * OPB, so + 3 * OPB, off, f64_to_f32_bits(c[x][0]), f64_to_f32_bits(c[x][1]),
-                         f64_to_f32_bits(c[x][2]), f64_to_f32_bits(c[x][3]));
+            const int sc = sh[p_row(x)];
+            store_split4(sm, so + 2 * OPB, so + 3 * OPB, off, f64_to_f32_sc(c[x][0], sc), f64_to_f32_sc(c[x][1], sc),
+                         f64_to_f32_sc(c[x][2], sc), f64_to_f32_sc(c[x][3], sc));
         }
         mixed_issue(&mbar[b], [&]() { mma_chunk(tmem, sbase + so, sbase + so + 2 * OPB, rr == 0); });
     }
@@ -444,7 +453,7 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         tc::tmem_ld32(tmem + lane_off + c0, v);
 #pragma unroll
         for (int j = 0; j < 32; j++)
-            v[j] += Bt ? f64_to_f32_bits(bv[j]) : 0.0f;
+            v[j] += Bt ? f64_to_f32_sc(bv[j], sh[c0 + j]) : 0.0f;
         stage_bop(v, c0);
     }
     __syncthreads();   // every warp is done with its scratch in R2
@@ -477,7 +486,7 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
                 bv[j] = ldcg(Bt + (size_t)(c0 + j) * NB + a_row);
 #pragma unroll
             for (int j = 0; j < 32; j++)
-                stcg(Bt + (size_t)(c0 + j) * NB + a_row, bv[j] - f32_to_f64_bits(w[j]));
+                stcg(Bt + (size_t)(c0 + j) * NB + a_row, bv[j] - f32_to_f64_sc(w[j], sh[c0 + j]));
         }
         stage_bop(w, c0);
     }
@@ -519,7 +528,7 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         tc::tmem_ld32(tmem + lane_off + c0, v);
 #pragma unroll
         for (int j = 0; j < 32; j++)
-            stcg(Ct + (size_t)(c0 + j) * NB + a_row, old[j] - f32_to_f64_bits(v[j]));
+            stcg(Ct + (size_t)(c0 + j) * NB + a_row, old[j] - f32_to_f64_sc(v[j], sh[c0 + j]));
     }
     tc::fence_before_sync();
     __syncthreads();

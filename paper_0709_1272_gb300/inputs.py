@@ -53,6 +53,33 @@ def kappa_matrix(n: int, kappa: float, seed: int):
     return A, s, u, v
 
 
+def kappa_factors(n: int, kappa: float, seed: int):
+    """(s, u, v) of kappa_matrix(n, kappa, seed), without forming A: the same
+    draws, so A = (I - 2uu^T) diag(s) (I - 2vv^T) can be formed elsewhere
+    (e.g. on the device) from them."""
+    g = _rng(seed)
+    u = g.standard_normal(n)
+    u /= np.linalg.norm(u)
+    v = g.standard_normal(n)
+    v /= np.linalg.norm(v)
+    s = kappa ** (-np.arange(n, dtype=np.float64) / max(n - 1, 1))
+    return s, u, v
+
+
+def kappa_columns(n: int, kappa: float, seed: int, j0: int, j1: int) -> np.ndarray:
+    """Columns j0..j1-1 of kappa_matrix(n, kappa, seed) (n x (j1-j0),
+    column-major), formed entry by entry from the same (s, u, v)."""
+    s, u, v = kappa_factors(n, kappa, seed)
+    c = float(u @ (s * v))
+    cols = np.arange(j0, j1)
+    A = np.zeros((n, j1 - j0), dtype=np.float64, order="F")
+    A[cols, np.arange(j1 - j0)] = s[cols]
+    A -= 2.0 * np.outer(u, (s * u)[cols])
+    A -= 2.0 * np.outer(s * v, v[cols])
+    A += 4.0 * c * np.outer(u, v[cols])
+    return A
+
+
 def spd_matrix(n: int, seed: int) -> np.ndarray:
     """Symmetric positive definite n x n: (G + G^T)/2 + n I with G uniform[-1,1)
     (column-major).  Each row's off-diagonal absolute sum is about n/2 < n, so

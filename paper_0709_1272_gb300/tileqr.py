@@ -26,6 +26,8 @@ TILEQR_ERR_SINGULAR = 1005
 TILEQR_ERR_UNSUPPORTED = 1006
 TILEQR_ERR_SCRATCH_LIMIT = 1007
 TILEQR_ERR_NOT_SPD = 1008
+TILEQR_UPDATE_LARFB, TILEQR_UPDATE_SSRFB = 0, 1
+TILEQR_MIXED_UPDATE_WS_BYTES = 132 * 1024
 
 EXPORTED = [
     "tileqr_workspace_size", "tileqr_factor", "tileqr_status", "tileqr_get_R",
@@ -39,7 +41,7 @@ EXPORTED = [
     "tileqr_apply_q", "tileqr_form_q",
     "tileqr_cholesky_workspace_size", "tileqr_cholesky", "tileqr_cholesky_get_L", "tileqr_cholesky_info",
     "tileqr_lu_workspace_size", "tileqr_lu", "tileqr_lu_info", "tileqr_lu_get_factors",
-    "tileqr_lu_solve_workspace_size", "tileqr_lu_solve",
+    "tileqr_lu_solve_workspace_size", "tileqr_lu_solve", "tileqr_mixed_update_tile",
 ]
 
 
@@ -136,6 +138,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_lu_get_factors": (i32, [dp, vp, i64, vp, i64, vp, i64, vp]),
         "tileqr_lu_solve_workspace_size": (i32, [dp, i64, ctypes.POINTER(sz)]),
         "tileqr_lu_solve": (i32, [dp, vp, i64, i64, vp, sz, vp]),
+        "tileqr_mixed_update_tile": (i32, [i32, i32, vp, vp, vp, vp, vp, sz, vp]),
         "tileqr_task_graph": (i32, [i64, i64, i32, i32, i32, vp, vp, vp, vp, ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)]),
     }
@@ -521,6 +524,20 @@ def tileqr_apply_qt(f: Factorization, B: torch.Tensor, stream=None) -> torch.Ten
 
 def tileqr_solve_ls(f: Factorization, B: torch.Tensor, stream=None) -> torch.Tensor:
     return f.solve_ls(B, stream)
+
+
+def tileqr_mixed_update_tile(kind: int, ib: int, V: torch.Tensor, T: torch.Tensor, B: torch.Tensor | None,
+                             C: torch.Tensor, stream=None) -> None:
+    """One TILEQR_TF32 update task (DLARFB or DSSRFB) on 128 x 128 column-
+    major float64 CUDA tiles, B and C updated in place; T is the ib x 128 strip
+    (column-major)."""
+    for t in (V, T, C) + ((B,) if B is not None else ()):
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    ws = torch.empty(TILEQR_MIXED_UPDATE_WS_BYTES, dtype=torch.uint8, device=C.device)
+    _check(load().tileqr_mixed_update_tile(kind, ib, ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                           ctypes.c_void_p(B.data_ptr()) if B is not None else None,
+                                           ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                           ws.numel(), _stream_ptr(stream)), "tileqr_mixed_update_tile")
 
 
 def tileqr_launch_count() -> int:

@@ -122,6 +122,21 @@ def test_extreme_magnitudes(tq, scale):
     assert _rel(T, ref.T) <= TOL
 
 
+def test_tails_whose_squares_underflow(tq):
+    """A graded matrix (singular values 1 .. 1e-6) scaled by 2^-530: late
+    panel columns have tails of ~1e-166, whose squares underflow to zero;
+    the panel must still see a nonzero tail (rescaled norm), as the oracle
+    does.  R is compared at unit scale (exact power-of-two rescaling)."""
+    A, _, _, _ = inputs.kappa_matrix(384, 1e6, seed=33)
+    As = np.ldexp(A, -530)
+    f, _, AV, T, R = _gpu_factor(tq, As, 64, 16)
+    ref = oracle.tiled_qr(As, 64, 16)
+    assert np.all(np.isfinite(AV)) and np.all(np.isfinite(T))
+    assert _rel(np.ldexp(np.triu(AV[:384]), 530), np.ldexp(np.triu(ref.A[:384]), 530)) <= TOL
+    assert _rel(np.tril(AV, -1), np.tril(ref.A, -1)) <= TOL
+    assert _rel(T, ref.T) <= TOL
+
+
 def test_nonfinite_input_is_reported(tq):
     A = inputs.normal_matrix(300, 200, seed=1)
     A[17, 33] = np.nan

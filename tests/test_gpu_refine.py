@@ -86,3 +86,22 @@ def test_refine_tall_tree_mixed(tq, m, n, h):
     assert info.converged == 1 and relres <= 1e-12, (info.as_dict(), relres)
     assert info.initial_rel_residual > 1e-9
     assert np.linalg.norm(x - xt) / np.linalg.norm(xt) <= 1e-11
+
+
+@pytest.mark.parametrize("scale_exp", [500, -530])
+def test_refined_solve_extreme_magnitudes(tq, scale_exp):
+    """A and b scaled by 2^500 (~3e150) or 2^-530 (~3e-160): the FP32
+    correction solve works on power-of-two scaled quantities, so the refined
+    solve reaches the same accuracy as unscaled (x is scale-free here)."""
+    n = 1024
+    A, _, _, _ = inputs.kappa_matrix(n, 1e6, seed=21)
+    xt = inputs.normal_matrix(n, 1, seed=22).reshape(-1)
+    As = np.ldexp(A, scale_exp)
+    b = As @ xt
+    x, info = _solve(tq, As, b, tq.TILEQR_TF32)
+    assert np.all(np.isfinite(x))
+    # the residual at unit scale (exact rescaling; the norms of ~1e-160
+    # vectors would underflow)
+    relres = np.linalg.norm(np.ldexp(b - As @ x, -scale_exp)) / np.linalg.norm(np.ldexp(b, -scale_exp))
+    assert info.converged == 1 and relres <= 1e-12, (info.as_dict(), relres)
+    assert np.linalg.norm(x - xt) / np.linalg.norm(xt) <= 1e6 * 1e-12

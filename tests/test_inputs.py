@@ -26,3 +26,13 @@ def test_generators_are_deterministic():
     assert not np.array_equal(inputs.normal_matrix(7, 5, 1), inputs.normal_matrix(7, 5, 2))
     a = inputs.uniform_matrix(100, 50, 4)
     assert a.flags.f_contiguous and a.min() >= -1 and a.max() < 1
+
+
+def test_kappa_columns_and_factors_match_the_full_matrix():
+    A, s, u, v = inputs.kappa_matrix(300, 1e6, seed=5)
+    s2, u2, v2 = inputs.kappa_factors(300, 1e6, seed=5)
+    assert np.array_equal(s, s2) and np.array_equal(u, u2) and np.array_equal(v, v2)
+    assert np.allclose(inputs.kappa_columns(300, 1e6, 5, 17, 140), A[:, 17:140], rtol=0, atol=1e-15)
+    # singular values exactly s: cond_2 = kappa
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert np.allclose(sv, s, rtol=1e-10, atol=1e-14)
