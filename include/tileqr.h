@@ -363,6 +363,35 @@ int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_t lda, cons
                         int max_iter, double tol, void *workspace, size_t ws_bytes, tileqr_stream_t stream,
                         tileqr_refine_info *info);
 
+/* Least squares min ||A X - B||_F (m >= n, inconsistent systems included)
+ * to FP64 accuracy on top of a factorization d of A that may be inexact (a
+ * TILEQR_TF32 one, flat or tree form): iterative refinement of the
+ * augmented system [I A; A^T 0] [r; x] = [b; 0] (Bjorck, 1967; an addition
+ * to the paper).  Each step forms u = b - r - A x and w = -A^T r in FP64
+ * and solves for the correction with the factors: h = R^-T w,
+ * [d1; d2] = Q^T u (the DLARFB / DSSRFB graph of Sec. 3.2.1),
+ * dx = R^-1 (d1 - h), dr = Q [h; d2] (the same graph reversed); x += dx,
+ * r += dr.  It starts from x = 0, r = 0, so the first step is the plain
+ * solve of tileqr_solve_ls.  A column stops when ||dx|| <= tol ||x|| or when
+ * ||dx|| no longer halves (the rounding level of the FP64 residuals).
+ *   A, lda    the original matrix (device, column-major, FP64)
+ *   B, ldb    device m x nrhs right-hand sides (not modified)
+ *   X, ldx    device n x nrhs solution (output)
+ *   Rres, ldr device m x nrhs residuals b - A x (output; NULL to skip)
+ *   max_iter  steps at most (>= 1);  tol  stopping tolerance (> 0)
+ *   workspace tileqr_ls_refine_workspace_size(d, nrhs) bytes, 256-aligned
+ *   info      iterations; method 3; converged = every column stopped;
+ *             initial_rel_residual = the largest ||dx||/||x|| of the first
+ *             correction after the plain solve, rel_residual = that of the
+ *             last step
+ * Synchronous.  Returns 0, -i, TILEQR_ERR_WORKSPACE, TILEQR_ERR_SINGULAR,
+ * TILEQR_ERR_TIMEOUT or TILEQR_ERR_CUDA. */
+int tileqr_ls_refine_workspace_size(const tileqr_desc *d, int64_t nrhs, size_t *bytes);
+int tileqr_solve_ls_refine(const tileqr_desc *d, const double *A, int64_t lda, const double *B, int64_t ldb,
+                           int64_t nrhs, double *X, int64_t ldx, double *Rres, int64_t ldr, int max_iter,
+                           double tol, void *workspace, size_t ws_bytes, tileqr_stream_t stream,
+                           tileqr_refine_info *info);
+
 /* Tiled Cholesky factorization A = L L^T of a symmetric positive definite
  * matrix (Sec. 3.1, Algorithm 1): the tasks DPOTF2 (Cholesky of a diagonal
  * tile), DTRSM (L_ik = A_ik L_kk^{-T}) and DGSMM (A_ij -= L_ik L_jk^T, lower

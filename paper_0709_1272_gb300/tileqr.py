@@ -42,6 +42,7 @@ EXPORTED = [
     "tileqr_cholesky_workspace_size", "tileqr_cholesky", "tileqr_cholesky_get_L", "tileqr_cholesky_info",
     "tileqr_lu_workspace_size", "tileqr_lu", "tileqr_lu_info", "tileqr_lu_get_factors",
     "tileqr_lu_solve_workspace_size", "tileqr_lu_solve", "tileqr_mixed_update_tile",
+    "tileqr_ls_refine_workspace_size", "tileqr_solve_ls_refine",
 ]
 
 
@@ -139,6 +140,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_lu_solve_workspace_size": (i32, [dp, i64, ctypes.POINTER(sz)]),
         "tileqr_lu_solve": (i32, [dp, vp, i64, i64, vp, sz, vp]),
         "tileqr_mixed_update_tile": (i32, [i32, i32, vp, vp, vp, vp, vp, sz, vp]),
+        "tileqr_ls_refine_workspace_size": (i32, [dp, i64, ctypes.POINTER(sz)]),
+        "tileqr_solve_ls_refine": (i32, [dp, vp, i64, vp, i64, i64, vp, i64, vp, i64, i32, ctypes.c_double, vp,
+                                         sz, vp, ctypes.POINTER(tileqr_refine_info)]),
         "tileqr_task_graph": (i32, [i64, i64, i32, i32, i32, vp, vp, vp, vp, ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)]),
     }
@@ -495,6 +499,30 @@ class Factorization:
                                           tol, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream),
                                           ctypes.byref(info)), "tileqr_solve_refine")
         return x, info
+
+    def solve_ls_refine(self, A: torch.Tensor, B: torch.Tensor, max_iter: int = 10, tol: float = 1e-14,
+                        residual: bool = False, stream=None):
+        """min ||A X - B|| refined in FP64 on the augmented system (see
+        tileqr_solve_ls_refine); B is not modified.  Returns (X, info), or
+        (X, R, info) with the residuals B - A X if residual is True."""
+        A = as_colmajor(A)
+        B = as_colmajor(B)
+        nrhs = B.shape[1]
+        need = ctypes.c_size_t(0)
+        _check(load().tileqr_ls_refine_workspace_size(ctypes.byref(self.desc), nrhs, ctypes.byref(need)),
+               "tileqr_ls_refine_workspace_size")
+        ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=self.device)
+        X = colmajor_empty(self.n, nrhs, self.device)
+        R = colmajor_empty(self.m, nrhs, self.device) if residual else None
+        info = tileqr_refine_info()
+        _check(load().tileqr_solve_ls_refine(ctypes.byref(self.desc), ctypes.c_void_p(A.data_ptr()), _ld(A),
+                                             ctypes.c_void_p(B.data_ptr()), _ld(B), nrhs,
+                                             ctypes.c_void_p(X.data_ptr()), _ld(X),
+                                             ctypes.c_void_p(R.data_ptr()) if R is not None else None,
+                                             _ld(R) if R is not None else 1, max_iter, tol,
+                                             ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream),
+                                             ctypes.byref(info)), "tileqr_solve_ls_refine")
+        return (X, R, info) if residual else (X, info)
 
     def solve_ls(self, B: torch.Tensor, stream=None) -> torch.Tensor:
         """min ||A X - B||: B overwritten (X in its first n rows); returns X."""
