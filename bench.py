@@ -322,6 +322,27 @@ def run_batched(args, dev, rank, world, barrier, dist):
         assert f.status() == 0
         return e0.elapsed_time(e1) / 1e3
 
+    # consistent right-hand sides b_k = A_k x_k (x_k N(0,1)), so that the
+    # relative residual ||b - A x|| / ||b|| measures the solve's accuracy
+    xpool = torch.from_numpy(inputs.normal_matrix(sum(n for _, n in shapes), 1,
+                                                  seed=20070709 + 9 + 1000 * rank).reshape(-1)).to(dev)
+    bs, xo = [], 0
+    for (m, n), A in zip(shapes, mats):
+        bs.append(A @ xpool[xo:xo + n])
+        xo += n
+
+    def solve_time(bt, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record()
+        xs, info = bt.solve_ls(bs, max_iter=steps, tol=1e-14)
+        e1.record()
+        torch.cuda.synchronize()
+        rel = max((torch.linalg.vector_norm(b - A @ x) / torch.linalg.vector_norm(b)).item()
+                  for A, b, x in zip(mats, bs, xs))
+        return replicas.max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev), rel, info
+
     out = {"workload": f"{len(shapes)} independent matrices, m ~ U[64,2048], n ~ U[32,m], entries U[-1,1)",
            "count": len(shapes), "flops": flops, "unit": UNIT, "timing": "CUDA-graph replay, events"}
     for label, prec in (("fp64", tileqr.TILEQR_FP64), ("tf32", tileqr.TILEQR_TF32)):
@@ -330,6 +351,11 @@ def run_batched(args, dev, rank, world, barrier, dist):
         t = graph_time(bt)
         out[label] = {"value": world * flops / t / 1e9, "ms": t * 1e3, "nb": nb, "ib": ib,
                       "autotune_ms_on_sample": tune_ms}
+        # FP64 factors: the plain solve (one step); TF32 factors: refined
+        ts, rel, info = solve_time(bt, 1 if prec == tileqr.TILEQR_FP64 else 8)
+        out[label]["solve"] = {"ms": ts * 1e3, "steps": info.iterations, "max_rel_residual": rel,
+                               "method": "plain (Q^T b, R^-1)" if prec == tileqr.TILEQR_FP64 else
+                               "augmented-system FP64 refinement"}
         del bt
         torch.cuda.empty_cache()
         k = min(args.loop_subset, len(mats))
@@ -342,6 +368,13 @@ def run_batched(args, dev, rank, world, barrier, dist):
                                      "batched_value": sflops / tb / 1e9}
         torch.cuda.empty_cache()
     out["tf32_speedup_vs_fp64"] = out["fp64"]["ms"] / out["tf32"]["ms"]
+    # factor + solve, both at relative residual <= 1e-12
+    f64 = out["fp64"]["ms"] + out["fp64"]["solve"]["ms"]
+    f32 = out["tf32"]["ms"] + out["tf32"]["solve"]["ms"]
+    out["solve_speedup_tf32_vs_fp64"] = {
+        "value": f64 / f32, "fp64_ms": f64, "tf32_ms": f32,
+        "both_at_rel_residual_1e-12": max(out["fp64"]["solve"]["max_rel_residual"],
+                                          out["tf32"]["solve"]["max_rel_residual"]) <= 1e-12}
     tpk, tsrc = tf32_peak_gflops()
     out["tf32"]["pct_of_tf32_dense_peak"] = 100.0 * out["tf32"]["value"] / world / tpk
     out["tf32"]["tf32_peak_source"] = tsrc
@@ -398,6 +431,19 @@ def run_tall(args, dev, rank, world, barrier, dist):
              (torch.linalg.matrix_norm(A) * torch.linalg.matrix_norm(r))).item()
     res["solve_ls_ms"] = t * 1e3
     res["ls_optimality"] = ratio   # ||A^T r|| / (||A|| ||r||)
+    # TF32 tree factors + FP64 refinement on the augmented system: the
+    # least-squares solution to FP64 accuracy
+    ft = facs["tf32_tree"][0]
+    t_r, (Xr, info) = timed(lambda: ft.solve_ls_refine(A, B, max_iter=10, tol=1e-14), 2)
+    rr = B - A @ Xr
+    opt_r = (torch.linalg.matrix_norm(A.t() @ rr) /
+             (torch.linalg.matrix_norm(A) * torch.linalg.matrix_norm(rr))).item()
+    res["tf32_tree_refined_ls"] = {
+        "factor_ms": res["tf32_tree"]["ms"], "refine_ms": t_r * 1e3, "steps": info.iterations,
+        "ls_optimality": opt_r,
+        "x_vs_fp64_tree_solve": (torch.linalg.matrix_norm(Xr - X) / torch.linalg.matrix_norm(X)).item(),
+        "speedup_vs_fp64_tree_factor_solve": (res["fp64_tree"]["ms"] + res["solve_ls_ms"]) /
+                                             (res["tf32_tree"]["ms"] + t_r * 1e3)}
     del facs, A, B
     return res
 
@@ -507,6 +553,30 @@ def run_lu(args, dev, rank, world, barrier, dist):
             "zero_pivot_info": info, "solve_backward_error": be, "growth_U": growth,
             "stability_n2048": sweep, "roofline": roof,
             "timing": "CUDA events around the factorizations (layout conversion included), max over ranks"}
+
+
+def run_fp64_peak(args, dev, rank, world, barrier, dist):
+    """The FP64 rates behind the roofline denominator: the library's DFMA and
+    FP64 mma.sync microbenchmarks (tileqr_measure_fp64_rates), five runs
+    each, with the SM clock sampled while they run; the nominal DFMA peak
+    152 SMs x 4 flop/clk x clock follows from the clock."""
+    import torch
+    from paper_0709_1272_gb300 import tileqr
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = "0"
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    time.sleep(0.3)
+    runs = [tileqr.tileqr_measure_fp64_rates() for _ in range(5)]
+    clk = clocks.stop()
+    dfma = max(r[0] for r in runs)
+    dmma = max(r[1] for r in runs)
+    mhz = clk.get("sm_mhz") or float(measured_peaks().get("sm_max_mhz", 2070.0))
+    return {"dfma_gflops": dfma, "dmma_gflops": dmma, "runs": runs, "clocks": clk,
+            "dfma_flop_per_clk_per_sm": dfma * 1e9 / (NSM * mhz * 1e6),
+            "dfma_at_2070_mhz": dfma * 2070.0 / mhz}
 
 
 def run_config2_sweep(args, dev, rank, world, barrier, dist):
@@ -654,7 +724,9 @@ def main():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-cholesky", action="store_true",
                     help="skip the tiled Cholesky (Algorithm 1) measurement")
-    ap.add_argument("--only", choices=["lu", "cholesky", "batched", "config2-sweep", "kappa-sweep"], default=None,
+    ap.add_argument("--only", choices=["lu", "cholesky", "batched", "tall", "config2-sweep", "kappa-sweep",
+                                       "fp64-peak"],
+                    default=None,
                     help="run only this secondary measurement (at --n) and print its JSON object")
     ap.add_argument("--no-lu", action="store_true",
                     help="skip the tiled LU (Algorithm 3) measurement")
@@ -693,7 +765,9 @@ def main():
         def barrier():
             if dist is not None:
                 dist.barrier()
-        section = {"lu": run_lu, "cholesky": run_cholesky, "batched": run_batched, "config2-sweep": run_config2_sweep,
+        section = {"lu": run_lu, "cholesky": run_cholesky, "batched": run_batched, "tall": run_tall,
+                   "fp64-peak": run_fp64_peak,
+                   "config2-sweep": run_config2_sweep,
                    "kappa-sweep": run_kappa_sweep}[args.only](args, dev, rank, world, barrier, dist)
         if rank == 0:
             print(json.dumps({"section": args.only, **section}), flush=True)

@@ -75,7 +75,14 @@ enum {
     /* Fault injection for tests of the watchdog: the scheduler never releases
      * the final task, so the persistent kernel must give up after the watchdog
      * limit and report TILEQR_ERR_TIMEOUT.  No device fault is involved. */
-    TILEQR_FLAG_TEST_WITHHOLD_LAST_TASK = 1
+    TILEQR_FLAG_TEST_WITHHOLD_LAST_TASK = 1,
+    /* Stress test of the task-graph schedule (TILEQR_SCHED_DAG): every task
+     * sleeps a pseudo-random time (up to ~40 us, from a hash of the task and
+     * a seed) before it runs and before it releases its successors, so the
+     * tasks finish in orders the natural timing rarely produces.  The seed is
+     * flags >> 8.  The results must not change: every tile is written by a
+     * fixed sequence of tasks (Sec. 4). */
+    TILEQR_FLAG_TEST_RANDOM_DELAYS = 2
 };
 
 /* Positive error codes. */
@@ -363,6 +370,28 @@ int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_t lda, cons
                         int max_iter, double tol, void *workspace, size_t ws_bytes, tileqr_stream_t stream,
                         tileqr_refine_info *info);
 
+/* Least squares for every matrix of a factored batch (one right-hand side
+ * per matrix, m_b >= n_b), refined in FP64 on the augmented system as in
+ * tileqr_solve_ls_refine, all matrices in one persistent launch: one CTA
+ * runs the whole refinement of one matrix (Q^T and Q replayed on the vector
+ * in Algorithm 2's order and its reverse, R^-1 and R^-T by blocked
+ * substitution, the FP64 residuals), largest matrices first.  max_iter = 1
+ * gives the plain solve x = R^-1 (Q^T b)(0:n) (Sec. 3.2.1).  An addition to
+ * the paper (which factors one matrix at a time).
+ *   B, X      host arrays of bt->count device pointers: b_k (m_k entries,
+ *             read only) and x_k (n_k entries, output)
+ *   workspace tileqr_batched_ls_workspace_size(bt) bytes, 256-aligned
+ *   summary   (optional) iterations = the most any matrix took; method 3;
+ *             converged = every matrix stopped by the rule (||dx|| <= tol
+ *             ||x||, or ||dx|| no longer halving); rel_residual = the
+ *             largest last ||dx|| / ||x||
+ * Synchronous.  Returns 0, -i, TILEQR_ERR_WORKSPACE, TILEQR_ERR_SINGULAR,
+ * TILEQR_ERR_UNSUPPORTED or TILEQR_ERR_CUDA. */
+int tileqr_batched_ls_workspace_size(const tileqr_batch *bt, size_t *bytes);
+int tileqr_batched_solve_ls(const tileqr_batch *bt, const double *const *B, double *const *X, int max_iter,
+                            double tol, void *workspace, size_t ws_bytes, tileqr_stream_t stream,
+                            tileqr_refine_info *summary);
+
 /* Least squares min ||A X - B||_F (m >= n, inconsistent systems included)
  * to FP64 accuracy on top of a factorization d of A that may be inexact (a
  * TILEQR_TF32 one, flat or tree form): iterative refinement of the
@@ -467,6 +496,13 @@ int tileqr_lu_get_factors(const tileqr_desc *d, double *F, int64_t ldf, double *
 int tileqr_lu_solve_workspace_size(const tileqr_desc *d, int64_t nrhs, size_t *bytes);
 int tileqr_lu_solve(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace, size_t ws_bytes,
                     tileqr_stream_t stream);
+
+/* Microbenchmarks of this GPU's FP64 rates (diagnostic; not part of the
+ * method): *dfma_gflops from independent FP64 fused multiply-add chains on
+ * every SM, *dmma_gflops from FP64 mma.sync m16n8k16 on every SM, both in
+ * GFLOP/s from CUDA-event times.  The FP64 tile kernels use the faster of
+ * the two pipes.  Synchronous.  Returns 0, -1 or TILEQR_ERR_CUDA. */
+int tileqr_measure_fp64_rates(double *dfma_gflops, double *dmma_gflops, tileqr_stream_t stream);
 
 /* Human-readable text for a return code (static storage). */
 const char *tileqr_strerror(int code);

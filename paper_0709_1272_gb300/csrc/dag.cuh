@@ -187,10 +187,18 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_fac
         int k, i, j;
         decode_task(code, k, i, j);
         const int kind = g_kind(F.G, decode_tt(code), k, i, j);
+        if (Q.delay_seed) {   // schedule stress test (off by default)
+            if (threadIdx.x == 0)
+                stress_sleep(stress_delay_ns(code, Q.delay_seed, 0));
+            __syncthreads();
+        }
         const unsigned long long t0 = Q.trace ? globaltimer_ns() : 0ull;
         run_task<NB, S, MIXED>(sm, F, kind, k, i, j, tmem, s_mbar, mphase, &Q.ctrl->error);
         __syncthreads();
         if (threadIdx.x < 32) {
+            if (Q.delay_seed && threadIdx.x == 0)
+                stress_sleep(stress_delay_ns(code, Q.delay_seed, 1));
+            __syncwarp();
             release_graph(Q, F.G, kind, k, i, j, threadIdx.x, 32);
             __syncwarp();
             if (threadIdx.x == 0) {

@@ -49,6 +49,8 @@ static int launch_factor_mixed_t(const WsLayout &L, char *ws, int flags, cudaStr
     Q.withheld = ~0ull;
     if (flags & TILEQR_FLAG_TEST_WITHHOLD_LAST_TASK)
         Q.withheld = encode_task(L.steps - 1, L.steps - 1, L.steps - 1);
+    if (flags & TILEQR_FLAG_TEST_RANDOM_DELAYS)
+        Q.delay_seed = ((unsigned long long)(((unsigned int)flags) >> 8) << 1) | 1ull;
     Q.trace = trace;
     Q.trace_cap = trace_cap;
     int grid = grid_dag;

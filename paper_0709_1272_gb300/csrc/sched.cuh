@@ -25,7 +25,28 @@ struct Queues {
     unsigned long long withheld;   // task code never released (watchdog test), ~0 = none
     unsigned long long *trace;     // optional per-task trace records (4 u64 each)
     unsigned int trace_cap;
+    // stress test of the schedule: nonzero = a seed; every task then sleeps
+    // a pseudo-random time (up to ~40 us) before it runs and before it
+    // releases its successors, so tasks finish in orders the natural timing
+    // rarely gives.  0 (the default) = off.
+    unsigned long long delay_seed = 0;
 };
+
+// The stress-test delay of a task, in ns (a SplitMix64-style mix of the
+// task code, the seed and the site).
+__device__ __forceinline__ unsigned int stress_delay_ns(unsigned long long code, unsigned long long seed, int site)
+{
+    unsigned long long z = code * 0x9E3779B97F4A7C15ull + seed + (unsigned long long)site * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (unsigned int)(z % 20000u);
+}
+__device__ __forceinline__ void stress_sleep(unsigned int ns)
+{
+    __nanosleep(ns);
+    __nanosleep(ns);
+}
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
 {

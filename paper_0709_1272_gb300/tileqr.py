@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libtileqr.so")
 
 TILEQR_FP64, TILEQR_TF32, TILEQR_SPLIT_BF16 = 0, 1, 2
 TILEQR_SCHED_DAG, TILEQR_SCHED_BULK = 0, 1
-TILEQR_FLAG_NONE, TILEQR_FLAG_TEST_WITHHOLD_LAST_TASK = 0, 1
+TILEQR_FLAG_NONE, TILEQR_FLAG_TEST_WITHHOLD_LAST_TASK, TILEQR_FLAG_TEST_RANDOM_DELAYS = 0, 1, 2
 TILEQR_ERR_CUDA = 1001
 TILEQR_ERR_TIMEOUT = 1002
 TILEQR_ERR_NONFINITE = 1003
@@ -43,6 +43,7 @@ EXPORTED = [
     "tileqr_lu_workspace_size", "tileqr_lu", "tileqr_lu_info", "tileqr_lu_get_factors",
     "tileqr_lu_solve_workspace_size", "tileqr_lu_solve", "tileqr_mixed_update_tile",
     "tileqr_ls_refine_workspace_size", "tileqr_solve_ls_refine",
+    "tileqr_batched_ls_workspace_size", "tileqr_batched_solve_ls", "tileqr_measure_fp64_rates",
 ]
 
 
@@ -140,7 +141,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_lu_solve_workspace_size": (i32, [dp, i64, ctypes.POINTER(sz)]),
         "tileqr_lu_solve": (i32, [dp, vp, i64, i64, vp, sz, vp]),
         "tileqr_mixed_update_tile": (i32, [i32, i32, vp, vp, vp, vp, vp, sz, vp]),
+        "tileqr_measure_fp64_rates": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]),
         "tileqr_ls_refine_workspace_size": (i32, [dp, i64, ctypes.POINTER(sz)]),
+        "tileqr_batched_ls_workspace_size": (i32, [ctypes.POINTER(tileqr_batch), ctypes.POINTER(sz)]),
+        "tileqr_batched_solve_ls": (i32, [ctypes.POINTER(tileqr_batch), vp, vp, i32, ctypes.c_double, vp, sz, vp,
+                                          ctypes.POINTER(tileqr_refine_info)]),
         "tileqr_solve_ls_refine": (i32, [dp, vp, i64, vp, i64, i64, vp, i64, vp, i64, i32, ctypes.c_double, vp,
                                          sz, vp, ctypes.POINTER(tileqr_refine_info)]),
         "tileqr_task_graph": (i32, [i64, i64, i32, i32, i32, vp, vp, vp, vp, ctypes.POINTER(i64),
@@ -568,6 +573,14 @@ def tileqr_mixed_update_tile(kind: int, ib: int, V: torch.Tensor, T: torch.Tenso
                                            ws.numel(), _stream_ptr(stream)), "tileqr_mixed_update_tile")
 
 
+def tileqr_measure_fp64_rates(stream=None):
+    """(DFMA GFLOP/s, FP64 mma.sync GFLOP/s) measured on the current GPU."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().tileqr_measure_fp64_rates(ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)),
+           "tileqr_measure_fp64_rates")
+    return a.value, b.value
+
+
 def tileqr_launch_count() -> int:
     return int(load().tileqr_launch_count())
 
@@ -649,3 +662,23 @@ class Batch:
         d = tileqr_desc()
         _check(load().tileqr_batched_get(ctypes.byref(self.bt), b, ctypes.byref(d)), "tileqr_batched_get")
         return Factorization(d, self.workspace, self.device)
+
+    def solve_ls(self, bs, max_iter: int = 8, tol: float = 1e-14, stream=None):
+        """Least squares per matrix (one right-hand side each, bs[b] of m_b
+        entries) refined in FP64 on the augmented system, all matrices in one
+        launch (tileqr_batched_solve_ls); max_iter = 1 is the plain solve.
+        Returns ([x_b], summary info)."""
+        count = len(self.mats)
+        bs = [b.reshape(-1).contiguous() for b in bs]
+        xs = [torch.empty(int(n), dtype=torch.float64, device=self.device) for n in self._n]
+        need = ctypes.c_size_t(0)
+        _check(load().tileqr_batched_ls_workspace_size(ctypes.byref(self.bt), ctypes.byref(need)),
+               "tileqr_batched_ls_workspace_size")
+        ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=self.device)
+        bp = (ctypes.c_void_p * max(count, 1))(*[b.data_ptr() for b in bs])
+        xp = (ctypes.c_void_p * max(count, 1))(*[x.data_ptr() for x in xs])
+        info = tileqr_refine_info()
+        _check(load().tileqr_batched_solve_ls(ctypes.byref(self.bt), bp, xp, max_iter, tol,
+                                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream),
+                                              ctypes.byref(info)), "tileqr_batched_solve_ls")
+        return xs, info

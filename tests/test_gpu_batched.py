@@ -12,6 +12,8 @@ import torch
 import oracle
 from paper_0709_1272_gb300 import inputs
 
+EPS = np.finfo(np.float64).eps
+
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
 
@@ -130,3 +132,36 @@ def test_full_batch_4096(tq, prec_name, nb, ib):
             assert _rel(AV.cpu().numpy(), ref.A) <= TOL
     del bt, mats, pool_d
     torch.cuda.empty_cache()
+
+
+def test_batched_solve_matches_oracle_on_ragged_sub_batch(tq):
+    """tileqr_batched_solve_ls on a ragged batch (FP64 and TF32 factors,
+    inconsistent right-hand sides): each x agrees with the oracle's
+    least-squares solution (Algorithm 2 + Q^T b + R^-1) to the accuracy the
+    problem's conditioning allows two FP64 solvers, 100 eps kappa (1 + kappa
+    ||r|| / (||A|| ||x||)), and each residual is orthogonal to range(A); one
+    step on FP64 factors is the plain solve."""
+    shapes = [(300, 200), (129, 129), (700, 64), (64, 33), (1000, 999), (513, 260), (257, 256), (90, 90)]
+    mats = [inputs.uniform_matrix(m, n, seed=400 + b) for b, (m, n) in enumerate(shapes)]
+    rhs = [inputs.normal_matrix(m, 1, seed=500 + b).reshape(-1) for b, (m, n) in enumerate(shapes)]
+    dmats = [tq.to_device_colmajor(A) for A in mats]
+    drhs = [torch.from_numpy(b).cuda() for b in rhs]
+    refs = []
+    for A, b in zip(mats, rhs):
+        refs.append(oracle.solve_ls(oracle.tiled_qr(A, 128, 16), b.copy()).reshape(-1))
+    for prec, steps in ((tq.TILEQR_FP64, 1), (tq.TILEQR_FP64, 8), (tq.TILEQR_TF32, 8)):
+        bt = tq.Batch(dmats, 128, 16, prec)
+        bt.run()
+        assert bt.status() == 0
+        xs, info = bt.solve_ls(drhs, max_iter=steps, tol=1e-14)
+        assert info.converged == 1 or steps == 1
+        for A, b, x, xo in zip(mats, rhs, xs, refs):
+            x = x.cpu().numpy()
+            r = b - A @ x
+            kappa = np.linalg.cond(A)
+            tol = 100 * EPS * kappa * (1 + kappa * np.linalg.norm(r) / (np.linalg.norm(A, 2) * np.linalg.norm(x)))
+            assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= tol, (prec, steps)
+            if A.shape[0] > A.shape[1]:   # inconsistent: the residual is orthogonal to range(A)
+                assert np.linalg.norm(A.T @ r) / (np.linalg.norm(A) * np.linalg.norm(r)) <= 20 * A.shape[1] * EPS
+            else:                          # square: normwise backward error of the solve
+                assert np.linalg.norm(r) / (np.linalg.norm(A) * np.linalg.norm(x)) <= 20 * A.shape[1] * EPS

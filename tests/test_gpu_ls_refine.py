@@ -74,7 +74,9 @@ def test_refined_ls_on_fp64_factors_stops_at_once(tq):
     X, info = f.solve_ls_refine(Ad, Bd, max_iter=10, tol=1e-14)
     assert info.converged == 1 and info.iterations <= 3
     Xo = oracle.solve_ls(oracle.tiled_qr(A, 64, 16), B.copy())
-    assert np.linalg.norm(X.cpu().numpy() - Xo) / np.linalg.norm(Xo) <= 1e-12
+    # two FP64 least-squares solutions differ by up to ~eps kappa^2 ||r|| /
+    # (||A|| ||x||) ~ 1e-10 here (kappa 1e3, residual as large as A x)
+    assert np.linalg.norm(X.cpu().numpy() - Xo) / np.linalg.norm(Xo) <= 1e-9
 
 
 def test_refined_ls_consistent_system(tq):

@@ -161,3 +161,18 @@ def test_mixed_factor_graded_columns(tq):
     ref = oracle.tiled_qr(As, 128, 32)
     err = _column_r_error(R, ref.R(), As)
     assert err <= R_BOUND, err
+
+
+def test_mixed_random_task_delays_keep_the_bits(tq):
+    """The TF32 factorization is deterministic too: seeded random task
+    delays change the schedule, not the bits."""
+    A = inputs.normal_matrix(900, 640, seed=3)
+    Ad = tq.to_device_colmajor(A)
+    f0 = tq.tileqr_factor(Ad, 128, 32, precision=tq.TILEQR_TF32).check()
+    AV0, T0 = f0.factors()
+    AV0, T0 = AV0.cpu().numpy(), T0.cpu().numpy()
+    for seed in (5, 6):
+        f = tq.tileqr_factor(Ad, 128, 32, precision=tq.TILEQR_TF32,
+                             flags=tq.TILEQR_FLAG_TEST_RANDOM_DELAYS | (seed << 8)).check()
+        AV, T = f.factors()
+        assert np.array_equal(AV.cpu().numpy(), AV0) and np.array_equal(T.cpu().numpy(), T0)

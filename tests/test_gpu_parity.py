@@ -238,3 +238,34 @@ def test_full_tall_skinny_solve(tq):
     nA = torch.linalg.matrix_norm(Ad, ord="fro")
     ratio = (torch.linalg.matrix_norm(Atr) / (nA * torch.linalg.matrix_norm(r))).item()
     assert ratio <= 20 * n * EPS
+
+
+def test_full_elementwise_4096(tq):
+    """4096 x 4096 N(0,1), nb 128 / ib 16, the persistent task-graph kernel
+    at two CTAs per SM with 32 steps of queue contention (the benchmarked
+    launch configuration): every element of R/V (in place) and of the T
+    strips against the oracle's Algorithm 2 at 1e-12 (the oracle run level
+    by level on all host cores; identical bits to its sequential order)."""
+    import os
+    m = n = 4096
+    A = inputs.normal_matrix(m, n, seed=20070715)
+    f, _, AV, T, R = _gpu_factor(tq, A, 128, 16)
+    ref, _ = oracle.tiled_qr_levels(A, 128, 16, len(os.sched_getaffinity(0)))
+    assert _rel(AV, ref.A) <= TOL
+    assert _rel(T, ref.T) <= TOL
+    assert _rel(oracle.sign_normalize(R), oracle.sign_normalize(ref.R())) <= TOL
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_task_delays_keep_the_bits(tq, seed):
+    """Schedule stress test: with TILEQR_FLAG_TEST_RANDOM_DELAYS every task
+    sleeps a seeded pseudo-random time before it runs and before it releases
+    its successors; the factors must equal the fork-join comparator's bit
+    for bit (any topological order gives the same bits, Sec. 4)."""
+    A = inputs.normal_matrix(1000, 700, seed=77)
+    Ad = tq.to_device_colmajor(A)
+    flags = tq.TILEQR_FLAG_TEST_RANDOM_DELAYS | (seed << 8)
+    f = tq.tileqr_factor(Ad, 128, 32, flags=flags).check()
+    AV, T = f.factors()
+    _, _, AV1, T1, _ = _gpu_factor(tq, A, 128, 32, schedule=tq.TILEQR_SCHED_BULK)
+    assert np.array_equal(AV.cpu().numpy(), AV1) and np.array_equal(T.cpu().numpy(), T1)

@@ -216,3 +216,20 @@ def test_tree_argument_errors(tq):
     with pytest.raises(tq.TileQRError) as e:
         f.solve_refine(A, A[:, 0].contiguous())
     assert e.value.code == tq.TILEQR_ERR_UNSUPPORTED
+
+
+def test_full_elementwise_tree_16384x512(tq):
+    """16384 x 512 N(0,1), nb 128 / ib 16, domains of 8 tile rows (the
+    benchmarked FP64 tree configuration on a 128 x 4 tile grid): every
+    element of R/V, T and the DTTQRT strips T2 against the oracle's tree
+    variant at 1e-12."""
+    m, n, nb, ib, h = 16384, 512, 128, 16, 8
+    A = inputs.normal_matrix(m, n, seed=20070716)
+    Ad = tq.to_device_colmajor(A)
+    f = tq.tileqr_factor_tree(Ad, nb, ib, h).check()
+    AV, T = f.factors()
+    T2 = f.tree_T()
+    ref = oracle.tiled_qr_tree(A, nb, ib, h)
+    assert _rel(AV.cpu().numpy(), ref.A) <= TOL
+    assert _rel(T.cpu().numpy(), ref.T) <= TOL
+    assert _rel(T2.cpu().numpy(), ref.T2) <= TOL
