@@ -237,7 +237,7 @@ int tileqr_factor_noalloc(int64_t m, int64_t n, const double *A, int64_t lda, in
  * Synchronous.  Returns 0, -i, TILEQR_ERR_UNSUPPORTED, TILEQR_ERR_WORKSPACE,
  * TILEQR_ERR_TIMEOUT (a tensor-core wait gave up) or TILEQR_ERR_CUDA. */
 enum { TILEQR_UPDATE_LARFB = 0, TILEQR_UPDATE_SSRFB = 1 };
-#define TILEQR_MIXED_UPDATE_WS_BYTES (132u * 1024u)
+#define TILEQR_MIXED_UPDATE_WS_BYTES (388u * 1024u)
 int tileqr_mixed_update_tile(int kind, int ib, const double *V, const double *T, double *B, double *C,
                              void *workspace, size_t ws_bytes, tileqr_stream_t stream);
 

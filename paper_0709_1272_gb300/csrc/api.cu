@@ -53,8 +53,8 @@ WsLayout make_layout(int64_t m, int64_t n, int nb, int ib, int h, int precision)
     L.off_tiles = 0;
     L.off_T = align256(tiles);
     L.off_T2 = L.off_T + align256(tst);
-    // pre-split T^T operands: 128 x 128 tf32 hi + lo per tile pair (128 KB)
-    const size_t tfb = (precision == TILEQR_TF32 && nb == 128) ? tf_pairs(L.p, L.steps) * TF_BYTES : 0;
+    // pre-split T^T, V^T and V operands: 3 x 128 x 128 tf32 hi + lo per tile pair (384 KB)
+    const size_t tfb = (precision == TILEQR_TF32 && nb == 128) ? tf_pairs(L.p, L.steps) * TF_PAIR_BYTES : 0;
     L.off_TF = L.off_T2 + (tree ? align256(tst) : 0);
     L.off_TF2 = L.off_TF + align256(tfb);
     L.off_ctrl = L.off_TF2 + (tree ? align256(tfb) : 0);

@@ -95,7 +95,7 @@ BatchLayout batch_layout(int count, const int64_t *m, const int64_t *n, int nb, 
         data += align256((size_t)mi.p * mi.q * ib * nb * sizeof(double));
         if (precision == TILEQR_TF32 && mi.steps > 0) {
             mi.TF = (unsigned char *)(uintptr_t)data;
-            data += align256(tf_pairs(mi.p, mi.steps) * TF_BYTES);
+            data += align256(tf_pairs(mi.p, mi.steps) * TF_PAIR_BYTES);
             // column exponents: offset (in ints) into the cleared cexp region
             mi.cexp = (int *)(uintptr_t)ncols;
             ncols += (size_t)n[b];

@@ -16,7 +16,7 @@ struct FactorArgs {
     double *T;
     double *T2;   // DTTQRT T strips (tree form only)
     // mixed precision: the panels' full T^T as pre-split tf32 operands
-    // (TF_BYTES per tile pair; TF2 for DTTQRT); unused in FP64
+    // (TF_PAIR_BYTES per tile pair; TF2 for DTTQRT); unused in FP64
     unsigned char *TF, *TF2;
     // mixed precision: the largest biased exponent of every matrix column
     // and ceil(log2 sqrt(m)), for the column scaling of the FP32 operands
@@ -52,7 +52,7 @@ __device__ __forceinline__ const int *cexp_ptr(const FactorArgs &F, int j)
 
 __device__ __forceinline__ unsigned char *tf_ptr(unsigned char *base, int p, int i, int k)
 {
-    return base + tf_index(p, i, k) * (size_t)TF_BYTES;
+    return base + tf_index(p, i, k) * TF_PAIR_BYTES;
 }
 
 // Run the tile kernel of one task.  DTSQRT / DSSRFB eliminate row i into the
@@ -148,14 +148,14 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM)) k_fac
     __shared__ unsigned long long s_code;
     __shared__ int s_cmd;
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ __align__(8) uint64_t s_mbar[4];   // MMA commits (0, 1), operand copies (2, 3)
     uint32_t tmem = 0, mphase = 0;
     if (MIXED) {
         // one tensor-memory allocation and one mbarrier per persistent CTA
         if ((threadIdx.x >> 5) == 0)
             tc::tmem_alloc(&s_tmem, MIX_TMEM_COLS);
         if (threadIdx.x == 0)
-            for (int b = 0; b < 2; b++)
+            for (int b = 0; b < 4; b++)
                 tc::mbar_init(&s_mbar[b], 1);
         tc::fence_before_sync();
         __syncthreads();
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
     __shared__ unsigned long long s_code;
     __shared__ int s_cmd;
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ __align__(8) uint64_t s_mbar[4];   // MMA commits (0, 1), operand copies (2, 3)
     __shared__ FactorArgs s_F;
     __shared__ size_t s_cnt;
     uint32_t tmem = 0, mphase = 0;
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
         if ((threadIdx.x >> 5) == 0)
             tc::tmem_alloc(&s_tmem, MIX_TMEM_COLS);
         if (threadIdx.x == 0)
-            for (int b = 0; b < 2; b++)
+            for (int b = 0; b < 4; b++)
                 tc::mbar_init(&s_mbar[b], 1);
         tc::fence_before_sync();
         __syncthreads();

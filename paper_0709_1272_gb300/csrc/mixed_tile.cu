@@ -32,12 +32,12 @@ __global__ void __launch_bounds__(NT, 1) k_mixed_update_one(const double *V, con
 {
     extern __shared__ double sm[];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ __align__(8) uint64_t s_mbar[4];
     unsigned char *smb = (unsigned char *)sm;
     if ((threadIdx.x >> 5) == 0)
         tc::tmem_alloc(&s_tmem, MIX_TMEM_COLS);
     if (threadIdx.x == 0)
-        for (int b = 0; b < 2; b++)
+        for (int b = 0; b < 4; b++)
             tc::mbar_init(&s_mbar[b], 1);
     tc::fence_before_sync();
     __syncthreads();
@@ -62,7 +62,7 @@ static int launch_mixed_update_one(const double *V, const double *T, double *B, 
     if (rc)
         return rc;
     unsigned char *TF = (unsigned char *)ws;
-    int *cexp = (int *)(ws + TF_BYTES);
+    int *cexp = (int *)(ws + TF_PAIR_BYTES);
     int *err = cexp + 128;
     if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
@@ -100,7 +100,7 @@ extern "C" int tileqr_mixed_update_tile(int kind, int ib, const double *V, const
         return -6;
     if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < TILEQR_MIXED_UPDATE_WS_BYTES)
         return TILEQR_ERR_WORKSPACE;
-    static_assert(TF_BYTES + 129 * sizeof(int) <= TILEQR_MIXED_UPDATE_WS_BYTES, "workspace of one update");
+    static_assert(TF_PAIR_BYTES + 129 * sizeof(int) <= TILEQR_MIXED_UPDATE_WS_BYTES, "workspace of one update");
     cudaStream_t st = (cudaStream_t)stream;
     char *ws = (char *)workspace;
     if (kind == TILEQR_UPDATE_LARFB)

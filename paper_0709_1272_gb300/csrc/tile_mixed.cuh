@@ -74,27 +74,6 @@ __device__ __forceinline__ double mixed_v_elem(const double *Vt, int trow, int t
     return ldcg(Vt + (size_t)tcol * 128 + trow);
 }
 
-// Four consecutive entries V(trow..trow+3, tcol) of a reflector tile (trow a
-// multiple of 4), read as two 16-byte loads and masked like mixed_v_elem.
-template <int VK>
-__device__ __forceinline__ void mixed_v_elem4(const double *Vt, int trow, int tcol, double (&v)[4])
-{
-    const double2 *p = (const double2 *)(Vt + (size_t)tcol * 128 + trow);
-    const double2 a = __ldcg(p), b = __ldcg(p + 1);
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = b.x;
-    v[3] = b.y;
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-        const int r = trow + e;
-        if (VK == VK_UNIT)
-            v[e] = (r < tcol) ? 0.0 : (r == tcol ? 1.0 : v[e]);
-        if (VK == VK_UPPER && r > tcol)
-            v[e] = 0.0;
-    }
-}
-
 // Split four FP32 values (consecutive K of one operand row) and store them
 // as one 16-byte vector in each of the hi and lo operand buffers.
 __device__ __forceinline__ void store_split4(unsigned char *sm, int off_hi, int off_lo, uint32_t byte_off,
@@ -150,6 +129,13 @@ __device__ __forceinline__ bool mixed_wait(uint64_t *mbar, uint32_t &phase, int 
 // orthogonal).
 constexpr int TF_CHUNK_BYTES = 2 * 128 * 32 * 4;
 constexpr int TF_BYTES = 4 * TF_CHUNK_BYTES;
+// Per tile pair the panel stores three pre-split operands of TF_BYTES each:
+// T^T (A operand of W = T^T Y), V^T (A operand of P = V^T C: row =
+// reflector, K = tile row) and V (A operand of D = V W: row = tile row, K =
+// reflector), so the update tasks copy them as they are, with the copy
+// engine, instead of converting V from FP64 twice per task.
+constexpr int TF_OFF_T = 0, TF_OFF_VT = TF_BYTES, TF_OFF_V = 2 * TF_BYTES;
+constexpr size_t TF_PAIR_BYTES = 3 * (size_t)TF_BYTES;
 // Operands are kept for the tile pairs (i, k), k < steps, i >= k only, in
 // step-major order: pair (i, k) is number k p - k (k - 1) / 2 + (i - k).
 __host__ __device__ inline size_t tf_pairs(int p, int steps)
@@ -314,9 +300,38 @@ __device__ __noinline__ void mixed_build_tfull(unsigned char *smb, const double 
         __stcg((float4 *)(TFg + off), h);
         __stcg((float4 *)(TFg + off + TF_CHUNK_BYTES / 2), l);
     }
+    // V^T (row = reflector a, K = tile rows r..r+3) and V (row = tile row r,
+    // K = reflectors a..a+3) from the staged FP32 reflectors, split
+    for (int u = tid; u < NB * (NB / 4); u += NT) {
+        const int a = u & (NB - 1), r = 4 * (u >> 7);
+        float4 h, l;
+        tc::split_tf32(Vs[(r + 0) * LD + a], h.x, l.x);
+        tc::split_tf32(Vs[(r + 1) * LD + a], h.y, l.y);
+        tc::split_tf32(Vs[(r + 2) * LD + a], h.z, l.z);
+        tc::split_tf32(Vs[(r + 3) * LD + a], h.w, l.w);
+        const uint32_t off = TF_OFF_VT + (r >> 5) * TF_CHUNK_BYTES + tc::kmajor_off(a, r & 31, 32);
+        __stcg((float4 *)(TFg + off), h);
+        __stcg((float4 *)(TFg + off + TF_CHUNK_BYTES / 2), l);
+    }
+    for (int u = tid; u < NB * (NB / 4); u += NT) {
+        const int r = u & (NB - 1), a = 4 * (u >> 7);
+        const float4 v = *(const float4 *)(Vs + r * LD + a);
+        float4 h, l;
+        tc::split_tf32(v.x, h.x, l.x);
+        tc::split_tf32(v.y, h.y, l.y);
+        tc::split_tf32(v.z, h.z, l.z);
+        tc::split_tf32(v.w, h.w, l.w);
+        const uint32_t off = TF_OFF_V + (a >> 5) * TF_CHUNK_BYTES + tc::kmajor_off(r, a & 31, 32);
+        __stcg((float4 *)(TFg + off), h);
+        __stcg((float4 *)(TFg + off + TF_CHUNK_BYTES / 2), l);
+    }
+    // the update tasks read these operands with the copy engine (async proxy)
+    tc::fence_async_all();
 }
 
-// The update with the panel's full T (pre-split by mixed_build_tfull):
+// The update with the panel's full T and reflectors (pre-split by
+// mixed_build_tfull; the copy engine brings their chunks into shared memory,
+// cp.async.bulk completing on mbar[2 + set]):
 //   P = V^T C;  W = T^T (B + P);  B -= W;  D = V W;  C -= D
 // three 128 x 128 x 128 3xTF32 products with FP32 accumulation in tensor
 // memory (P and D in columns 0..127, W in 128..255), each in 4 K-chunks of
@@ -359,6 +374,28 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
             tc::mma_tf32(d, al, bh, idesc, 1u);
         }
     };
+    // Copy-engine loads of the pre-split operand chunks into operand set b
+    // (mbar[2 + b]; thread 0 issues and waits, its phase bits 2 and 3).  A
+    // wait that gives up waits once more (bounded) so that no copy is left
+    // writing into shared memory after the task returns.
+    auto load_chunk = [&](unsigned char *dst, const unsigned char *src, int b) {
+        tc::mbar_expect_tx(&mbar[2 + b], TF_CHUNK_BYTES);
+        tc::bulk_g2s(dst, src, TF_CHUNK_BYTES, &mbar[2 + b]);
+    };
+    auto load_wait = [&](int b) {
+        const uint32_t par = (phase >> (2 + b)) & 1u;
+        bool r = tc::mbar_wait(&mbar[2 + b], par);
+        if (!r)
+            tc::mbar_wait(&mbar[2 + b], par);
+        phase ^= 1u << (2 + b);
+        return r;
+    };
+    // the copies need 16-byte aligned addresses: checked once per task
+    if (((sbase | (uint32_t)(uintptr_t)TFg) & 15u) != 0u) {
+        if (tid == 0)
+            atomicCAS(err, 0, TILEQR_ERR_CUDA);
+        return false;
+    }
     const int a_row = 32 * (warp & 3) + lane;   // this thread's tensor-memory lane
     const int cbase = (warp >> 2) * 64;
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
@@ -397,15 +434,19 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     // 32-row round at a time, and the later phases (B, T^T, the second reads
     // of V and C) find them in L2.
     if (tid == 0) {
-        tc::prefetch_l2(Vt, NB * NB * 8);
         tc::prefetch_l2(Ct, NB * NB * 8);
         if (Bt)
             tc::prefetch_l2(Bt, NB * NB * 8);
-        tc::prefetch_l2(TFg, TF_BYTES);
+        tc::prefetch_l2(TFg + TF_OFF_T, TF_BYTES);
+        tc::prefetch_l2(TFg + TF_OFF_V, TF_BYTES);
     }
     int *sh = (int *)(sm + TF_UPDATE_SMEM);   // column shifts of the updated tile column
     if (tid < NB)
         sh[tid] = cex ? col_shift(__ldg(cex + tid), lm) : 0;
+    // earlier generic writes to the operand areas (the last task, a panel)
+    // are ordered before this task's copy-engine writes, and the operands the
+    // panel task wrote to global memory before this task's copy-engine reads
+    tc::fence_async_all();
     __syncthreads();
     // ---- P = V^T C: A = V^T (row = reflector, K = tile row), B = C^T (row =
     // column); sets at 0 and 4 OPB
@@ -413,12 +454,13 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         const int b = rr & 1, r0 = rr * KC, so = b * 4 * OPB;
         if (rr >= 2)
             ok &= mixed_wait(mbar, phase, b);
-        double v[4][4], c[4][4];
+        if (tid == 0)   // V^T chunk rr into the set's A area
+            load_chunk(sm + so, TFg + TF_OFF_VT + (size_t)rr * TF_CHUNK_BYTES, b);
+        double c[4][4];
 #pragma unroll
         for (int x = 0; x < 4; x++) {
-            // four consecutive rows of column m of V and C: two 16-byte loads each
+            // four consecutive rows of column m of C: two 16-byte loads
             const int m = p_row(x), j = p_kgrp(x), r = r0 + 4 * j;
-            mixed_v_elem4<VK>(Vt, r, m, v[x]);
             const double2 *cp = (const double2 *)(Ct + (size_t)m * NB + r);
             const double2 c01 = __ldcg(cp), c23 = __ldcg(cp + 1);
             c[x][0] = c01.x;
@@ -429,13 +471,14 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
 #pragma unroll
         for (int x = 0; x < 4; x++) {
             const uint32_t off = tc::kmajor_off(p_row(x), 4 * p_kgrp(x), KC);
-            store_split4(sm, so, so + OPB, off, f64_to_f32_bits(v[x][0]), f64_to_f32_bits(v[x][1]),
-                         f64_to_f32_bits(v[x][2]), f64_to_f32_bits(v[x][3]));
             const int sc = sh[p_row(x)];
             store_split4(sm, so + 2 * OPB, so + 3 * OPB, off, f64_to_f32_sc(c[x][0], sc), f64_to_f32_sc(c[x][1], sc),
                          f64_to_f32_sc(c[x][2], sc), f64_to_f32_sc(c[x][3], sc));
         }
-        mixed_issue(&mbar[b], [&]() { mma_chunk(tmem, sbase + so, sbase + so + 2 * OPB, rr == 0); });
+        mixed_issue(&mbar[b], [&]() {
+            ok &= load_wait(b);
+            mma_chunk(tmem, sbase + so, sbase + so + 2 * OPB, rr == 0);
+        });
     }
     ok &= mixed_wait(mbar, phase, 0);
     ok &= mixed_wait(mbar, phase, 1);
@@ -456,18 +499,19 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
             v[j] += Bt ? f64_to_f32_sc(bv[j], sh[c0 + j]) : 0.0f;
         stage_bop(v, c0);
     }
+    tc::fence_async_smem();
     __syncthreads();   // every warp is done with its scratch in R2
-    // ---- W = T^T Y: A = T^T chunks copied from the panel's pre-split operand
+    // ---- W = T^T Y: A = T^T chunks, copied from the panel's pre-split operand
     for (int kk = 0; kk < NB / KC; kk++) {
         const int b = kk & 1;
         if (kk >= 2)
             ok &= mixed_wait(mbar, phase, b);
-        const float4 *src = (const float4 *)(TFg + (size_t)kk * TF_CHUNK_BYTES);
-        float4 *dst = (float4 *)(sm + R2 + b * 2 * OPB);
-        for (int e = tid; e < TF_CHUNK_BYTES / 16; e += NT)
-            dst[e] = __ldcg(src + e);
-        mixed_issue(&mbar[b],
-                    [&]() { mma_chunk(tmem + 128, sbase + R2 + b * 2 * OPB, sbase + kk * 2 * OPB, kk == 0); });
+        if (tid == 0)
+            load_chunk(sm + R2 + b * 2 * OPB, TFg + TF_OFF_T + (size_t)kk * TF_CHUNK_BYTES, b);
+        mixed_issue(&mbar[b], [&]() {
+            ok &= load_wait(b);
+            mma_chunk(tmem + 128, sbase + R2 + b * 2 * OPB, sbase + kk * 2 * OPB, kk == 0);
+        });
     }
     ok &= mixed_wait(mbar, phase, 0);
     ok &= mixed_wait(mbar, phase, 1);
@@ -490,27 +534,20 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         }
         stage_bop(w, c0);
     }
+    tc::fence_async_smem();
     __syncthreads();   // every warp is done with its scratch in R2
-    // ---- D = V W: A = V (row = tile row, K = reflector) chunks staged in R2
+    // ---- D = V W: A = V (row = tile row, K = reflector) chunks, copied from
+    // the panel's pre-split operand into R2
     for (int kk = 0; kk < NB / KC; kk++) {
-        const int b = kk & 1, k0 = kk * KC, ao = R2 + b * 2 * OPB;
+        const int b = kk & 1, ao = R2 + b * 2 * OPB;
         if (kk >= 2)
             ok &= mixed_wait(mbar, phase, b);
-        double v[4][4];
-#pragma unroll
-        for (int x = 0; x < 4; x++) {
-            const int u = tid + x * NT, r = u & (NB - 1), j = u >> 7, k = k0 + 4 * j;
-#pragma unroll
-            for (int e = 0; e < 4; e++)
-                v[x][e] = mixed_v_elem<VK>(Vt, r, k + e);
-        }
-#pragma unroll
-        for (int x = 0; x < 4; x++) {
-            const int u = tid + x * NT, r = u & (NB - 1), j = u >> 7;
-            store_split4(sm, ao, ao + OPB, tc::kmajor_off(r, 4 * j, KC), f64_to_f32_bits(v[x][0]),
-                         f64_to_f32_bits(v[x][1]), f64_to_f32_bits(v[x][2]), f64_to_f32_bits(v[x][3]));
-        }
-        mixed_issue(&mbar[b], [&]() { mma_chunk(tmem, sbase + ao, sbase + kk * 2 * OPB, kk == 0); });
+        if (tid == 0)
+            load_chunk(sm + ao, TFg + TF_OFF_V + (size_t)kk * TF_CHUNK_BYTES, b);
+        mixed_issue(&mbar[b], [&]() {
+            ok &= load_wait(b);
+            mma_chunk(tmem, sbase + ao, sbase + kk * 2 * OPB, kk == 0);
+        });
     }
     ok &= mixed_wait(mbar, phase, 0);
     ok &= mixed_wait(mbar, phase, 1);

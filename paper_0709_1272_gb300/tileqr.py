@@ -27,7 +27,7 @@ TILEQR_ERR_UNSUPPORTED = 1006
 TILEQR_ERR_SCRATCH_LIMIT = 1007
 TILEQR_ERR_NOT_SPD = 1008
 TILEQR_UPDATE_LARFB, TILEQR_UPDATE_SSRFB = 0, 1
-TILEQR_MIXED_UPDATE_WS_BYTES = 132 * 1024
+TILEQR_MIXED_UPDATE_WS_BYTES = 388 * 1024
 
 EXPORTED = [
     "tileqr_workspace_size", "tileqr_factor", "tileqr_status", "tileqr_get_R",
