@@ -390,6 +390,33 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         phase ^= 1u << (2 + b);
         return r;
     };
+    // A product whose A operands all come from the copy engine (T^T, V): the
+    // threads have nothing to stage, so thread 0 alone streams the four A
+    // chunks through the two buffers of R2 (copy of chunk kk + 2 as soon as
+    // the MMAs of chunk kk are done) and issues the MMAs; the B operand (R1)
+    // was staged and published by every thread before.  Each of mbar[0] and
+    // mbar[1] completes two phases here, which thread 0 waits in order; the
+    // other threads skip both and keep their parity bits, which two phases
+    // leave unchanged.  Returns thread 0's wait outcome.
+    auto stream_product = [&](uint32_t d, uint32_t toff) {
+        bool r = true;
+        if (tid == 0) {
+            tc::fence_after_sync();
+            for (int kk = 0; kk < 2; kk++)
+                load_chunk(sm + R2 + kk * 2 * OPB, TFg + toff + (size_t)kk * TF_CHUNK_BYTES, kk);
+            for (int kk = 0; kk < NB / KC; kk++) {
+                const int b = kk & 1;
+                r &= load_wait(b);
+                mma_chunk(d, sbase + R2 + b * 2 * OPB, sbase + kk * 2 * OPB, kk == 0);
+                tc::commit(&mbar[b]);
+                r &= mixed_wait(mbar, phase, b);
+                if (kk + 2 < NB / KC)
+                    load_chunk(sm + R2 + b * 2 * OPB, TFg + toff + (size_t)(kk + 2) * TF_CHUNK_BYTES, b);
+            }
+            tc::fence_before_sync();
+        }
+        return r;
+    };
     // the copies need 16-byte aligned addresses: checked once per task
     if (((sbase | (uint32_t)(uintptr_t)TFg) & 15u) != 0u) {
         if (tid == 0)
@@ -450,17 +477,13 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     __syncthreads();
     // ---- P = V^T C: A = V^T (row = reflector, K = tile row), B = C^T (row =
     // column); sets at 0 and 4 OPB
-    for (int rr = 0; rr < NB / KC; rr++) {
-        const int b = rr & 1, r0 = rr * KC, so = b * 4 * OPB;
-        if (rr >= 2)
-            ok &= mixed_wait(mbar, phase, b);
-        if (tid == 0)   // V^T chunk rr into the set's A area
-            load_chunk(sm + so, TFg + TF_OFF_VT + (size_t)rr * TF_CHUNK_BYTES, b);
-        double c[4][4];
+    // C rows of round rr: four consecutive rows of column m, two 16-byte
+    // loads per (m, row group); the next round's loads are issued before
+    // this round's conversion and barrier, so they are in flight meanwhile
+    auto load_c = [&](int rr, double (&c)[4][4]) {
 #pragma unroll
         for (int x = 0; x < 4; x++) {
-            // four consecutive rows of column m of C: two 16-byte loads
-            const int m = p_row(x), j = p_kgrp(x), r = r0 + 4 * j;
+            const int m = p_row(x), j = p_kgrp(x), r = rr * KC + 4 * j;
             const double2 *cp = (const double2 *)(Ct + (size_t)m * NB + r);
             const double2 c01 = __ldcg(cp), c23 = __ldcg(cp + 1);
             c[x][0] = c01.x;
@@ -468,17 +491,33 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
             c[x][2] = c23.x;
             c[x][3] = c23.y;
         }
+    };
+    double cc[4][4], cn[4][4];
+    load_c(0, cc);
+    for (int rr = 0; rr < NB / KC; rr++) {
+        const int b = rr & 1, so = b * 4 * OPB;
+        if (rr >= 2)
+            ok &= mixed_wait(mbar, phase, b);
+        if (tid == 0)   // V^T chunk rr into the set's A area
+            load_chunk(sm + so, TFg + TF_OFF_VT + (size_t)rr * TF_CHUNK_BYTES, b);
+        if (rr + 1 < NB / KC)
+            load_c(rr + 1, cn);
 #pragma unroll
         for (int x = 0; x < 4; x++) {
             const uint32_t off = tc::kmajor_off(p_row(x), 4 * p_kgrp(x), KC);
             const int sc = sh[p_row(x)];
-            store_split4(sm, so + 2 * OPB, so + 3 * OPB, off, f64_to_f32_sc(c[x][0], sc), f64_to_f32_sc(c[x][1], sc),
-                         f64_to_f32_sc(c[x][2], sc), f64_to_f32_sc(c[x][3], sc));
+            store_split4(sm, so + 2 * OPB, so + 3 * OPB, off, f64_to_f32_sc(cc[x][0], sc),
+                         f64_to_f32_sc(cc[x][1], sc), f64_to_f32_sc(cc[x][2], sc), f64_to_f32_sc(cc[x][3], sc));
         }
         mixed_issue(&mbar[b], [&]() {
             ok &= load_wait(b);
             mma_chunk(tmem, sbase + so, sbase + so + 2 * OPB, rr == 0);
         });
+#pragma unroll
+        for (int x = 0; x < 4; x++)
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                cc[x][e] = cn[x][e];
     }
     ok &= mixed_wait(mbar, phase, 0);
     ok &= mixed_wait(mbar, phase, 1);
@@ -502,21 +541,10 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     tc::fence_async_smem();
     __syncthreads();   // every warp is done with its scratch in R2
     // ---- W = T^T Y: A = T^T chunks, copied from the panel's pre-split operand
-    for (int kk = 0; kk < NB / KC; kk++) {
-        const int b = kk & 1;
-        if (kk >= 2)
-            ok &= mixed_wait(mbar, phase, b);
-        if (tid == 0)
-            load_chunk(sm + R2 + b * 2 * OPB, TFg + TF_OFF_T + (size_t)kk * TF_CHUNK_BYTES, b);
-        mixed_issue(&mbar[b], [&]() {
-            ok &= load_wait(b);
-            mma_chunk(tmem + 128, sbase + R2 + b * 2 * OPB, sbase + kk * 2 * OPB, kk == 0);
-        });
-    }
-    ok &= mixed_wait(mbar, phase, 0);
-    ok &= mixed_wait(mbar, phase, 1);
+    ok &= stream_product(tmem + 128, TF_OFF_T);
     if (!__syncthreads_and(ok))
         return fail();
+    tc::fence_after_sync();
 
     // ---- B -= W (FP64); W^T into R1 as the B operand of D = V W
     for (int h = 0; h < 2; h++) {
@@ -538,21 +566,10 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     __syncthreads();   // every warp is done with its scratch in R2
     // ---- D = V W: A = V (row = tile row, K = reflector) chunks, copied from
     // the panel's pre-split operand into R2
-    for (int kk = 0; kk < NB / KC; kk++) {
-        const int b = kk & 1, ao = R2 + b * 2 * OPB;
-        if (kk >= 2)
-            ok &= mixed_wait(mbar, phase, b);
-        if (tid == 0)
-            load_chunk(sm + ao, TFg + TF_OFF_V + (size_t)kk * TF_CHUNK_BYTES, b);
-        mixed_issue(&mbar[b], [&]() {
-            ok &= load_wait(b);
-            mma_chunk(tmem, sbase + ao, sbase + kk * 2 * OPB, kk == 0);
-        });
-    }
-    ok &= mixed_wait(mbar, phase, 0);
-    ok &= mixed_wait(mbar, phase, 1);
+    ok &= stream_product(tmem, TF_OFF_V);
     if (!__syncthreads_and(ok))
         return fail();
+    tc::fence_after_sync();
 
     // ---- C -= D (FP64), row = tensor-memory lane
     for (int h = 0; h < 2; h++) {
