@@ -231,8 +231,9 @@ int tileqr_factor_noalloc(int64_t m, int64_t n, const double *A, int64_t lda, in
  *   ib    16 or 32 (nb is 128)
  *   V, T  device: the 128 x 128 reflector tile (column-major) and its
  *         ib x 128 T strip (column-major, ld ib), as in tileqr_desc
- *   B, C  device 128 x 128 column-major tiles, updated in place (B is not
- *         read for TILEQR_UPDATE_LARFB and may be NULL)
+ *   B, C  device 128 x 128 column-major tiles, 16-byte aligned (else -5 /
+ *         -6), updated in place (B is not read for TILEQR_UPDATE_LARFB and
+ *         may be NULL)
  *   workspace  device, 256-byte aligned, >= TILEQR_MIXED_UPDATE_WS_BYTES
  * Synchronous.  Returns 0, -i, TILEQR_ERR_UNSUPPORTED, TILEQR_ERR_WORKSPACE,
  * TILEQR_ERR_TIMEOUT (a tensor-core wait gave up) or TILEQR_ERR_CUDA. */
@@ -279,6 +280,25 @@ int tileqr_apply_qt(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, 
  * workspace and returns as tileqr_apply_qt. */
 int tileqr_apply_q(const tileqr_desc *d, double *B, int64_t ldb, int64_t nrhs, void *workspace, size_t ws_bytes,
                    tileqr_stream_t stream);
+
+/* B <- Q^T B (trans = 1) or Q B (trans = 0) on the tensor cores, for a
+ * TILEQR_TF32 factorization with nb 128: the same task graphs as
+ * tileqr_apply_qt / tileqr_apply_q (Sec. 3.2.1, Algorithm 2's order and its
+ * reverse), each update applied with the full T and the pre-split operands
+ * the factorization kept (3xTF32 products, FP32 accumulation, columns of B
+ * scaled by powers of two), on column chunks of 128.  Not FP64: each column
+ * comes out within about 2^-19 of the exact product relative to its norm;
+ * the FP64 refinement of tileqr_solve_ls_refine uses it for its corrections.
+ *   trans      1: Q^T B;  0: Q B (T is first transposed into the workspace)
+ *   B, ldb     device, column-major m x nrhs, ldb >= max(1,m), in place
+ *   workspace  device, 256-byte aligned, tileqr_apply_mixed_workspace_size()
+ *              bytes (the factorization's workspace must be intact)
+ * Synchronous.  Returns 0, -i, TILEQR_ERR_UNSUPPORTED (not TILEQR_TF32 or
+ * nb != 128), TILEQR_ERR_WORKSPACE, TILEQR_ERR_TIMEOUT (a tensor-core or
+ * copy wait gave up) or TILEQR_ERR_CUDA. */
+int tileqr_apply_mixed_workspace_size(const tileqr_desc *d, int64_t nrhs, size_t *bytes);
+int tileqr_apply_mixed(const tileqr_desc *d, int trans, double *B, int64_t ldb, int64_t nrhs, void *workspace,
+                       size_t ws_bytes, tileqr_stream_t stream);
 
 /* The leading ncols columns of Q (0 <= ncols <= m; ncols = min(m,n) gives
  * the thin factor with A = Q R), written to Q (device, column-major m x

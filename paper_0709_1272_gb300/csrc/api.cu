@@ -382,6 +382,112 @@ extern "C" int tileqr_apply_q(const tileqr_desc *d, double *B, int64_t ldb, int6
     return apply_impl(d, B, ldb, nrhs, workspace, ws_bytes, stream, true);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed application (TILEQR_TF32 factorizations, nb 128): Q^T B or Q B on
+// the tensor cores from the operands the factorization kept.
+namespace tqr {
+
+size_t mixed_tn_bytes(const WsLayout &L)
+{
+    return (L.H < L.p ? 2 : 1) * tf_pairs(L.p, L.steps) * TF_BYTES;
+}
+
+int mixed_operands(const tileqr_desc *d, const WsLayout &L, unsigned char *TN, cudaStream_t st, MixedOperands *M)
+{
+    if (d->precision != TILEQR_TF32 || d->nb != 128 || d->workspace == nullptr || L.off_TF2 <= L.off_TF)
+        return TILEQR_ERR_UNSUPPORTED;
+    const unsigned char *ws = (const unsigned char *)d->workspace;
+    const size_t npairs = tf_pairs(L.p, L.steps);
+    const bool tree = L.H < L.p;
+    *M = MixedOperands{};
+    M->TF = ws + L.off_TF;
+    M->TF2 = tree ? ws + L.off_TF2 : nullptr;
+    if (TN != nullptr) {
+        int rc = launch_tf_transpose(M->TF, TF_PAIR_BYTES, TN, npairs, st);
+        if (rc)
+            return rc;
+        M->TN = TN;
+        if (tree) {
+            if ((rc = launch_tf_transpose(M->TF2, TF_PAIR_BYTES, TN + npairs * TF_BYTES, npairs, st)) != 0)
+                return rc;
+            M->TN2 = TN + npairs * TF_BYTES;
+        }
+    }
+    return 0;
+}
+
+}  // namespace tqr
+
+static int64_t mixed_ncp(int64_t nrhs) { return ((nrhs + 127) / 128) * 128; }
+
+extern "C" int tileqr_apply_mixed_workspace_size(const tileqr_desc *d, int64_t nrhs, size_t *bytes)
+{
+    if (d == nullptr)
+        return -1;
+    if (nrhs < 0)
+        return -2;
+    if (bytes == nullptr)
+        return -3;
+    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib, d->domain, d->precision);
+    const int64_t ncp = mixed_ncp(nrhs);
+    *bytes = align256((size_t)L.p * L.nb * ncp * sizeof(double)) + align256(mixed_tn_bytes(L)) +
+             align256(apply_sched_bytes(L, (int)(ncp / 128))) + align256((size_t)(ncp ? ncp : 1) * sizeof(int));
+    return 0;
+}
+
+extern "C" int tileqr_apply_mixed(const tileqr_desc *d, int trans, double *B, int64_t ldb, int64_t nrhs,
+                                  void *workspace, size_t ws_bytes, tileqr_stream_t stream)
+{
+    if (d == nullptr)
+        return -1;
+    if (trans != 0 && trans != 1)
+        return -2;
+    if (B == nullptr && nrhs > 0 && d->m > 0)
+        return -3;
+    if (ldb < (d->m > 1 ? d->m : 1))
+        return -4;
+    if (nrhs < 0)
+        return -5;
+    if (d->precision != TILEQR_TF32 || d->nb != 128)
+        return TILEQR_ERR_UNSUPPORTED;
+    size_t need = 0;
+    tileqr_apply_mixed_workspace_size(d, nrhs, &need);
+    if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < need)
+        return TILEQR_ERR_WORKSPACE;
+    if (nrhs == 0 || d->m == 0 || d->n == 0)
+        return 0;
+    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib, d->domain, d->precision);
+    const int64_t ncp = mixed_ncp(nrhs);
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    double *Bt = (double *)ws;
+    size_t off = align256((size_t)L.p * L.nb * ncp * sizeof(double));
+    unsigned char *TN = (unsigned char *)ws + off;
+    off += align256(mixed_tn_bytes(L));
+    char *sched = ws + off;
+    off += align256(apply_sched_bytes(L, (int)(ncp / 128)));
+    int *cexp = (int *)(ws + off);
+    if (cudaMemsetAsync(sched, 0, 256, st) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    MixedOperands M;
+    int rc = mixed_operands(d, L, trans ? nullptr : TN, st, &M);
+    if (rc == 0)
+        rc = launch_cm2rows(B, ldb, d->m, nrhs, Bt, d->nb, d->p, ncp, st);
+    if (rc == 0)
+        rc = launch_rows_cexp(Bt, d->nb, d->p, ncp, cexp, st);
+    if (rc == 0)
+        rc = launch_apply_mixed(L, M, Bt, ncp, cexp, sched, st, watchdog_ns_default(), trans == 0);
+    if (rc == 0)
+        rc = launch_rows2cm(Bt, d->nb, d->p, ncp, d->m, nrhs, B, ldb, st);
+    if (rc)
+        return rc;
+    SchedCtrl c;
+    if (cudaMemcpyAsync(&c, sched, sizeof(c), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    return c.error;
+}
+
 extern "C" int tileqr_form_q(const tileqr_desc *d, double *Q, int64_t ldq, int64_t ncols, void *workspace,
                              size_t ws_bytes, tileqr_stream_t stream)
 {
@@ -432,7 +538,7 @@ extern "C" int tileqr_solve_ls(const tileqr_desc *d, double *B, int64_t ldb, int
     int rc = apply_core(d, L, B, ldb, nrhs, (char *)workspace, st, &Bt, &ncp, &flag);
     if (rc)
         return rc;
-    rc = launch_trsm(L, d->tiles, Bt, ncp, flag, st);
+    rc = launch_trsm(L, d->tiles, Bt, ncp, flag, st, false, nrhs);
     if (rc)
         return rc;
     rc = launch_rows2cm(Bt, d->nb, d->p, ncp, d->m, nrhs, B, ldb, st);

@@ -15,6 +15,7 @@
 #include "graph.cuh"
 #include "sched.cuh"
 #include "tile_f64.cuh"
+#include "tile_mixed.cuh"
 
 namespace tqr {
 
@@ -26,12 +27,21 @@ struct ApplyArgs {
     int p, q, steps, nchunk;
     int64_t ncp;
     TGraph G;
+    // mixed form (tensor-core updates, chunks of nb = 128 columns): the
+    // factorization's pre-split operands per tile pair (TF; TF2 of the tree
+    // merges), the A operand of W for each pair at TW + pair * tw_stride +
+    // tw_off (T^T inside the TF block for Q^T, the transposed copy for Q),
+    // and the column exponents of Bt for the column scaling
+    const unsigned char *TF, *TF2, *TW, *TW2;
+    size_t tw_stride, tw_off;
+    const int *cexp;
+    int lm;
 };
 
-template <int NB, int S>
+template <int NB, int S, int CW = APPLY_W>
 __device__ __forceinline__ double *chunk_ptr(const ApplyArgs &A, int i, int cb)
 {
-    return A.Bt + ((size_t)i * A.ncp + (size_t)cb * APPLY_W) * NB;
+    return A.Bt + ((size_t)i * A.ncp + (size_t)cb * CW) * NB;
 }
 
 __device__ __forceinline__ size_t apply_cnt_idx(const ApplyArgs &A, int tt, int k, int i, int cb)
@@ -39,13 +49,31 @@ __device__ __forceinline__ size_t apply_cnt_idx(const ApplyArgs &A, int tt, int 
     return (((size_t)tt * A.steps + k) * A.p + i) * A.nchunk + cb;
 }
 
-template <int NB, int S, bool NOTRANS>
+// MIXED: the updates on the tensor cores (task_update_mixed_tf, 3xTF32 with
+// FP32 accumulation) on column chunks of nb = 128, for a TILEQR_TF32
+// factorization; one CTA per SM, holding tensor memory for the whole launch.
+template <int NB, int S, bool NOTRANS, bool MIXED = false>
 __global__ void __launch_bounds__(NT, 1) k_apply_dag(ApplyArgs A, Queues Q)
 {
     extern __shared__ double sm[];
     __shared__ unsigned long long s_code;
     __shared__ int s_cmd;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[4];
     const TGraph &G = A.G;
+    constexpr int CW = MIXED ? NB : APPLY_W;
+    uint32_t tmem = 0, mphase = 0;
+    if constexpr (MIXED) {
+        if ((threadIdx.x >> 5) == 0)
+            tc::tmem_alloc(&s_tmem, MIX_TMEM_COLS);
+        if (threadIdx.x == 0)
+            for (int b = 0; b < 4; b++)
+                tc::mbar_init(&s_mbar[b], 1);
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tmem = s_tmem;
+    }
     if (blockIdx.x == 0) {
         if (!NOTRANS) {
             // step 0's DLARFBs (one per domain head and chunk) have no predecessors
@@ -75,16 +103,38 @@ __global__ void __launch_bounds__(NT, 1) k_apply_dag(ApplyArgs A, Queues Q)
         int k, i, cb;
         decode_task(s_code, k, i, cb);
         const int kind = ga_kind(G, decode_tt(s_code), k, i);
-        const double *Vt = A.tiles + ((size_t)k * A.p + i) * (size_t)NB * NB;
-        const size_t strip = ((size_t)k * A.p + i) * (size_t)S * NB;
-        if (kind == K_LARFB)
-            task_larfb<NB, S, APPLY_W, NOTRANS>(sm, chunk_ptr<NB, S>(A, i, cb), Vt, A.T + strip, APPLY_W);
-        else if (kind == K_SSRFB)
-            task_ssrfb<NB, S, APPLY_W, false, NOTRANS>(sm, chunk_ptr<NB, S>(A, g_head(G, k, g_dom(G, k, i)), cb),
-                                                       chunk_ptr<NB, S>(A, i, cb), Vt, A.T + strip, APPLY_W);
-        else
-            task_ssrfb<NB, S, APPLY_W, true, NOTRANS>(sm, chunk_ptr<NB, S>(A, g_partner(G, k, i), cb),
-                                                      chunk_ptr<NB, S>(A, i, cb), Vt, A.T2 + strip, APPLY_W);
+        if constexpr (MIXED) {
+            unsigned char *smb = (unsigned char *)sm;
+            const size_t pi = tf_index(A.p, i, k);
+            const bool tt = kind != K_LARFB && kind != K_SSRFB;
+            const unsigned char *pair = (tt ? A.TF2 : A.TF) + pi * TF_PAIR_BYTES;
+            const unsigned char *tw = (tt ? A.TW2 : A.TW) + pi * A.tw_stride + A.tw_off;
+            const int *cx = A.cexp + (size_t)cb * NB;
+            int *err = &Q.ctrl->error;
+            if (kind == K_LARFB)
+                task_update_mixed_tf<S, VK_UNIT>(smb, nullptr, chunk_ptr<NB, S, CW>(A, i, cb), pair, tw, cx, A.lm,
+                                                 tmem, s_mbar, mphase, err);
+            else if (kind == K_SSRFB)
+                task_update_mixed_tf<S, VK_FULL>(smb, chunk_ptr<NB, S, CW>(A, g_head(G, k, g_dom(G, k, i)), cb),
+                                                 chunk_ptr<NB, S, CW>(A, i, cb), pair, tw, cx, A.lm, tmem, s_mbar,
+                                                 mphase, err);
+            else
+                task_update_mixed_tf<S, VK_UPPER>(smb, chunk_ptr<NB, S, CW>(A, g_partner(G, k, i), cb),
+                                                  chunk_ptr<NB, S, CW>(A, i, cb), pair, tw, cx, A.lm, tmem, s_mbar,
+                                                  mphase, err);
+        } else {
+            const double *Vt = A.tiles + ((size_t)k * A.p + i) * (size_t)NB * NB;
+            const size_t strip = ((size_t)k * A.p + i) * (size_t)S * NB;
+            if (kind == K_LARFB)
+                task_larfb<NB, S, APPLY_W, NOTRANS>(sm, chunk_ptr<NB, S>(A, i, cb), Vt, A.T + strip, APPLY_W);
+            else if (kind == K_SSRFB)
+                task_ssrfb<NB, S, APPLY_W, false, NOTRANS>(sm,
+                                                           chunk_ptr<NB, S>(A, g_head(G, k, g_dom(G, k, i)), cb),
+                                                           chunk_ptr<NB, S>(A, i, cb), Vt, A.T + strip, APPLY_W);
+            else
+                task_ssrfb<NB, S, APPLY_W, true, NOTRANS>(sm, chunk_ptr<NB, S>(A, g_partner(G, k, i), cb),
+                                                          chunk_ptr<NB, S>(A, i, cb), Vt, A.T2 + strip, APPLY_W);
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             // successors: forward ones for Q^T; forward predecessors for Q, each
@@ -100,6 +150,12 @@ __global__ void __launch_bounds__(NT, 1) k_apply_dag(ApplyArgs A, Queues Q)
             __threadfence();
             atomicAdd(&Q.ctrl->completed, 1u);
         }
+    }
+    if constexpr (MIXED) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0)
+            tc::tmem_dealloc(tmem, MIX_TMEM_COLS);
     }
 }
 
@@ -129,28 +185,13 @@ size_t apply_sched_bytes(const WsLayout &L, int nchunk)
     return 256 + a.cnt_bytes + a.q0_bytes + a.q1_bytes;
 }
 
-template <int NB, int S, bool NOTRANS>
-static int launch_apply_t(const WsLayout &L, const double *tiles, const double *T, const double *T2, double *Bt,
-                          int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns)
+// Queues of one application over nchunk column chunks (state at sched,
+// zeroed here); returns the task count (0: nothing to run).
+static unsigned int apply_queues(const WsLayout &L, int nchunk, char *sched, unsigned long long watchdog_ns,
+                                 Queues &Q)
 {
-    constexpr size_t smem = F64Cfg<NB, S, APPLY_W>::SMEM;
-    int grid_max = 0;
-    const int rc = kernel_grid((const void *)k_apply_dag<NB, S, NOTRANS>, NT, smem, &grid_max);
-    if (rc)
-        return rc;
-    ApplyArgs A;
-    A.tiles = tiles;
-    A.T = T;
-    A.T2 = T2;
-    A.Bt = Bt;
-    A.p = L.p;
-    A.q = L.q;
-    A.steps = L.steps;
-    A.ncp = ncp;
-    A.nchunk = (int)(ncp / APPLY_W);
-    A.G = make_graph(L.p, L.q, L.H);
-    const ApplySched a = apply_sched(L, A.nchunk);
-    Queues Q;
+    const ApplySched a = apply_sched(L, nchunk);
+    Q = Queues{};
     Q.ctrl = (SchedCtrl *)sched;
     Q.cnt = (unsigned int *)(sched + 256);
     Q.slot[0] = (unsigned long long *)(sched + 256 + a.cnt_bytes);
@@ -164,7 +205,38 @@ static int launch_apply_t(const WsLayout &L, const double *tiles, const double *
     Q.withheld = ~0ull;
     Q.trace = nullptr;
     Q.trace_cap = 0;
-    if (Q.total == 0)
+    return Q.total;
+}
+
+static ApplyArgs apply_args(const WsLayout &L, const double *tiles, const double *T, const double *T2, double *Bt,
+                            int64_t ncp, int chunk)
+{
+    ApplyArgs A{};
+    A.tiles = tiles;
+    A.T = T;
+    A.T2 = T2;
+    A.Bt = Bt;
+    A.p = L.p;
+    A.q = L.q;
+    A.steps = L.steps;
+    A.ncp = ncp;
+    A.nchunk = (int)(ncp / chunk);
+    A.G = make_graph(L.p, L.q, L.H);
+    return A;
+}
+
+template <int NB, int S, bool NOTRANS>
+static int launch_apply_t(const WsLayout &L, const double *tiles, const double *T, const double *T2, double *Bt,
+                          int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns)
+{
+    constexpr size_t smem = F64Cfg<NB, S, APPLY_W>::SMEM;
+    int grid_max = 0;
+    const int rc = kernel_grid((const void *)k_apply_dag<NB, S, NOTRANS>, NT, smem, &grid_max);
+    if (rc)
+        return rc;
+    const ApplyArgs A = apply_args(L, tiles, T, T2, Bt, ncp, APPLY_W);
+    Queues Q;
+    if (apply_queues(L, A.nchunk, sched, watchdog_ns, Q) == 0)
         return 0;
     if (cudaMemsetAsync(sched, 0, apply_sched_bytes(L, A.nchunk), st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
@@ -172,6 +244,158 @@ static int launch_apply_t(const WsLayout &L, const double *tiles, const double *
     if ((unsigned)grid > Q.total)
         grid = (int)Q.total;
     k_apply_dag<NB, S, NOTRANS><<<grid, NT, smem, st>>>(A, Q);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
+}
+
+template <int S, bool NOTRANS>
+static int launch_apply_mixed_t(const WsLayout &L, const MixedOperands &M, double *Bt, int64_t ncp,
+                                const int *cexp, char *sched, cudaStream_t st, unsigned long long watchdog_ns)
+{
+    constexpr size_t smem = TF_UPDATE_SMEM_TOTAL;
+    int grid_max = 0;
+    int rc = kernel_grid((const void *)k_apply_dag<128, S, NOTRANS, true>, NT, smem, &grid_max);
+    if (rc)
+        return rc;
+    // one CTA per SM: each holds MIX_TMEM_COLS of the SM's tensor memory
+    int nsm = 0;
+    if ((rc = device_sm_count(&nsm)) != 0)
+        return rc;
+    if (grid_max > nsm)
+        grid_max = nsm;
+    ApplyArgs A = apply_args(L, nullptr, nullptr, nullptr, Bt, ncp, 128);
+    A.TF = M.TF;
+    A.TF2 = M.TF2;
+    if (NOTRANS) {
+        A.TW = M.TN;
+        A.TW2 = M.TN2;
+        A.tw_stride = TF_BYTES;
+        A.tw_off = 0;
+    } else {
+        A.TW = M.TF;
+        A.TW2 = M.TF2;
+        A.tw_stride = TF_PAIR_BYTES;
+        A.tw_off = TF_OFF_T;
+    }
+    A.cexp = cexp;
+    A.lm = ceil_log2_sqrt((int64_t)L.p * L.nb);
+    Queues Q;
+    if (apply_queues(L, A.nchunk, sched, watchdog_ns, Q) == 0)
+        return 0;
+    if (cudaMemsetAsync(sched, 0, apply_sched_bytes(L, A.nchunk), st) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    int grid = grid_max;
+    if ((unsigned)grid > Q.total)
+        grid = (int)Q.total;
+    k_apply_dag<128, S, NOTRANS, true><<<grid, NT, smem, st>>>(A, Q);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
+}
+
+int launch_apply_mixed(const WsLayout &L, const MixedOperands &M, double *Bt, int64_t ncp, const int *cexp,
+                       char *sched, cudaStream_t st, unsigned long long watchdog_ns, bool notrans)
+{
+    if (L.nb != 128 || ncp % 128 != 0 || M.TF == nullptr || (L.H < L.p && M.TF2 == nullptr) ||
+        (notrans && (M.TN == nullptr || (L.H < L.p && M.TN2 == nullptr))))
+        return TILEQR_ERR_UNSUPPORTED;
+    if (kernel_smem_optin((const void *)k_apply_dag<128, 16, false, true>, TF_UPDATE_SMEM_TOTAL) ||
+        kernel_smem_optin((const void *)k_apply_dag<128, 16, true, true>, TF_UPDATE_SMEM_TOTAL) ||
+        kernel_smem_optin((const void *)k_apply_dag<128, 32, false, true>, TF_UPDATE_SMEM_TOTAL) ||
+        kernel_smem_optin((const void *)k_apply_dag<128, 32, true, true>, TF_UPDATE_SMEM_TOTAL))
+        return TILEQR_ERR_CUDA;
+    if (L.ib == 16)
+        return notrans ? launch_apply_mixed_t<16, true>(L, M, Bt, ncp, cexp, sched, st, watchdog_ns)
+                       : launch_apply_mixed_t<16, false>(L, M, Bt, ncp, cexp, sched, st, watchdog_ns);
+    if (L.ib == 32)
+        return notrans ? launch_apply_mixed_t<32, true>(L, M, Bt, ncp, cexp, sched, st, watchdog_ns)
+                       : launch_apply_mixed_t<32, false>(L, M, Bt, ncp, cexp, sched, st, watchdog_ns);
+    return TILEQR_ERR_UNSUPPORTED;
+}
+
+// T (not transposed) of every tile pair, pre-split like the T^T operand:
+// TN(r, K = c) = TT(c, r), hi and lo parts transposed separately (exact).
+// One CTA per pair (grid-stride); src pairs are src_stride bytes apart with
+// T^T at offset TF_OFF_T, dst pairs TF_BYTES apart.
+__global__ void __launch_bounds__(256) k_tf_transpose(const unsigned char *__restrict__ src, size_t src_stride,
+                                                      unsigned char *dst, size_t npairs)
+{
+    extern __shared__ float ts[];   // [c][r], ld 129
+    constexpr int LD = 129, HALF = TF_CHUNK_BYTES / 2;
+    for (size_t pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        const unsigned char *tt = src + pr * src_stride + TF_OFF_T;
+        unsigned char *tn = dst + pr * TF_BYTES;
+        for (int part = 0; part < 2; part++) {
+            __syncthreads();
+            // element (row a, K = k) of chunk ch, part: 4-byte word w of the
+            // chunk's part in core-matrix order (tc::kmajor_off with K extent 32)
+            for (int e = threadIdx.x; e < 128 * 128; e += 256) {
+                const int ch = e >> 12, w = e & 4095;
+                const int a = ((w >> 8) << 3) | ((w >> 2) & 7), k = (((w >> 5) & 7) << 2) | (w & 3);
+                ts[(ch * 32 + k) * LD + a] = *(const float *)(tt + ch * TF_CHUNK_BYTES + part * HALF + 4 * w);
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < 128 * 128; e += 256) {
+                const int ch = e >> 12, w = e & 4095;
+                const int r = ((w >> 8) << 3) | ((w >> 2) & 7), c = ch * 32 + ((((w >> 5) & 7) << 2) | (w & 3));
+                *(float *)(tn + ch * TF_CHUNK_BYTES + part * HALF + 4 * w) = ts[r * LD + c];
+            }
+        }
+    }
+}
+
+int launch_tf_transpose(const unsigned char *src, size_t src_stride, unsigned char *dst, size_t npairs,
+                        cudaStream_t st)
+{
+    if (npairs == 0)
+        return 0;
+    constexpr size_t smem = (size_t)128 * 129 * sizeof(float);
+    if (kernel_smem_optin((const void *)k_tf_transpose, smem))
+        return TILEQR_ERR_CUDA;
+    int nsm = 0;
+    const int rc = device_sm_count(&nsm);
+    if (rc)
+        return rc;
+    const size_t grid = npairs < (size_t)nsm * 2 ? npairs : (size_t)nsm * 2;
+    k_tf_transpose<<<(unsigned)grid, 256, smem, st>>>(src, src_stride, dst, npairs);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
+}
+
+// cexp[c] = the largest biased FP64 exponent of column c of the tile-row
+// buffer Bt (p blocks of nb x ncp), for the column scaling of the mixed
+// application: block (x, y) takes column x over the tile rows y, y +
+// gridDim.y, ..., cexp cleared beforehand.
+__global__ void __launch_bounds__(256) k_rows_cexp(const double *__restrict__ Bt, int nb, int p, int64_t ncp,
+                                                   int *cexp)
+{
+    __shared__ unsigned int red[8];
+    const int64_t c = blockIdx.x;
+    unsigned int e = 0;
+    for (int64_t i = blockIdx.y; i < p; i += gridDim.y)
+        for (int r = threadIdx.x; r < nb; r += 256)
+            e = max(e, (unsigned int)(__double2hiint(Bt[(i * ncp + c) * nb + r]) >> 20) & 0x7FFu);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; w++)
+            e = max(e, red[w]);
+        if (e)
+            atomicMax(cexp + c, (int)e);
+    }
+}
+
+int launch_rows_cexp(const double *Bt, int nb, int p, int64_t ncp, int *cexp, cudaStream_t st)
+{
+    if (ncp == 0)
+        return 0;
+    if (cudaMemsetAsync(cexp, 0, (size_t)ncp * sizeof(int), st) != cudaSuccess)
+        return TILEQR_ERR_CUDA;
+    const int ysplit = p < 64 ? (p > 0 ? p : 1) : 64;
+    k_rows_cexp<<<dim3((unsigned)ncp, (unsigned)ysplit), 256, 0, st>>>(Bt, nb, p, ncp, cexp);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
 }
@@ -191,92 +415,6 @@ int launch_apply(const WsLayout &L, const double *tiles, const double *T, const 
     TQR_CASE(256, 32)
 #undef TQR_CASE
     return TILEQR_ERR_UNSUPPORTED;
-}
-
-// ---------------------------------------------------------------------------
-// Tiled back substitution R X = Y, Y = the first q row blocks of Bt (m >= n).
-// For j = q-1 .. 0: X_j = R_jj^{-1} Y_j (k_trsm_diag), then Y_i -= R_ij X_j
-// for i < j (k_trsm_update).  One CTA per 32-column chunk (and row block).
-__global__ void __launch_bounds__(NT) k_trsm_diag(const double *__restrict__ tiles, double *Bt, int nb,
-                                                  int p, int64_t ncp, int j, int64_t n, int *flag)
-{
-    extern __shared__ double ys[];  // nb x 32, [r][c] ld 33
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cb = blockIdx.x;
-    const double *R = tiles + ((size_t)j * p + j) * (size_t)nb * nb;
-    double *Y = Bt + ((size_t)j * ncp + (size_t)cb * 32) * nb;
-    for (int idx = threadIdx.x; idx < nb * 32; idx += NT) {
-        const int c = idx / nb, r = idx - c * nb;
-        ys[r * 33 + c] = Y[(size_t)c * nb + r];
-    }
-    __syncthreads();
-    const int64_t col0 = (int64_t)j * nb;
-    int last = nb - 1;
-    if (col0 + last >= n)
-        last = (int)(n - 1 - col0);
-    for (int c = last; c >= 0; c--) {
-        const double d = ldcg(R + (size_t)c * nb + c);
-        double x = 0.0;
-        if (d != 0.0)
-            x = ys[c * 33 + lane] / d;
-        else if (threadIdx.x == 0)
-            atomicCAS(flag, 0, (int)(col0 + c + 1));
-        __syncthreads();
-        if (warp == 0)
-            ys[c * 33 + lane] = x;
-        for (int r = warp; r < c; r += NWARP)
-            ys[r * 33 + lane] = fma(-ldcg(R + (size_t)c * nb + r), x, ys[r * 33 + lane]);
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < nb * 32; idx += NT) {
-        const int c = idx / nb, r = idx - c * nb;
-        Y[(size_t)c * nb + r] = (r <= last) ? ys[r * 33 + c] : 0.0;
-    }
-}
-
-__global__ void __launch_bounds__(NT) k_trsm_update(const double *__restrict__ tiles, double *Bt, int nb,
-                                                    int p, int64_t ncp, int j)
-{
-    extern __shared__ double xs[];  // nb x 32, [r][c] ld 33
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x, cb = blockIdx.y;
-    const double *R = tiles + ((size_t)j * p + i) * (size_t)nb * nb;
-    const double *X = Bt + ((size_t)j * ncp + (size_t)cb * 32) * nb;
-    double *Y = Bt + ((size_t)i * ncp + (size_t)cb * 32) * nb;
-    for (int idx = threadIdx.x; idx < nb * 32; idx += NT) {
-        const int c = idx / nb, r = idx - c * nb;
-        xs[r * 33 + c] = X[(size_t)c * nb + r];
-    }
-    __syncthreads();
-    for (int r = warp; r < nb; r += NWARP) {
-        double acc0 = Y[(size_t)lane * nb + r], acc1 = 0.0;
-        int c = 0;
-        for (; c + 1 < nb; c += 2) {
-            acc0 = fma(-ldcg(R + (size_t)c * nb + r), xs[c * 33 + lane], acc0);
-            acc1 = fma(-ldcg(R + (size_t)(c + 1) * nb + r), xs[(c + 1) * 33 + lane], acc1);
-        }
-        if (c < nb)
-            acc0 = fma(-ldcg(R + (size_t)c * nb + r), xs[c * 33 + lane], acc0);
-        Y[(size_t)lane * nb + r] = acc0 + acc1;
-    }
-}
-
-int launch_trsm(const WsLayout &L, const double *tiles, double *Bt, int64_t ncp, int *flag, cudaStream_t st)
-{
-    const int nchunk = (int)(ncp / 32);
-    const size_t smem = (size_t)L.nb * 33 * sizeof(double);
-    if (kernel_smem_optin((const void *)k_trsm_diag, 256 * 33 * 8) != 0 ||
-        kernel_smem_optin((const void *)k_trsm_update, 256 * 33 * 8) != 0)
-        return TILEQR_ERR_CUDA;
-    for (int j = L.q - 1; j >= 0; j--) {
-        k_trsm_diag<<<nchunk, NT, smem, st>>>(tiles, Bt, L.nb, L.p, ncp, j, L.n, flag);
-        count_launch();
-        if (j > 0) {
-            k_trsm_update<<<dim3(j, nchunk), NT, smem, st>>>(tiles, Bt, L.nb, L.p, ncp, j);
-            count_launch();
-        }
-    }
-    return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
 }
 
 }  // namespace tqr

@@ -98,9 +98,9 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
         break;
     case K_LARFB:
         if constexpr (MIXED) {
-            task_update_mixed_tf<S, VK_UNIT>(smb, nullptr, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                             tf_ptr(F.TF, F.p, i, k), cexp_ptr<NB>(F, j), F.lm, tmem, mbar, mphase,
-                                             err);
+            task_update_mixed_tf<S, VK_UNIT>(smb, nullptr, tile_ptr<NB, S>(F, i, j), tf_ptr(F.TF, F.p, i, k),
+                                             tf_ptr(F.TF, F.p, i, k) + TF_OFF_T, cexp_ptr<NB>(F, j), F.lm, tmem,
+                                             mbar, mphase, err);
         } else {
             task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
         }
@@ -108,9 +108,9 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
     case K_SSRFB: {
         double *top = tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), j);
         if constexpr (MIXED) {
-            task_update_mixed_tf<S, VK_FULL>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                             tf_ptr(F.TF, F.p, i, k), cexp_ptr<NB>(F, j), F.lm, tmem, mbar, mphase,
-                                             err);
+            task_update_mixed_tf<S, VK_FULL>(smb, top, tile_ptr<NB, S>(F, i, j), tf_ptr(F.TF, F.p, i, k),
+                                             tf_ptr(F.TF, F.p, i, k) + TF_OFF_T, cexp_ptr<NB>(F, j), F.lm, tmem,
+                                             mbar, mphase, err);
         } else {
             task_ssrfb<NB, S>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
                               strip_ptr<NB, S>(F, i, k));
@@ -120,9 +120,9 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
     default: {   // K_TTMQR
         double *top = tile_ptr<NB, S>(F, g_partner(G, k, i), j);
         if constexpr (MIXED) {
-            task_update_mixed_tf<S, VK_UPPER>(smb, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                                              tf_ptr(F.TF2, F.p, i, k), cexp_ptr<NB>(F, j), F.lm, tmem, mbar,
-                                              mphase, err);
+            task_update_mixed_tf<S, VK_UPPER>(smb, top, tile_ptr<NB, S>(F, i, j), tf_ptr(F.TF2, F.p, i, k),
+                                              tf_ptr(F.TF2, F.p, i, k) + TF_OFF_T, cexp_ptr<NB>(F, j), F.lm, tmem,
+                                              mbar, mphase, err);
         } else
             task_ssrfb<NB, S, FactorW<NB>::value, true>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
                                                         strip2_ptr<NB, S>(F, i, k));

@@ -54,11 +54,34 @@ size_t apply_sched_bytes(const WsLayout &L, int nchunk);
 // notrans: Q B instead of Q^T B.
 int launch_apply(const WsLayout &L, const double *tiles, const double *T, const double *T2, double *Bt,
                  int64_t ncp, char *sched, cudaStream_t st, unsigned long long watchdog_ns, bool notrans = false);
+// Mixed form of the application for a TILEQR_TF32 factorization (nb 128):
+// the updates as 3xTF32 tensor-core products (task_update_mixed_tf) on column
+// chunks of 128 (ncp a multiple of 128), with the operands the factorization
+// kept per tile pair (TF; TF2 for the tree merges) and, for Q B (notrans),
+// T itself pre-split (TN, TN2, from launch_tf_transpose).  cexp: the largest
+// biased exponent of every column of Bt (launch_rows_cexp).
+struct MixedOperands {
+    const unsigned char *TF = nullptr, *TF2 = nullptr, *TN = nullptr, *TN2 = nullptr;
+};
+int launch_apply_mixed(const WsLayout &L, const MixedOperands &M, double *Bt, int64_t ncp, const int *cexp,
+                       char *sched, cudaStream_t st, unsigned long long watchdog_ns, bool notrans);
+// dst pair t (TF_BYTES apart) <- T of src pair t (src_stride apart, T^T at
+// TF_OFF_T), pre-split the same way.
+int launch_tf_transpose(const unsigned char *src, size_t src_stride, unsigned char *dst, size_t npairs,
+                        cudaStream_t st);
+int launch_rows_cexp(const double *Bt, int nb, int p, int64_t ncp, int *cexp, cudaStream_t st);
+// Bytes of the transposed T copies of a TILEQR_TF32 layout; the operand
+// blocks of the factorization described by d (L: its TILEQR_TF32 layout),
+// with T transposed into TN first when TN is not NULL.
+size_t mixed_tn_bytes(const WsLayout &L);
+int mixed_operands(const tileqr_desc *d, const WsLayout &L, unsigned char *TN, cudaStream_t st, MixedOperands *M);
 // B (m x ncols, column-major) <- the leading ncols columns of the m x m identity.
 int launch_eye(double *B, int64_t ldb, int64_t m, int64_t ncols, cudaStream_t st);
-// Back substitution R X = Y on the first q row blocks of Bt; sets *flag to
-// j+1 (device int) for an exact zero R(j,j).
-int launch_trsm(const WsLayout &L, const double *tiles, double *Bt, int64_t ncp, int *flag, cudaStream_t st);
+// Back substitution R X = Y (trans: forward substitution R^T X = Y) on the
+// first q row blocks of Bt, for its first ncols columns (all ncp if
+// negative); sets *flag to j+1 (device int) for an exact zero R(j,j).
+int launch_trsm(const WsLayout &L, const double *tiles, double *Bt, int64_t ncp, int *flag, cudaStream_t st,
+                bool trans = false, int64_t ncols = -1);
 
 }  // namespace tqr
 

@@ -7,6 +7,10 @@
 #include "factor.h"
 #include "launch_cache.h"
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 namespace tqr {
 
 static int current_device(int *dev)
@@ -25,15 +29,12 @@ int kernel_grid(const void *func, int threads, size_t smem, int *grid)
     int rc = current_device(&dev);
     if (rc)
         return rc;
+    if ((rc = kernel_smem_optin(func, smem)) != 0)
+        return rc;
     return cache.get(
         dev, func, smem, threads,
         [&](int &g) {
             int nsm = 0, per_sm = 0;
-            if (smem > 0 &&
-                cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-                cudaGetLastError();
-                return (int)TILEQR_ERR_CUDA;
-            }
             if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess ||
                 nsm < 1 || per_sm < 1) {
@@ -46,25 +47,31 @@ int kernel_grid(const void *func, int threads, size_t smem, int *grid)
         grid);
 }
 
+// The opt-in only ever raises a kernel's dynamic shared-memory limit: sizes
+// within the default 48 KB need none, and a kernel launched with several
+// sizes (a tile size per call) keeps the largest opt-in made on the device,
+// so a later call with a smaller size cannot lower the limit under an
+// earlier one.
 int kernel_smem_optin(const void *func, size_t smem)
 {
-    static LaunchCache<char> cache;
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> raised;   // largest opt-in per (device, kernel)
+    if (smem <= 48 * 1024)
+        return 0;
     int dev = 0;
-    int rc = current_device(&dev);
+    const int rc = current_device(&dev);
     if (rc)
         return rc;
-    char done = 0;
-    return cache.get(
-        dev, func, smem, 0,
-        [&](char &v) {
-            if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-                cudaGetLastError();
-                return (int)TILEQR_ERR_CUDA;
-            }
-            v = 1;
-            return 0;
-        },
-        &done);
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = raised[std::make_pair(dev, func)];
+    if (smem <= cur)
+        return 0;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return TILEQR_ERR_CUDA;
+    }
+    cur = smem;
+    return 0;
 }
 
 int device_sm_count(int *nsm)

@@ -13,6 +13,10 @@
 // proportional to the factors' error times the residual; this form converges
 // to the FP64 least-squares solution.  The refinement is an addition to the
 // paper.  Starting from x = 0, r = 0, the first step is the plain solve.
+// For a TILEQR_TF32 factorization (nb 128) the two applications of Q run on
+// the tensor cores (launch_apply_mixed: 3xTF32, about 2^-19 relative per
+// column, the same order of error as the factors), since they only form the
+// corrections; the residuals stay FP64, so the fixed point is the same.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -111,78 +115,6 @@ __global__ void k_ls_atr_reduce(const double *__restrict__ part, int nsplit, int
     }
 }
 
-// Tiled forward substitution R^T H = W on the first q row blocks of a
-// tile-row layout (nb x ncp per block).  For j = 0 .. q-1: H_j = R_jj^-T W_j
-// (k_trsmt_diag), then W_i -= R_ji^T H_j for i > j (k_trsmt_update).  One CTA
-// per 32-column chunk (and row block).
-__global__ void __launch_bounds__(NT) k_trsmt_diag(const double *__restrict__ tiles, double *Bt, int nb, int p,
-                                                   int64_t ncp, int j, int64_t n, int *flag)
-{
-    extern __shared__ double ys[];  // nb x 32, [r][c] ld 33
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cb = blockIdx.x;
-    const double *R = tiles + ((size_t)j * p + j) * (size_t)nb * nb;
-    double *Y = Bt + ((size_t)j * ncp + (size_t)cb * 32) * nb;
-    for (int idx = threadIdx.x; idx < nb * 32; idx += NT) {
-        const int c = idx / nb, r = idx - c * nb;
-        ys[r * 33 + c] = Y[(size_t)c * nb + r];
-    }
-    __syncthreads();
-    const int64_t col0 = (int64_t)j * nb;
-    int last = nb - 1;
-    if (col0 + last >= n)
-        last = (int)(n - 1 - col0);
-    // row c of R^T is column c of R: h(c) = (w(c) - sum_{r<c} R(r,c) h(r)) / R(c,c)
-    for (int c = 0; c <= last; c++) {
-        const double d = ldcg(R + (size_t)c * nb + c);
-        double x = 0.0;
-        if (d != 0.0)
-            x = ys[c * 33 + lane] / d;
-        else if (threadIdx.x == 0)
-            atomicCAS(flag, 0, (int)(col0 + c + 1));
-        __syncthreads();
-        if (warp == 0)
-            ys[c * 33 + lane] = x;
-        // rows r > c of the transposed system use R(c, r)
-        for (int r = c + 1 + warp; r <= last; r += NWARP)
-            ys[r * 33 + lane] = fma(-ldcg(R + (size_t)r * nb + c), x, ys[r * 33 + lane]);
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < nb * 32; idx += NT) {
-        const int c = idx / nb, r = idx - c * nb;
-        Y[(size_t)c * nb + r] = (r <= last) ? ys[r * 33 + c] : 0.0;
-    }
-}
-
-__global__ void __launch_bounds__(NT) k_trsmt_update(const double *__restrict__ tiles, double *Bt, int nb, int p,
-                                                     int64_t ncp, int j)
-{
-    extern __shared__ double xs[];  // nb x 32, [r][c] ld 33
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = j + 1 + blockIdx.x, cb = blockIdx.y;
-    const double *R = tiles + ((size_t)i * p + j) * (size_t)nb * nb;   // tile (j, i)
-    const double *X = Bt + ((size_t)j * ncp + (size_t)cb * 32) * nb;
-    double *Y = Bt + ((size_t)i * ncp + (size_t)cb * 32) * nb;
-    for (int idx = threadIdx.x; idx < nb * 32; idx += NT) {
-        const int c = idx / nb, r = idx - c * nb;
-        xs[r * 33 + c] = X[(size_t)c * nb + r];
-    }
-    __syncthreads();
-    // Y(r) -= sum_c R_ji(c, r) X(c): column r of the tile, contiguous
-    for (int r = warp; r < nb; r += NWARP) {
-        const double *col = R + (size_t)r * nb;
-        double acc0 = Y[(size_t)lane * nb + r], acc1 = 0.0;
-        int c = 0;
-        for (; c + 1 < nb; c += 2) {
-            acc0 = fma(-ldcg(col + c), xs[c * 33 + lane], acc0);
-            acc1 = fma(-ldcg(col + c + 1), xs[(c + 1) * 33 + lane], acc1);
-        }
-        if (c < nb)
-            acc0 = fma(-ldcg(col + c), xs[c * 33 + lane], acc0);
-        Y[(size_t)lane * nb + r] = acc0 + acc1;
-    }
-}
-
 // Row-layout helpers on the first n rows (q blocks of nb x ncp):
 // mode 0: Y -= H; mode 1: Y = H.
 __global__ void k_rows_combine(double *Y, const double *__restrict__ H, int nb, int q, int64_t ncp, int64_t n,
@@ -195,6 +127,26 @@ __global__ void k_rows_combine(double *Y, const double *__restrict__ H, int nb, 
         if (blk * nb + r >= n)
             continue;
         Y[e] = mode == 0 ? Y[e] - H[e] : H[e];
+    }
+}
+
+// The same on buffers of different widths, for the tensor-core form: Y
+// (ncpy columns) over the first q blocks.  mode 0: Y = X - H on the first n
+// rows and ncols columns, 0 elsewhere; mode 1: Y = H there, Y kept elsewhere.
+__global__ void k_rows_combine2(double *Y, int64_t ncpy, const double *__restrict__ X, int64_t ncpx,
+                                const double *__restrict__ H, int64_t ncph, int nb, int q, int64_t n, int64_t ncols,
+                                int mode)
+{
+    const size_t total = (size_t)q * ncpy * nb;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % nb);
+        const int64_t c = (int64_t)((e / nb) % (size_t)ncpy), i = (int64_t)(e / ((size_t)ncpy * nb));
+        const bool in = i * nb + r < n && c < ncols;
+        const double h = in ? H[((size_t)i * ncph + c) * nb + r] : 0.0;
+        if (mode == 0)
+            Y[e] = in ? X[((size_t)i * ncpx + c) * nb + r] - h : 0.0;
+        else if (in)
+            Y[e] = h;
     }
 }
 
@@ -240,13 +192,20 @@ constexpr int64_t ATR_ROWS = 8192;   // rows per partial sum of A^T r
 
 struct LsLayout {
     int64_t ncp, nsplit;
-    size_t Bt, Ct, Wt, sched, flag, Rr, U, DX, DR, W, part, colsq, end;
+    size_t Bt, Ct, Wt, sched, sched2, flag, Rr, U, DX, DR, W, part, colsq, end;
+    // tensor-core form (TILEQR_TF32 factorization, nb 128): the applications
+    // on ncpm = nrhs rounded up to 128 columns, T transposed for Q
+    bool mixed;
+    int64_t ncpm;
+    size_t BtM, CtM, TN, cexpm;
 };
 
 LsLayout ls_layout(const tileqr_desc *d, int64_t nrhs)
 {
-    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib, d->domain);
+    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib, d->domain, d->precision);
     LsLayout S{};
+    S.mixed = d->precision == TILEQR_TF32 && d->nb == 128 && L.off_TF2 > L.off_TF;
+    S.ncpm = ((nrhs + 127) / 128) * 128;
     S.ncp = ((nrhs + APPLY_W - 1) / APPLY_W) * APPLY_W;
     S.nsplit = (d->m + ATR_ROWS - 1) / ATR_ROWS;
     if (S.nsplit < 1)
@@ -260,7 +219,12 @@ LsLayout ls_layout(const tileqr_desc *d, int64_t nrhs)
     S.Wt = off;
     off += align256(rows_q);
     S.sched = off;
-    off += align256(apply_sched_bytes(L, (int)(S.ncp / APPLY_W)));
+    size_t sb = apply_sched_bytes(L, (int)(S.ncp / APPLY_W));
+    if (S.mixed && apply_sched_bytes(L, (int)(S.ncpm / 128)) > sb)
+        sb = apply_sched_bytes(L, (int)(S.ncpm / 128));
+    off += align256(sb);
+    S.sched2 = off;   // the application of Q, so that both report errors
+    off += align256(sb);
     S.flag = off;
     off += 256;
     const size_t mcols = (size_t)d->m * nrhs * 8, ncols = (size_t)d->n * nrhs * 8;
@@ -278,6 +242,17 @@ LsLayout ls_layout(const tileqr_desc *d, int64_t nrhs)
     off += align256((size_t)S.nsplit * ncols);
     S.colsq = off;
     off += align256((size_t)2 * nrhs * 8);
+    if (S.mixed) {
+        const size_t rows_m = (size_t)L.p * L.nb * S.ncpm * 8;
+        S.BtM = off;
+        off += align256(rows_m);
+        S.CtM = off;
+        off += align256(rows_m);
+        S.TN = off;
+        off += align256(mixed_tn_bytes(L));
+        S.cexpm = off;
+        off += align256((size_t)(S.ncpm ? S.ncpm : 1) * sizeof(int));
+    }
     S.end = off;
     return S;
 }
@@ -336,21 +311,16 @@ extern "C" int tileqr_solve_ls_refine(const tileqr_desc *d, const double *A, int
     info->method = 3;
     if (nrhs == 0 || d->n == 0)
         return 0;
-    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib, d->domain);
+    const WsLayout L = make_layout(d->m, d->n, d->nb, d->ib, d->domain, d->precision);
     cudaStream_t st = (cudaStream_t)stream;
     char *ws = (char *)workspace;
     double *Bt = (double *)(ws + S.Bt), *Ct = (double *)(ws + S.Ct), *Wt = (double *)(ws + S.Wt);
-    char *sched = ws + S.sched;
+    char *sched = ws + S.sched, *sched2 = ws + S.sched2;
     int *flag = (int *)(ws + S.flag);
     double *Rr = (double *)(ws + S.Rr), *U = (double *)(ws + S.U), *DR = (double *)(ws + S.DR);
     double *DX = (double *)(ws + S.DX), *W = (double *)(ws + S.W), *part = (double *)(ws + S.part);
     double *colsq = (double *)(ws + S.colsq);
     const int64_t m = d->m, n = d->n, ncp = S.ncp;
-    const int nchunk = (int)(ncp / 32);
-    const size_t tsm = (size_t)L.nb * 33 * sizeof(double);
-    if (kernel_smem_optin((const void *)k_trsmt_diag, 256 * 33 * 8) != 0 ||
-        kernel_smem_optin((const void *)k_trsmt_update, 256 * 33 * 8) != 0)
-        return TILEQR_ERR_CUDA;
     const unsigned long long wd = watchdog_ns_default();
     // x = 0, r = 0: the first step is the plain solve
     for (int64_t k = 0; k < nrhs; k++)
@@ -359,55 +329,90 @@ extern "C" int tileqr_solve_ls_refine(const tileqr_desc *d, const double *A, int
     if (cudaMemsetAsync(Rr, 0, (size_t)m * nrhs * 8, st) != cudaSuccess ||
         cudaMemsetAsync(flag, 0, 256, st) != cudaSuccess)
         return TILEQR_ERR_CUDA;
+    // tensor-core form: the operand blocks of the factorization, T transposed once
+    MixedOperands M;
+    double *BtM = nullptr, *CtM = nullptr;
+    int *cexpm = nullptr;
+    if (S.mixed) {
+        BtM = (double *)(ws + S.BtM);
+        CtM = (double *)(ws + S.CtM);
+        cexpm = (int *)(ws + S.cexpm);
+        const int rcm = mixed_operands(d, L, (unsigned char *)(ws + S.TN), st, &M);
+        if (rcm)
+            return rcm;
+    }
     std::vector<double> prev(nrhs, INFINITY), hsq(2 * nrhs);
     std::vector<char> done(nrhs, 0);
     int rc = 0;
     int it = 0;
     for (it = 1; it <= max_iter; it++) {
-        // u = b - r - A x ;  w = -A^T r (zero while r = 0)
-        k_ls_resid<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(A, lda, m, n, X, ldx, B, ldb, Rr, m, U, m,
-                                                               (int)nrhs);
-        count_launch();
-        if (it > 1) {
+        if (it == 1) {
+            // x = 0, r = 0: u = b and w = 0, so h = 0 (the plain solve)
+            if (cudaMemcpy2DAsync(U, (size_t)m * 8, B, (size_t)ldb * 8, (size_t)m * 8, (size_t)nrhs,
+                                  cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                cudaMemsetAsync(Wt, 0, (size_t)L.q * L.nb * ncp * 8, st) != cudaSuccess)
+                return TILEQR_ERR_CUDA;
+        } else {
+            // u = b - r - A x ;  w = -A^T r
+            k_ls_resid<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(A, lda, m, n, X, ldx, B, ldb, Rr, m, U, m,
+                                                                   (int)nrhs);
             k_ls_atr<<<dim3((unsigned)((n + 7) / 8), (unsigned)S.nsplit), 256, 0, st>>>(A, lda, m, n, Rr, m,
                                                                                        (int)nrhs, ATR_ROWS, part);
             k_ls_atr_reduce<<<152, 256, 0, st>>>(part, (int)S.nsplit, n, (int)nrhs, W);
-            count_launch(2);
-        } else if (cudaMemsetAsync(W, 0, (size_t)n * nrhs * 8, st) != cudaSuccess) {
-            return TILEQR_ERR_CUDA;
+            count_launch(3);
+            // h = R^-T w, in the tile-row layout of the first q blocks
+            if ((rc = launch_cm2rows(W, n, n, nrhs, Wt, L.nb, L.q, ncp, st)) != 0 ||
+                (rc = launch_trsm(L, d->tiles, Wt, ncp, flag, st, true, nrhs)) != 0)
+                return rc;
         }
-        // h = R^-T w, in the tile-row layout of the first q blocks
-        if ((rc = launch_cm2rows(W, n, n, nrhs, Wt, L.nb, L.q, ncp, st)) != 0)
-            return rc;
-        for (int j = 0; j < L.q; j++) {
-            k_trsmt_diag<<<nchunk, NT, tsm, st>>>(d->tiles, Wt, L.nb, L.p, ncp, j, n, flag);
+        if (S.mixed) {
+            // [d1; d2] = Q^T u on the tensor cores; keep a copy for dr
+            const int64_t ncpm = S.ncpm;
+            const size_t rows_m = (size_t)L.p * L.nb * ncpm * 8;
+            if ((rc = launch_cm2rows(U, m, m, nrhs, BtM, L.nb, L.p, ncpm, st)) != 0 ||
+                (rc = launch_rows_cexp(BtM, L.nb, L.p, ncpm, cexpm, st)) != 0 ||
+                (rc = launch_apply_mixed(L, M, BtM, ncpm, cexpm, sched, st, wd, false)) != 0)
+                return rc;
+            if (cudaMemcpyAsync(CtM, BtM, rows_m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return TILEQR_ERR_CUDA;
+            // dx = R^-1 (d1 - h), in the narrow layout of the triangular solves
+            k_rows_combine2<<<4 * 152, 256, 0, st>>>(Bt, ncp, BtM, ncpm, Wt, ncp, L.nb, L.q, n, nrhs, 0);
             count_launch();
-            if (j + 1 < L.q) {
-                k_trsmt_update<<<dim3(L.q - j - 1, nchunk), NT, tsm, st>>>(d->tiles, Wt, L.nb, L.p, ncp, j);
-                count_launch();
-            }
+            if ((rc = launch_trsm(L, d->tiles, Bt, ncp, flag, st, false, nrhs)) != 0)
+                return rc;
+            if ((rc = launch_rows2cm(Bt, L.nb, L.q, ncp, n, nrhs, DX, n, st)) != 0)
+                return rc;
+            // dr = Q [h; d2] on the tensor cores
+            k_rows_combine2<<<4 * 152, 256, 0, st>>>(CtM, ncpm, nullptr, 0, Wt, ncp, L.nb, L.q, n, nrhs, 1);
+            count_launch();
+            if ((rc = launch_rows_cexp(CtM, L.nb, L.p, ncpm, cexpm, st)) != 0 ||
+                (rc = launch_apply_mixed(L, M, CtM, ncpm, cexpm, sched2, st, wd, true)) != 0)
+                return rc;
+            if ((rc = launch_rows2cm(CtM, L.nb, L.p, ncpm, m, nrhs, DR, m, st)) != 0)
+                return rc;
+        } else {
+            // [d1; d2] = Q^T u; keep a copy for dr
+            if ((rc = launch_cm2rows(U, m, m, nrhs, Bt, L.nb, L.p, ncp, st)) != 0)
+                return rc;
+            if ((rc = launch_apply(L, d->tiles, d->T, d->T2, Bt, ncp, sched, st, wd, false)) != 0)
+                return rc;
+            if (cudaMemcpyAsync(Ct, Bt, (size_t)L.p * L.nb * ncp * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return TILEQR_ERR_CUDA;
+            // dx = R^-1 (d1 - h)
+            k_rows_combine<<<4 * 152, 256, 0, st>>>(Bt, Wt, L.nb, L.q, ncp, n, 0);
+            count_launch();
+            if ((rc = launch_trsm(L, d->tiles, Bt, ncp, flag, st, false, nrhs)) != 0)
+                return rc;
+            if ((rc = launch_rows2cm(Bt, L.nb, L.q, ncp, n, nrhs, DX, n, st)) != 0)
+                return rc;
+            // dr = Q [h; d2]
+            k_rows_combine<<<4 * 152, 256, 0, st>>>(Ct, Wt, L.nb, L.q, ncp, n, 1);
+            count_launch();
+            if ((rc = launch_apply(L, d->tiles, d->T, d->T2, Ct, ncp, sched2, st, wd, true)) != 0)
+                return rc;
+            if ((rc = launch_rows2cm(Ct, L.nb, L.p, ncp, m, nrhs, DR, m, st)) != 0)
+                return rc;
         }
-        // [d1; d2] = Q^T u; keep a copy for dr
-        if ((rc = launch_cm2rows(U, m, m, nrhs, Bt, L.nb, L.p, ncp, st)) != 0)
-            return rc;
-        if ((rc = launch_apply(L, d->tiles, d->T, d->T2, Bt, ncp, sched, st, wd, false)) != 0)
-            return rc;
-        if (cudaMemcpyAsync(Ct, Bt, (size_t)L.p * L.nb * ncp * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            return TILEQR_ERR_CUDA;
-        // dx = R^-1 (d1 - h)
-        k_rows_combine<<<4 * 152, 256, 0, st>>>(Bt, Wt, L.nb, L.q, ncp, n, 0);
-        count_launch();
-        if ((rc = launch_trsm(L, d->tiles, Bt, ncp, flag, st)) != 0)
-            return rc;
-        if ((rc = launch_rows2cm(Bt, L.nb, L.q, ncp, n, nrhs, DX, n, st)) != 0)
-            return rc;
-        // dr = Q [h; d2]
-        k_rows_combine<<<4 * 152, 256, 0, st>>>(Ct, Wt, L.nb, L.q, ncp, n, 1);
-        count_launch();
-        if ((rc = launch_apply(L, d->tiles, d->T, d->T2, Ct, ncp, sched, st, wd, true)) != 0)
-            return rc;
-        if ((rc = launch_rows2cm(Ct, L.nb, L.p, ncp, m, nrhs, DR, m, st)) != 0)
-            return rc;
         // x += dx, r += dr
         for (int64_t k = 0; k < nrhs; k++) {
             k_add_cm<<<152, 256, 0, st>>>(X + k * ldx, ldx, DX + k * n, n, n, 1);
@@ -424,12 +429,15 @@ extern "C" int tileqr_solve_ls_refine(const tileqr_desc *d, const double *A, int
             cudaStreamSynchronize(st) != cudaSuccess)
             return TILEQR_ERR_CUDA;
         int hflag = 0;
-        SchedCtrl c;
+        SchedCtrl c, c2;
         if (cudaMemcpy(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(&c, sched, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+            cudaMemcpy(&c, sched, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(&c2, sched2, sizeof(c2), cudaMemcpyDeviceToHost) != cudaSuccess)
             return TILEQR_ERR_CUDA;
         if (c.error)
             return c.error;
+        if (c2.error)
+            return c2.error;
         if (hflag)
             return TILEQR_ERR_SINGULAR;
         // per column: stop once the correction is negligible or no longer

@@ -570,7 +570,7 @@ extern "C" int tileqr_lu_solve(const tileqr_desc *d, double *B, int64_t ldb, int
     if (rc)
         return rc;
     const WsLayout W = make_layout(d->n, d->n, d->nb, d->ib, 0);
-    rc = launch_trsm(W, d->tiles, Bt, ncp, flag, st);
+    rc = launch_trsm(W, d->tiles, Bt, ncp, flag, st, false, nrhs);
     if (rc)
         return rc;
     rc = launch_rows2cm(Bt, d->nb, d->p, ncp, d->n, nrhs, B, ldb, st);

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(NT, 1) k_mixed_update_one(const double *V, con
     mixed_build_tfull<S, VK>(smb, V, Tstrip, TF);
     __syncthreads();
     uint32_t phase = 0;
-    task_update_mixed_tf<S, VK>(smb, B, C, V, TF, cexp, lm, tmem, s_mbar, phase, err);
+    task_update_mixed_tf<S, VK>(smb, B, C, TF, TF + TF_OFF_T, cexp, lm, tmem, s_mbar, phase, err);
     tc::fence_before_sync();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0)
@@ -94,9 +94,9 @@ extern "C" int tileqr_mixed_update_tile(int kind, int ib, const double *V, const
         return -3;
     if (T == nullptr)
         return -4;
-    if (kind == TILEQR_UPDATE_SSRFB && B == nullptr)
+    if (kind == TILEQR_UPDATE_SSRFB && (B == nullptr || ((uintptr_t)B & 15) != 0))
         return -5;
-    if (C == nullptr)
+    if (C == nullptr || ((uintptr_t)C & 15) != 0)
         return -6;
     if (workspace == nullptr || ((uintptr_t)workspace & 255) != 0 || ws_bytes < TILEQR_MIXED_UPDATE_WS_BYTES)
         return TILEQR_ERR_WORKSPACE;

@@ -333,6 +333,10 @@ __device__ __noinline__ void mixed_build_tfull(unsigned char *smb, const double 
 // mixed_build_tfull; the copy engine brings their chunks into shared memory,
 // cp.async.bulk completing on mbar[2 + set]):
 //   P = V^T C;  W = T^T (B + P);  B -= W;  D = V W;  C -= D
+// TFg is the tile pair's operand block (V^T and V are read from it) and TW
+// the A operand of W: T^T (TFg + TF_OFF_T) for the factorization and Q^T B,
+// or T pre-split the same way (k_tf_transpose) for Q B, whose blocks apply
+// I - V T V^T instead of its transpose.
 // three 128 x 128 x 128 3xTF32 products with FP32 accumulation in tensor
 // memory (P and D in columns 0..127, W in 128..255), each in 4 K-chunks of
 // 32 on double-buffered operands.  Shared memory: R1 (128 KB) holds the two
@@ -348,8 +352,8 @@ constexpr size_t TF_UPDATE_SMEM = 192 * 1024;
 constexpr size_t TF_UPDATE_SMEM_TOTAL = TF_UPDATE_SMEM + 128 * sizeof(int);
 
 template <int S, int VK>
-__device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt, double *Ct, const double *Vt,
-                                                  const unsigned char *TFg, const int *cex, int lm, uint32_t tmem,
+__device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt, double *Ct, const unsigned char *TFg,
+                                                  const unsigned char *TW, const int *cex, int lm, uint32_t tmem,
                                                   uint64_t *mbar, uint32_t &phase, int *err)
 {
     constexpr int NB = 128, KC = 32, OPB = NB * KC * 4, R2 = 8 * OPB;
@@ -398,12 +402,12 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     // mbar[1] completes two phases here, which thread 0 waits in order; the
     // other threads skip both and keep their parity bits, which two phases
     // leave unchanged.  Returns thread 0's wait outcome.
-    auto stream_product = [&](uint32_t d, uint32_t toff) {
+    auto stream_product = [&](uint32_t d, const unsigned char *src) {
         bool r = true;
         if (tid == 0) {
             tc::fence_after_sync();
             for (int kk = 0; kk < 2; kk++)
-                load_chunk(sm + R2 + kk * 2 * OPB, TFg + toff + (size_t)kk * TF_CHUNK_BYTES, kk);
+                load_chunk(sm + R2 + kk * 2 * OPB, src + (size_t)kk * TF_CHUNK_BYTES, kk);
             for (int kk = 0; kk < NB / KC; kk++) {
                 const int b = kk & 1;
                 r &= load_wait(b);
@@ -411,14 +415,15 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
                 tc::commit(&mbar[b]);
                 r &= mixed_wait(mbar, phase, b);
                 if (kk + 2 < NB / KC)
-                    load_chunk(sm + R2 + b * 2 * OPB, TFg + toff + (size_t)(kk + 2) * TF_CHUNK_BYTES, b);
+                    load_chunk(sm + R2 + b * 2 * OPB, src + (size_t)(kk + 2) * TF_CHUNK_BYTES, b);
             }
             tc::fence_before_sync();
         }
         return r;
     };
     // the copies need 16-byte aligned addresses: checked once per task
-    if (((sbase | (uint32_t)(uintptr_t)TFg) & 15u) != 0u) {
+    if (((sbase | (uint32_t)(uintptr_t)TFg | (uint32_t)(uintptr_t)TW | (uint32_t)(uintptr_t)Ct |
+          (uint32_t)(uintptr_t)Bt) & 15u) != 0u) {
         if (tid == 0)
             atomicCAS(err, 0, TILEQR_ERR_CUDA);
         return false;
@@ -464,7 +469,7 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         tc::prefetch_l2(Ct, NB * NB * 8);
         if (Bt)
             tc::prefetch_l2(Bt, NB * NB * 8);
-        tc::prefetch_l2(TFg + TF_OFF_T, TF_BYTES);
+        tc::prefetch_l2(TW, TF_BYTES);
         tc::prefetch_l2(TFg + TF_OFF_V, TF_BYTES);
     }
     int *sh = (int *)(sm + TF_UPDATE_SMEM);   // column shifts of the updated tile column
@@ -541,7 +546,7 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     tc::fence_async_smem();
     __syncthreads();   // every warp is done with its scratch in R2
     // ---- W = T^T Y: A = T^T chunks, copied from the panel's pre-split operand
-    ok &= stream_product(tmem + 128, TF_OFF_T);
+    ok &= stream_product(tmem + 128, TW);
     if (!__syncthreads_and(ok))
         return fail();
     tc::fence_after_sync();
@@ -566,7 +571,7 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     __syncthreads();   // every warp is done with its scratch in R2
     // ---- D = V W: A = V (row = tile row, K = reflector) chunks, copied from
     // the panel's pre-split operand into R2
-    ok &= stream_product(tmem, TF_OFF_V);
+    ok &= stream_product(tmem, TFg + TF_OFF_V);
     if (!__syncthreads_and(ok))
         return fail();
     tc::fence_after_sync();

@@ -44,6 +44,7 @@ EXPORTED = [
     "tileqr_lu_solve_workspace_size", "tileqr_lu_solve", "tileqr_mixed_update_tile",
     "tileqr_ls_refine_workspace_size", "tileqr_solve_ls_refine",
     "tileqr_batched_ls_workspace_size", "tileqr_batched_solve_ls", "tileqr_measure_fp64_rates",
+    "tileqr_apply_mixed_workspace_size", "tileqr_apply_mixed",
 ]
 
 
@@ -108,6 +109,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tileqr_get_factors": (i32, [dp, vp, i64, vp, i64, vp]),
         "tileqr_apply_workspace_size": (i32, [dp, i64, ctypes.POINTER(sz)]),
         "tileqr_apply_qt": (i32, [dp, vp, i64, i64, vp, sz, vp]),
+        "tileqr_apply_mixed_workspace_size": (i32, [dp, i64, ctypes.POINTER(sz)]),
+        "tileqr_apply_mixed": (i32, [dp, i32, vp, i64, i64, vp, sz, vp]),
         "tileqr_solve_ls": (i32, [dp, vp, i64, i64, vp, sz, vp]),
         "tileqr_strerror": (ctypes.c_char_p, [i32]),
         "tileqr_launch_count": (ctypes.c_uint64, []),
@@ -475,6 +478,20 @@ class Factorization:
         _check(load().tileqr_apply_q(ctypes.byref(self.desc), ctypes.c_void_p(B.data_ptr()), _ld(B), B.shape[1],
                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)),
                "tileqr_apply_q")
+        return B
+
+    def apply_mixed(self, B: torch.Tensor, trans: bool = True, stream=None) -> torch.Tensor:
+        """Q^T B (trans) or Q B on the tensor cores, in place, for a
+        TILEQR_TF32 factorization with nb 128 (3xTF32: about 2^-19 relative
+        per column, not FP64); synchronous; returns B."""
+        B = as_colmajor(B)
+        out = ctypes.c_size_t(0)
+        _check(load().tileqr_apply_mixed_workspace_size(ctypes.byref(self.desc), B.shape[1], ctypes.byref(out)),
+               "tileqr_apply_mixed_workspace_size")
+        ws = torch.empty(max(out.value, 256), dtype=torch.uint8, device=self.device)
+        _check(load().tileqr_apply_mixed(ctypes.byref(self.desc), 1 if trans else 0, ctypes.c_void_p(B.data_ptr()),
+                                         _ld(B), B.shape[1], ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                         _stream_ptr(stream)), "tileqr_apply_mixed")
         return B
 
     def form_q(self, ncols: int | None = None, stream=None) -> torch.Tensor:
