@@ -421,8 +421,12 @@ int tileqr_batched_solve_ls(const tileqr_batch *bt, const double *const *B, doub
  * [d1; d2] = Q^T u (the DLARFB / DSSRFB graph of Sec. 3.2.1),
  * dx = R^-1 (d1 - h), dr = Q [h; d2] (the same graph reversed); x += dx,
  * r += dr.  It starts from x = 0, r = 0, so the first step is the plain
- * solve of tileqr_solve_ls.  A column stops when ||dx|| <= tol ||x|| or when
- * ||dx|| no longer halves (the rounding level of the FP64 residuals).
+ * solve of tileqr_solve_ls.  For a TILEQR_TF32 factorization with nb 128
+ * the two applications of Q run on the tensor cores as in
+ * tileqr_apply_mixed (they only form corrections; the residuals are FP64).
+ * A column stops when ||dx|| <= tol ||x||, when ||dx|| no longer halves (the
+ * rounding level of the FP64 residuals), or when the rate of its last two
+ * steps puts the next correction below tol ||x||.
  *   A, lda    the original matrix (device, column-major, FP64)
  *   B, ldb    device m x nrhs right-hand sides (not modified)
  *   X, ldx    device n x nrhs solution (output)

@@ -476,7 +476,7 @@ extern "C" int tileqr_apply_mixed(const tileqr_desc *d, int trans, double *B, in
     if (rc == 0)
         rc = launch_rows_cexp(Bt, d->nb, d->p, ncp, cexp, st);
     if (rc == 0)
-        rc = launch_apply_mixed(L, M, Bt, ncp, cexp, sched, st, watchdog_ns_default(), trans == 0);
+        rc = launch_apply_mixed(L, M, Bt, ncp, nrhs, cexp, sched, st, watchdog_ns_default(), trans == 0);
     if (rc == 0)
         rc = launch_rows2cm(Bt, d->nb, d->p, ncp, d->m, nrhs, B, ldb, st);
     if (rc)

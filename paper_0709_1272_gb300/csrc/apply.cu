@@ -36,6 +36,7 @@ struct ApplyArgs {
     size_t tw_stride, tw_off;
     const int *cexp;
     int lm;
+    int64_t ncols;   // live columns of Bt (the rest of its ncp are zero)
 };
 
 template <int NB, int S, int CW = APPLY_W>
@@ -111,17 +112,19 @@ __global__ void __launch_bounds__(NT, 1) k_apply_dag(ApplyArgs A, Queues Q)
             const unsigned char *tw = (tt ? A.TW2 : A.TW) + pi * A.tw_stride + A.tw_off;
             const int *cx = A.cexp + (size_t)cb * NB;
             int *err = &Q.ctrl->error;
+            const int64_t left = A.ncols - (int64_t)cb * NB;
+            const int nl = left < NB ? (int)left : NB;
             if (kind == K_LARFB)
-                task_update_mixed_tf<S, VK_UNIT>(smb, nullptr, chunk_ptr<NB, S, CW>(A, i, cb), pair, tw, cx, A.lm,
-                                                 tmem, s_mbar, mphase, err);
+                task_update_mixed_tf<S, VK_UNIT, true>(smb, nullptr, chunk_ptr<NB, S, CW>(A, i, cb), pair, tw, cx, A.lm,
+                                                 tmem, s_mbar, mphase, err, nl);
             else if (kind == K_SSRFB)
-                task_update_mixed_tf<S, VK_FULL>(smb, chunk_ptr<NB, S, CW>(A, g_head(G, k, g_dom(G, k, i)), cb),
+                task_update_mixed_tf<S, VK_FULL, true>(smb, chunk_ptr<NB, S, CW>(A, g_head(G, k, g_dom(G, k, i)), cb),
                                                  chunk_ptr<NB, S, CW>(A, i, cb), pair, tw, cx, A.lm, tmem, s_mbar,
-                                                 mphase, err);
+                                                 mphase, err, nl);
             else
-                task_update_mixed_tf<S, VK_UPPER>(smb, chunk_ptr<NB, S, CW>(A, g_partner(G, k, i), cb),
+                task_update_mixed_tf<S, VK_UPPER, true>(smb, chunk_ptr<NB, S, CW>(A, g_partner(G, k, i), cb),
                                                   chunk_ptr<NB, S, CW>(A, i, cb), pair, tw, cx, A.lm, tmem, s_mbar,
-                                                  mphase, err);
+                                                  mphase, err, nl);
         } else {
             const double *Vt = A.tiles + ((size_t)k * A.p + i) * (size_t)NB * NB;
             const size_t strip = ((size_t)k * A.p + i) * (size_t)S * NB;
@@ -249,7 +252,7 @@ static int launch_apply_t(const WsLayout &L, const double *tiles, const double *
 }
 
 template <int S, bool NOTRANS>
-static int launch_apply_mixed_t(const WsLayout &L, const MixedOperands &M, double *Bt, int64_t ncp,
+static int launch_apply_mixed_t(const WsLayout &L, const MixedOperands &M, double *Bt, int64_t ncp, int64_t ncols,
                                 const int *cexp, char *sched, cudaStream_t st, unsigned long long watchdog_ns)
 {
     constexpr size_t smem = TF_UPDATE_SMEM_TOTAL;
@@ -279,6 +282,7 @@ static int launch_apply_mixed_t(const WsLayout &L, const MixedOperands &M, doubl
     }
     A.cexp = cexp;
     A.lm = ceil_log2_sqrt((int64_t)L.p * L.nb);
+    A.ncols = ncols;
     Queues Q;
     if (apply_queues(L, A.nchunk, sched, watchdog_ns, Q) == 0)
         return 0;
@@ -292,10 +296,10 @@ static int launch_apply_mixed_t(const WsLayout &L, const MixedOperands &M, doubl
     return cudaGetLastError() == cudaSuccess ? 0 : TILEQR_ERR_CUDA;
 }
 
-int launch_apply_mixed(const WsLayout &L, const MixedOperands &M, double *Bt, int64_t ncp, const int *cexp,
-                       char *sched, cudaStream_t st, unsigned long long watchdog_ns, bool notrans)
+int launch_apply_mixed(const WsLayout &L, const MixedOperands &M, double *Bt, int64_t ncp, int64_t ncols,
+                       const int *cexp, char *sched, cudaStream_t st, unsigned long long watchdog_ns, bool notrans)
 {
-    if (L.nb != 128 || ncp % 128 != 0 || M.TF == nullptr || (L.H < L.p && M.TF2 == nullptr) ||
+    if (L.nb != 128 || ncp % 128 != 0 || ncols < 0 || ncols > ncp || M.TF == nullptr || (L.H < L.p && M.TF2 == nullptr) ||
         (notrans && (M.TN == nullptr || (L.H < L.p && M.TN2 == nullptr))))
         return TILEQR_ERR_UNSUPPORTED;
     if (kernel_smem_optin((const void *)k_apply_dag<128, 16, false, true>, TF_UPDATE_SMEM_TOTAL) ||
@@ -304,11 +308,11 @@ int launch_apply_mixed(const WsLayout &L, const MixedOperands &M, double *Bt, in
         kernel_smem_optin((const void *)k_apply_dag<128, 32, true, true>, TF_UPDATE_SMEM_TOTAL))
         return TILEQR_ERR_CUDA;
     if (L.ib == 16)
-        return notrans ? launch_apply_mixed_t<16, true>(L, M, Bt, ncp, cexp, sched, st, watchdog_ns)
-                       : launch_apply_mixed_t<16, false>(L, M, Bt, ncp, cexp, sched, st, watchdog_ns);
+        return notrans ? launch_apply_mixed_t<16, true>(L, M, Bt, ncp, ncols, cexp, sched, st, watchdog_ns)
+                       : launch_apply_mixed_t<16, false>(L, M, Bt, ncp, ncols, cexp, sched, st, watchdog_ns);
     if (L.ib == 32)
-        return notrans ? launch_apply_mixed_t<32, true>(L, M, Bt, ncp, cexp, sched, st, watchdog_ns)
-                       : launch_apply_mixed_t<32, false>(L, M, Bt, ncp, cexp, sched, st, watchdog_ns);
+        return notrans ? launch_apply_mixed_t<32, true>(L, M, Bt, ncp, ncols, cexp, sched, st, watchdog_ns)
+                       : launch_apply_mixed_t<32, false>(L, M, Bt, ncp, ncols, cexp, sched, st, watchdog_ns);
     return TILEQR_ERR_UNSUPPORTED;
 }
 

@@ -59,12 +59,13 @@ int launch_apply(const WsLayout &L, const double *tiles, const double *T, const 
 // chunks of 128 (ncp a multiple of 128), with the operands the factorization
 // kept per tile pair (TF; TF2 for the tree merges) and, for Q B (notrans),
 // T itself pre-split (TN, TN2, from launch_tf_transpose).  cexp: the largest
-// biased exponent of every column of Bt (launch_rows_cexp).
+// biased exponent of every column of Bt (launch_rows_cexp); only its first
+// ncols columns are live (the rest zero), the others are skipped.
 struct MixedOperands {
     const unsigned char *TF = nullptr, *TF2 = nullptr, *TN = nullptr, *TN2 = nullptr;
 };
-int launch_apply_mixed(const WsLayout &L, const MixedOperands &M, double *Bt, int64_t ncp, const int *cexp,
-                       char *sched, cudaStream_t st, unsigned long long watchdog_ns, bool notrans);
+int launch_apply_mixed(const WsLayout &L, const MixedOperands &M, double *Bt, int64_t ncp, int64_t ncols,
+                       const int *cexp, char *sched, cudaStream_t st, unsigned long long watchdog_ns, bool notrans);
 // dst pair t (TF_BYTES apart) <- T of src pair t (src_stride apart, T^T at
 // TF_OFF_T), pre-split the same way.
 int launch_tf_transpose(const unsigned char *src, size_t src_stride, unsigned char *dst, size_t npairs,

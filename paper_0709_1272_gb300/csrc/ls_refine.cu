@@ -371,7 +371,7 @@ extern "C" int tileqr_solve_ls_refine(const tileqr_desc *d, const double *A, int
             const size_t rows_m = (size_t)L.p * L.nb * ncpm * 8;
             if ((rc = launch_cm2rows(U, m, m, nrhs, BtM, L.nb, L.p, ncpm, st)) != 0 ||
                 (rc = launch_rows_cexp(BtM, L.nb, L.p, ncpm, cexpm, st)) != 0 ||
-                (rc = launch_apply_mixed(L, M, BtM, ncpm, cexpm, sched, st, wd, false)) != 0)
+                (rc = launch_apply_mixed(L, M, BtM, ncpm, nrhs, cexpm, sched, st, wd, false)) != 0)
                 return rc;
             if (cudaMemcpyAsync(CtM, BtM, rows_m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
                 return TILEQR_ERR_CUDA;
@@ -386,7 +386,7 @@ extern "C" int tileqr_solve_ls_refine(const tileqr_desc *d, const double *A, int
             k_rows_combine2<<<4 * 152, 256, 0, st>>>(CtM, ncpm, nullptr, 0, Wt, ncp, L.nb, L.q, n, nrhs, 1);
             count_launch();
             if ((rc = launch_rows_cexp(CtM, L.nb, L.p, ncpm, cexpm, st)) != 0 ||
-                (rc = launch_apply_mixed(L, M, CtM, ncpm, cexpm, sched2, st, wd, true)) != 0)
+                (rc = launch_apply_mixed(L, M, CtM, ncpm, nrhs, cexpm, sched2, st, wd, true)) != 0)
                 return rc;
             if ((rc = launch_rows2cm(CtM, L.nb, L.p, ncpm, m, nrhs, DR, m, st)) != 0)
                 return rc;
@@ -440,14 +440,17 @@ extern "C" int tileqr_solve_ls_refine(const tileqr_desc *d, const double *A, int
             return c2.error;
         if (hflag)
             return TILEQR_ERR_SINGULAR;
-        // per column: stop once the correction is negligible or no longer
-        // halves (the rounding level of the FP64 residuals)
+        // per column: stop once the correction is negligible, or no longer
+        // halves (the rounding level of the FP64 residuals), or once the
+        // linear rate of the last two steps puts the next correction below
+        // tol (the error left in x is about that next correction)
         double worst = 0.0;
         bool all = true;
         for (int64_t k = 0; k < nrhs; k++) {
             const double ndx = std::sqrt(hsq[k]), nx = std::sqrt(hsq[nrhs + k]);
             const double ratio = nx > 0.0 ? ndx / nx : ndx;
-            if (it > 1 && !done[k] && (ratio <= tol || ndx > 0.5 * prev[k]))
+            const bool predicted = it > 2 && ndx <= 0.5 * prev[k] && ratio * (ndx / prev[k]) <= tol;
+            if (it > 1 && !done[k] && (ratio <= tol || ndx > 0.5 * prev[k] || predicted))
                 done[k] = 1;
             if (it > 1)
                 worst = ratio > worst ? ratio : worst;

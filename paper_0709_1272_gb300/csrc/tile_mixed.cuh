@@ -345,16 +345,20 @@ __device__ __noinline__ void mixed_build_tfull(unsigned char *smb, const double 
 // double-buffered A operand of those (T^T chunks, then V chunks), and before
 // each a per-warp transpose scratch for staging Y and W^T.  Returns
 // false on a tensor-core wait timeout (an error is recorded).
+// PARTIAL: only the first nlive columns of B and C are live (the rest are
+// zero and stay zero, e.g. the padding of right-hand sides): the threads
+// skip the 32-column blocks past them; the products still run on all 128
+// columns, whose dead ones only reach dead columns of P, W and D.
 // B and C enter the products scaled per column by 2^-s_c (the column
 // shifts of common.cuh, staged after the operand areas), and W and D leave
 // them scaled back, so any magnitude of A stays within FP32's range.
 constexpr size_t TF_UPDATE_SMEM = 192 * 1024;
 constexpr size_t TF_UPDATE_SMEM_TOTAL = TF_UPDATE_SMEM + 128 * sizeof(int);
 
-template <int S, int VK>
+template <int S, int VK, bool PARTIAL = false>
 __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt, double *Ct, const unsigned char *TFg,
                                                   const unsigned char *TW, const int *cex, int lm, uint32_t tmem,
-                                                  uint64_t *mbar, uint32_t &phase, int *err)
+                                                  uint64_t *mbar, uint32_t &phase, int *err, int nlive = 128)
 {
     constexpr int NB = 128, KC = 32, OPB = NB * KC * 4, R2 = 8 * OPB;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -490,7 +494,9 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         for (int x = 0; x < 4; x++) {
             const int m = p_row(x), j = p_kgrp(x), r = rr * KC + 4 * j;
             const double2 *cp = (const double2 *)(Ct + (size_t)m * NB + r);
-            const double2 c01 = __ldcg(cp), c23 = __ldcg(cp + 1);
+            const bool live = !PARTIAL || m < nlive;
+            const double2 c01 = live ? __ldcg(cp) : make_double2(0.0, 0.0);
+            const double2 c23 = live ? __ldcg(cp + 1) : make_double2(0.0, 0.0);
             c[x][0] = c01.x;
             c[x][1] = c01.y;
             c[x][2] = c23.x;
@@ -509,6 +515,8 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
             load_c(rr + 1, cn);
 #pragma unroll
         for (int x = 0; x < 4; x++) {
+            if (PARTIAL && p_row(x) >= nlive)
+                continue;
             const uint32_t off = tc::kmajor_off(p_row(x), 4 * p_kgrp(x), KC);
             const int sc = sh[p_row(x)];
             store_split4(sm, so + 2 * OPB, so + 3 * OPB, off, f64_to_f32_sc(cc[x][0], sc),
@@ -532,6 +540,8 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     // ---- Y = P + B into R1 as the B operand of W = T^T Y (row c, K = reflector)
     for (int h = 0; h < 2; h++) {
         const int c0 = cbase + 32 * h;
+        if (PARTIAL && c0 >= nlive)   // warp-uniform
+            continue;
         float v[32];
         double bv[32];
 #pragma unroll
@@ -554,6 +564,8 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     // ---- B -= W (FP64); W^T into R1 as the B operand of D = V W
     for (int h = 0; h < 2; h++) {
         const int c0 = cbase + 32 * h;
+        if (PARTIAL && c0 >= nlive)
+            continue;
         float w[32];
         tc::tmem_ld32(tmem + 128 + lane_off + c0, w);
         if (Bt) {
@@ -579,6 +591,8 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     // ---- C -= D (FP64), row = tensor-memory lane
     for (int h = 0; h < 2; h++) {
         const int c0 = cbase + 32 * h;
+        if (PARTIAL && c0 >= nlive)
+            continue;
         float v[32];
         double old[32];
 #pragma unroll
