@@ -24,6 +24,9 @@ struct FactorArgs {
     const int *cexp;
     int lm;
     int p, q, steps;
+    // the matrix's columns in the last tile column and rows in the last tile
+    // row (1..nb); the FP64 updates skip the zero padding past them
+    int ncl, nrl;
     TGraph G;
 };
 
@@ -102,7 +105,12 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
                                              tf_ptr(F.TF, F.p, i, k) + TF_OFF_T, cexp_ptr<NB>(F, j), F.lm, tmem,
                                              mbar, mphase, err);
         } else {
-            task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
+            if (j == F.q - 1 && F.ncl < NB)
+                task_larfb<NB, S, FactorW<NB>::value, false, true>(sm, tile_ptr<NB, S>(F, i, j),
+                                                                   tile_ptr<NB, S>(F, i, k),
+                                                                   strip_ptr<NB, S>(F, i, k), F.ncl);
+            else
+                task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
         }
         break;
     case K_SSRFB: {
@@ -112,8 +120,13 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
                                              tf_ptr(F.TF, F.p, i, k) + TF_OFF_T, cexp_ptr<NB>(F, j), F.lm, tmem,
                                              mbar, mphase, err);
         } else {
-            task_ssrfb<NB, S>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
-                              strip_ptr<NB, S>(F, i, k));
+            if ((j == F.q - 1 && F.ncl < NB) || (i == F.p - 1 && F.nrl < NB))
+                task_ssrfb_edge<NB, S>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                       strip_ptr<NB, S>(F, i, k), j == F.q - 1 ? F.ncl : NB,
+                                       i == F.p - 1 ? F.nrl : NB);
+            else
+                task_ssrfb<NB, S>(sm, top, tile_ptr<NB, S>(F, i, j), tile_ptr<NB, S>(F, i, k),
+                                  strip_ptr<NB, S>(F, i, k));
         }
         break;
     }
@@ -350,6 +363,8 @@ __global__ void __launch_bounds__(NT, (DagCfg<NB, S, MIXED>::CTAS_PER_SM))
             s_F.p = mi.p;
             s_F.q = mi.q;
             s_F.steps = mi.steps;
+            s_F.ncl = (int)(mi.n - (int64_t)(mi.q - 1) * NB);
+            s_F.nrl = (int)(mi.m - (int64_t)(mi.p - 1) * NB);
             s_F.G = make_graph(mi.p, mi.q, 0);
             s_cnt = mi.cnt_off;
         }

@@ -77,6 +77,8 @@ static int launch_factor_t(const WsLayout &L, char *ws, int schedule, int flags,
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;
+    F.ncl = (int)(L.n - (int64_t)(L.q - 1) * L.nb);
+    F.nrl = (int)(L.m - (int64_t)(L.p - 1) * L.nb);
     F.G = make_graph(L.p, L.q, L.H);
     if (schedule == TILEQR_SCHED_DAG) {
         Queues Q;
@@ -165,6 +167,8 @@ static int launch_factor_dag_at_t(const WsLayout &L, double *tiles, double *T, c
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;
+    F.ncl = (int)(L.n - (int64_t)(L.q - 1) * L.nb);
+    F.nrl = (int)(L.m - (int64_t)(L.p - 1) * L.nb);
     F.G = make_graph(L.p, L.q, 0);
     Queues Q;
     Q.ctrl = (SchedCtrl *)sched;

@@ -36,6 +36,8 @@ static int launch_factor_mixed_t(const WsLayout &L, char *ws, int flags, cudaStr
     F.p = L.p;
     F.q = L.q;
     F.steps = L.steps;
+    F.ncl = (int)(L.n - (int64_t)(L.q - 1) * L.nb);
+    F.nrl = (int)(L.m - (int64_t)(L.p - 1) * L.nb);
     F.G = make_graph(L.p, L.q, L.H);
     Queues Q;
     Q.ctrl = (SchedCtrl *)(ws + L.off_ctrl);

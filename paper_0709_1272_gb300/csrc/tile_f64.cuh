@@ -253,14 +253,20 @@ __device__ __forceinline__ void stage_t(double *sm, const double *Tt, int l0)
 // ---------------------------------------------------------------------------
 // DSSRFB (Sec. 3.2.1): [Bt; Ct] <- Q^T [Bt; Ct] with Q = H_1..H_nb from the
 // DTSQRT reflectors in Vt and the T strip Tt, blocks l = 0..t-1 in order.
-// ncols: columns of Bt/Ct to update (tile ld is NB); the factorization
-// passes NB, the Q^T application the width of its column chunk.
+// ncols: columns of Bt/Ct to update (tile ld is NB): the factorization
+// passes the matrix's columns in the tile (the rest is zero padding, which
+// the update would leave zero), the Q^T application the width of its column
+// chunk.  ROWS (task_ssrfb_edge): only the first nrows rows of Ct (and of
+// the reflectors in Vt) are inside the matrix; the rows past them are zero in
+// both, so the products skip them.  The factorization calls the full tile
+// and the matrix's ragged edge through separate functions, so the full-tile
+// update keeps its registers.
 // TRI (DTTMQR of the tree form): the reflectors are the upper triangle of
 // Vt, so block l reaches only rows < l0 + S of Ct.
 // NOTRANS: apply Q itself (the inner blocks in reverse order, each with T_l).
-template <int NB, int S, int W_ = FactorW<NB>::value, bool TRI = false, bool NOTRANS = false>
-__device__ __noinline__ void task_ssrfb(double *sm, double *Bt, double *Ct, const double *Vt, const double *Tt,
-                           int ncols = NB)
+template <int NB, int S, int W_, bool TRI, bool NOTRANS, bool ROWS>
+__device__ __forceinline__ void ssrfb_body(double *sm, double *Bt, double *Ct, const double *Vt, const double *Tt,
+                                           int ncols, int nrows)
 {
     using C_ = F64Cfg<NB, S, W_>;
     for (int c0 = 0; c0 < ncols; c0 += C_::W) {
@@ -274,16 +280,33 @@ __device__ __noinline__ void task_ssrfb(double *sm, double *Bt, double *Ct, cons
                 stage_v_full<NB, S, W_>(sm, Vt, l0);
             stage_t<NB, S, W_>(sm, Tt, l0);
             __syncthreads();
-            apply_block<NB, S, W_, NOTRANS>(sm, Bt + (size_t)c0 * NB + l0, 0, nc, TRI ? l0 + S : NB);
+            apply_block<NB, S, W_, NOTRANS>(sm, Bt + (size_t)c0 * NB + l0, 0, nc,
+                                            TRI ? l0 + S : (ROWS ? nrows : NB));
         }
         store_chunk<NB, S, W_>(sm, Ct, c0, nc, 0);
         __syncthreads();
     }
 }
+template <int NB, int S, int W_ = FactorW<NB>::value, bool TRI = false, bool NOTRANS = false>
+__device__ __noinline__ void task_ssrfb(double *sm, double *Bt, double *Ct, const double *Vt, const double *Tt,
+                           int ncols = NB)
+{
+    ssrfb_body<NB, S, W_, TRI, NOTRANS, false>(sm, Bt, Ct, Vt, Tt, ncols, NB);
+}
+// The matrix's ragged edge: ncols < NB columns and / or nrows < NB rows of
+// Ct (and of the reflectors) inside the matrix.
+template <int NB, int S>
+__device__ __noinline__ void task_ssrfb_edge(double *sm, double *Bt, double *Ct, const double *Vt, const double *Tt,
+                                             int ncols, int nrows)
+{
+    ssrfb_body<NB, S, FactorW<NB>::value, false, false, true>(sm, Bt, Ct, Vt, Tt, ncols, nrows);
+}
 
 // DLARFB (Sec. 3.2.1): Ct <- Q^T Ct with the DGEQRT reflectors of the
 // diagonal tile Vt (unit lower) and its T strip.
-template <int NB, int S, int W_ = FactorW<NB>::value, bool NOTRANS = false>
+// EDGE: a separate instance for the matrix's ragged last tile column (ncols
+// < NB), so the full-tile instance keeps constant arguments.
+template <int NB, int S, int W_ = FactorW<NB>::value, bool NOTRANS = false, bool EDGE = false>
 __device__ __noinline__ void task_larfb(double *sm, double *Ct, const double *Vt, const double *Tt,
                            int ncols = NB)
 {
