@@ -79,9 +79,14 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
             }
         break;
     case K_TSQRT:
-        task_tsqrt<NB, S, MIXED, false>(sm, tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), k),
-                                        tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), cexp_ptr<NB>(F, k),
-                                        F.lm);
+        if (!MIXED && i == F.p - 1 && F.nrl < NB)
+            task_tsqrt<NB, S, false, false, true>(sm, tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), k),
+                                                  tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), nullptr, 0,
+                                                  F.nrl);
+        else
+            task_tsqrt<NB, S, MIXED, false>(sm, tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), k),
+                                            tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), cexp_ptr<NB>(F, k),
+                                            F.lm);
         if constexpr (MIXED)
             {
                 __syncthreads();

@@ -12,27 +12,32 @@ namespace tqr {
 // Fork-join comparator: per step k the host launches GEQRT, then the LARFB
 // row, then the TSQRT chain (one CTA, serial in i), then one CTA per column j
 // running its SSRFB chain over i.  Each launch waits for the previous one.
+// The tasks run through run_task, the same tile kernels (and ragged-edge
+// instances) as the task graph, so both schedules give the same bits.
+template <int NB, int S>
+__device__ __forceinline__ void bulk_task(double *sm, const FactorArgs &F, int kind, int k, int i, int j)
+{
+    uint32_t mphase = 0;
+    run_task<NB, S, false>(sm, F, kind, k, i, j, 0u, nullptr, mphase, nullptr);
+}
 template <int NB, int S>
 __global__ void __launch_bounds__(NT, 1) k_bulk_geqrt(FactorArgs F, int k)
 {
     extern __shared__ double sm[];
-    task_geqrt<NB, S>(sm, tile_ptr<NB, S>(F, k, k), strip_ptr<NB, S>(F, k, k));
+    bulk_task<NB, S>(sm, F, K_GEQRT, k, k, k);
 }
 template <int NB, int S>
 __global__ void __launch_bounds__(NT, 1) k_bulk_larfb(FactorArgs F, int k)
 {
     extern __shared__ double sm[];
-    const int j = k + 1 + blockIdx.x;
-    task_larfb<NB, S>(sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, k, k),
-                      strip_ptr<NB, S>(F, k, k));
+    bulk_task<NB, S>(sm, F, K_LARFB, k, k, k + 1 + (int)blockIdx.x);
 }
 template <int NB, int S>
 __global__ void __launch_bounds__(NT, 1) k_bulk_tsqrt(FactorArgs F, int k)
 {
     extern __shared__ double sm[];
     for (int i = k + 1; i < F.p; i++) {
-        task_tsqrt<NB, S>(sm, tile_ptr<NB, S>(F, k, k), tile_ptr<NB, S>(F, i, k),
-                          strip_ptr<NB, S>(F, i, k));
+        bulk_task<NB, S>(sm, F, K_TSQRT, k, i, k);
         __syncthreads();
     }
 }
@@ -42,8 +47,7 @@ __global__ void __launch_bounds__(NT, 1) k_bulk_ssrfb(FactorArgs F, int k)
     extern __shared__ double sm[];
     const int j = k + 1 + blockIdx.x;
     for (int i = k + 1; i < F.p; i++) {
-        task_ssrfb<NB, S>(sm, tile_ptr<NB, S>(F, k, j), tile_ptr<NB, S>(F, i, j),
-                          tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k));
+        bulk_task<NB, S>(sm, F, K_SSRFB, k, i, j);
         __syncthreads();
     }
 }

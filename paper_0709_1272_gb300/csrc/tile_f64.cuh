@@ -587,14 +587,14 @@ __device__ __noinline__ void build_t(double *sm, int r0, double *Tt, int l0, int
 // (Rt == nullptr, rows >= r0 = l0) and DTSQRT (B rows l0.. of the R tile Rt).
 // TRI (DTTQRT): At is an upper triangle and V_l reaches rows < l0 + S only.
 template <int NB, int S, bool TRI = false>
-__device__ __noinline__ void trailing_update(double *sm, double *At, double *Rt, int l0, int r0)
+__device__ __noinline__ void trailing_update(double *sm, double *At, double *Rt, int l0, int r0, int r1 = NB)
 {
     using C_ = F64Cfg<NB, S>;
     for (int c0 = l0 + S; c0 < NB; c0 += C_::W) {
         const int nc = min(C_::W, NB - c0);
         stage_chunk<NB, S, C_::W, TRI>(sm, At, c0, nc);
         __syncthreads();
-        apply_block<NB, S, C_::W>(sm, Rt ? Rt + (size_t)c0 * NB + l0 : nullptr, r0, nc, TRI ? l0 + S : NB);
+        apply_block<NB, S, C_::W>(sm, Rt ? Rt + (size_t)c0 * NB + l0 : nullptr, r0, nc, TRI ? l0 + S : r1);
         store_chunk<NB, S, C_::W, TRI>(sm, At, c0, nc, r0);
         __syncthreads();
     }
@@ -776,10 +776,15 @@ __device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt, cons
 // At, the tile's DGEQRT reflectors, is neither read nor written); reflector
 // j then has nonzeros in rows 0..j only, so inner block l works on rows
 // < l0 + S.
-template <int NB, int S, bool MIXED = false, bool TRI = false>
+// EDGE (FP64): the tile is the matrix's ragged last tile row, with nrows of
+// its rows inside the matrix; the rows past them are zero and so are the
+// reflectors' entries there, so the panel, T and the trailing updates skip
+// them (a separate instance: the full tile keeps constant bounds).
+template <int NB, int S, bool MIXED = false, bool TRI = false, bool EDGE = false>
 __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, double *Tt, const int *cex = nullptr,
-                                        int lm = 0)
+                                        int lm = 0, int nrows = NB)
 {
+    const int R1 = EDGE ? nrows : NB;
     using C_ = F64Cfg<NB, S>;
     constexpr int LDC = C_::LDC, LDV = C_::LDV;
     double *Pt = sm + C_::OFF_PT;
@@ -796,7 +801,7 @@ __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, doub
             Ph[c * S + a] = (a <= c) ? ldcg(Rt + (size_t)(l0 + c) * NB + l0 + a) : 0.0;
         }
         __syncthreads();
-        panel_factor<NB, S, true>(sm, Pt, Ph, S, TRI ? l0 + S : NB);
+        panel_factor<NB, S, true>(sm, Pt, Ph, S, TRI ? l0 + S : R1);
         for (int idx = threadIdx.x; idx < S * NB; idx += NT) {
             const int c = idx / NB, r = idx - c * NB;
             const bool in = !TRI || r <= l0 + c;
@@ -811,11 +816,11 @@ __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, doub
                 stcg(Rt + (size_t)(l0 + c) * NB + l0 + a, Ph[c * S + a]);
         }
         __syncthreads();
-        build_t<NB, S>(sm, 0, Tt, l0, TRI ? l0 + S : NB);
+        build_t<NB, S>(sm, 0, Tt, l0, TRI ? l0 + S : R1);
         if constexpr (MIXED)
             trailing_update_mixed<NB, S, TRI>(sm, At, Rt, l0, 0, cex, lm);
         else
-            trailing_update<NB, S, TRI>(sm, At, Rt, l0, 0);
+            trailing_update<NB, S, TRI>(sm, At, Rt, l0, 0, R1);
     }
 }
 
