@@ -70,7 +70,12 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
     unsigned char *smb = (unsigned char *)sm;
     switch (kind) {
     case K_GEQRT:
-        task_geqrt<NB, S, MIXED>(sm, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), cexp_ptr<NB>(F, k), F.lm);
+        if (!MIXED && k == F.q - 1 && F.ncl < NB)
+            task_geqrt<NB, S, false, true>(sm, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), nullptr, 0,
+                                           F.ncl);
+        else
+            task_geqrt<NB, S, MIXED>(sm, tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), cexp_ptr<NB>(F, k),
+                                     F.lm);
         if constexpr (MIXED)
             {
                 __syncthreads();
@@ -79,10 +84,10 @@ __device__ __forceinline__ void run_task(double *sm, const FactorArgs &F, int ki
             }
         break;
     case K_TSQRT:
-        if (!MIXED && i == F.p - 1 && F.nrl < NB)
+        if (!MIXED && ((i == F.p - 1 && F.nrl < NB) || (k == F.q - 1 && F.ncl < NB)))
             task_tsqrt<NB, S, false, false, true>(sm, tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), k),
                                                   tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), nullptr, 0,
-                                                  F.nrl);
+                                                  i == F.p - 1 ? F.nrl : NB, k == F.q - 1 ? F.ncl : NB);
         else
             task_tsqrt<NB, S, MIXED, false>(sm, tile_ptr<NB, S>(F, g_head(G, k, g_dom(G, k, i)), k),
                                             tile_ptr<NB, S>(F, i, k), strip_ptr<NB, S>(F, i, k), cexp_ptr<NB>(F, k),

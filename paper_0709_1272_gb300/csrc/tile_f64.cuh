@@ -587,11 +587,12 @@ __device__ __noinline__ void build_t(double *sm, int r0, double *Tt, int l0, int
 // (Rt == nullptr, rows >= r0 = l0) and DTSQRT (B rows l0.. of the R tile Rt).
 // TRI (DTTQRT): At is an upper triangle and V_l reaches rows < l0 + S only.
 template <int NB, int S, bool TRI = false>
-__device__ __noinline__ void trailing_update(double *sm, double *At, double *Rt, int l0, int r0, int r1 = NB)
+__device__ __noinline__ void trailing_update(double *sm, double *At, double *Rt, int l0, int r0, int r1 = NB,
+                                             int c1 = NB)
 {
     using C_ = F64Cfg<NB, S>;
-    for (int c0 = l0 + S; c0 < NB; c0 += C_::W) {
-        const int nc = min(C_::W, NB - c0);
+    for (int c0 = l0 + S; c0 < c1; c0 += C_::W) {
+        const int nc = min(C_::W, c1 - c0);
         stage_chunk<NB, S, C_::W, TRI>(sm, At, c0, nc);
         __syncthreads();
         apply_block<NB, S, C_::W>(sm, Rt ? Rt + (size_t)c0 * NB + l0 : nullptr, r0, nc, TRI ? l0 + S : r1);
@@ -733,15 +734,26 @@ __device__ __noinline__ void trailing_update_mixed(double *sm, double *At, doubl
 // DGEQRT (Sec. 3.2.1): QR of the diagonal tile At in place (R on and above
 // the diagonal, V below), T strip to Tt.  Inner blocks l in order: panel
 // factorization, T_l, then the block applied to the trailing tile columns.
-template <int NB, int S, bool MIXED = false>
-__device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt, const int *cex = nullptr, int lm = 0)
+// EDGE (FP64): the diagonal tile of the matrix's ragged last tile column,
+// with ncols of its columns inside the matrix: inner blocks wholly past them
+// are zero columns (identity reflectors), so they are not factored and their
+// T blocks are written as zero; the trailing updates stop at ncols.
+template <int NB, int S, bool MIXED = false, bool EDGE = false>
+__device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt, const int *cex = nullptr, int lm = 0,
+                                        int ncols = NB)
 {
     using C_ = F64Cfg<NB, S>;
     constexpr int LDC = C_::LDC, LDV = C_::LDV;
     double *Pt = sm + C_::OFF_PT;
     double *Vs = sm + C_::OFF_V;
     static_assert(C_::PANEL_FITS, "panel must fit in the chunk area");
+    const int C1 = EDGE ? ncols : NB;
     for (int l0 = 0; l0 < NB; l0 += S) {
+        if (EDGE && l0 >= C1) {
+            for (int idx = threadIdx.x; idx < S * S; idx += NT)
+                stcg(Tt + (size_t)l0 * S + idx, 0.0);
+            continue;
+        }
         // stage panel columns l0..l0+S-1, all rows (rows < l0 are R above the block)
         for (int idx = threadIdx.x; idx < S * NB; idx += NT) {
             const int c = idx / NB, r = idx - c * NB;
@@ -764,7 +776,7 @@ __device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt, cons
         if constexpr (MIXED)
             trailing_update_mixed<NB, S>(sm, At, nullptr, l0, l0, cex, lm);
         else
-            trailing_update<NB, S>(sm, At, nullptr, l0, l0);
+            trailing_update<NB, S>(sm, At, nullptr, l0, l0, NB, C1);
     }
 }
 
@@ -776,15 +788,18 @@ __device__ __noinline__ void task_geqrt(double *sm, double *At, double *Tt, cons
 // At, the tile's DGEQRT reflectors, is neither read nor written); reflector
 // j then has nonzeros in rows 0..j only, so inner block l works on rows
 // < l0 + S.
-// EDGE (FP64): the tile is the matrix's ragged last tile row, with nrows of
-// its rows inside the matrix; the rows past them are zero and so are the
-// reflectors' entries there, so the panel, T and the trailing updates skip
-// them (a separate instance: the full tile keeps constant bounds).
+// EDGE (FP64): the tile lies on the matrix's ragged edge, with nrows of its
+// rows and ncols of its columns inside the matrix.  The rows past nrows are
+// zero and so are the reflectors' entries there, so the panel, T and the
+// trailing updates skip them; inner blocks wholly past ncols are zero
+// columns (identity reflectors, T block zero) and are not factored, and the
+// trailing updates stop at ncols.  A separate instance: the full tile keeps
+// constant bounds.
 template <int NB, int S, bool MIXED = false, bool TRI = false, bool EDGE = false>
 __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, double *Tt, const int *cex = nullptr,
-                                        int lm = 0, int nrows = NB)
+                                        int lm = 0, int nrows = NB, int ncols = NB)
 {
-    const int R1 = EDGE ? nrows : NB;
+    const int R1 = EDGE ? nrows : NB, C1 = EDGE ? ncols : NB;
     using C_ = F64Cfg<NB, S>;
     constexpr int LDC = C_::LDC, LDV = C_::LDV;
     double *Pt = sm + C_::OFF_PT;
@@ -792,6 +807,11 @@ __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, doub
     double *Vs = sm + C_::OFF_V;
     static_assert(C_::PANEL_FITS, "panel must fit in the chunk area");
     for (int l0 = 0; l0 < NB; l0 += S) {
+        if (EDGE && l0 >= C1) {
+            for (int idx = threadIdx.x; idx < S * S; idx += NT)
+                stcg(Tt + (size_t)l0 * S + idx, 0.0);
+            continue;
+        }
         for (int idx = threadIdx.x; idx < S * NB; idx += NT) {
             const int c = idx / NB, r = idx - c * NB;
             Pt[c * LDC + r] = (!TRI || r <= l0 + c) ? ldcg(At + (size_t)(l0 + c) * NB + r) : 0.0;
@@ -820,7 +840,7 @@ __device__ __noinline__ void task_tsqrt(double *sm, double *Rt, double *At, doub
         if constexpr (MIXED)
             trailing_update_mixed<NB, S, TRI>(sm, At, Rt, l0, 0, cex, lm);
         else
-            trailing_update<NB, S, TRI>(sm, At, Rt, l0, 0, R1);
+            trailing_update<NB, S, TRI>(sm, At, Rt, l0, 0, R1, C1);
     }
 }
 
