@@ -479,10 +479,13 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     int *sh = (int *)(sm + TF_UPDATE_SMEM);   // column shifts of the updated tile column
     if (tid < NB)
         sh[tid] = cex ? col_shift(__ldg(cex + tid), lm) : 0;
-    // earlier generic writes to the operand areas (the last task, a panel)
-    // are ordered before this task's copy-engine writes, and the operands the
-    // panel task wrote to global memory before this task's copy-engine reads
-    tc::fence_async_all();
+    // this CTA's earlier generic accesses of the operand areas (the last
+    // task, a panel) are ordered before this task's copy-engine writes.  The
+    // operands in global memory need no fence here: the panel task that wrote
+    // them ran a proxy fence (fence_async_all in mixed_build_tfull) between its
+    // stores and the release of its successors, and this task's copies are
+    // issued after the acquire that observed that release.
+    tc::fence_async_smem();
     __syncthreads();
     // ---- P = V^T C: A = V^T (row = reflector, K = tile row), B = C^T (row =
     // column); sets at 0 and 4 OPB
