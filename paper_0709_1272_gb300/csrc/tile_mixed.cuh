@@ -490,8 +490,8 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
     // ---- P = V^T C: A = V^T (row = reflector, K = tile row), B = C^T (row =
     // column); sets at 0 and 4 OPB
     // C rows of round rr: four consecutive rows of column m, two 16-byte
-    // loads per (m, row group); the next round's loads are issued before
-    // this round's conversion and barrier, so they are in flight meanwhile
+    // loads per (m, row group); the next K chunk's loads are issued before
+    // this chunk's conversion and barrier, so they are in flight meanwhile
     auto load_c = [&](int rr, double (&c)[4][4]) {
 #pragma unroll
         for (int x = 0; x < 4; x++) {
