@@ -403,8 +403,9 @@ int tileqr_solve_refine(const tileqr_desc *d, const double *A, int64_t lda, cons
  *   workspace tileqr_batched_ls_workspace_size(bt) bytes, 256-aligned
  *   summary   (optional) iterations = the most any matrix took; method 3;
  *             converged = every matrix stopped by the rule (||dx|| <= tol
- *             ||x||, or ||dx|| no longer halving); rel_residual = the
- *             largest last ||dx|| / ||x||
+ *             ||x||, ||dx|| no longer halving, or the rate of the last two
+ *             steps putting the next correction below tol ||x||);
+ *             rel_residual = the largest last ||dx|| / ||x||
  * Synchronous.  Returns 0, -i, TILEQR_ERR_WORKSPACE, TILEQR_ERR_SINGULAR,
  * TILEQR_ERR_UNSUPPORTED or TILEQR_ERR_CUDA. */
 int tileqr_batched_ls_workspace_size(const tileqr_batch *bt, size_t *bytes);

@@ -6,7 +6,8 @@
 // One CTA owns one matrix at a time (largest first, claimed with a ticket)
 // and runs the whole refinement on it: u = b - r - A x, w = -A^T r,
 // h = R^-T w, d = Q^T u, dx = R^-1 (d1 - h), dr = Q [h; d2], x += dx,
-// r += dr, until ||dx|| <= tol ||x|| or ||dx|| stops halving.  Q^T replays
+// r += dr, until ||dx|| <= tol ||x||, ||dx|| stops halving, or the rate of
+// the last two steps puts the next correction below tol.  Q^T replays
 // the factorization's DLARFB / DSSRFB transformations on the vector in the
 // order of Algorithm 2 (Sec. 3.2.1), inner blocks in order (Sec. 3.2.3); Q
 // replays them in reverse with T_l in place of T_l^T.  Starting from x = 0,
@@ -316,7 +317,10 @@ __device__ void bls_refine(const MatInfo &mi, const BlsEntry &e, int max_iter, d
         }
         const double ndx = sqrt(sdx), nx = sqrt(sx);
         ratio = nx > 0.0 ? ndx / nx : ndx;
-        if (it > 1 && (ratio <= tol || ndx > 0.5 * prev)) {
+        // as tileqr_solve_ls_refine: also stop once the rate of the last two
+        // steps puts the next correction below tol
+        const bool predicted = it > 2 && ndx <= 0.5 * prev && ratio * (ndx / prev) <= tol;
+        if (it > 1 && (ratio <= tol || ndx > 0.5 * prev || predicted)) {
             status = 1;
             break;
         }
