@@ -465,7 +465,7 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         __syncwarp();
     };
 
-    // One thread asks L2 for the task's tiles and T^T operand at once: the
+    // One thread asks L2 for the task's tiles and operands at once: the
     // first phase streams V and C from HBM at full rate instead of one
     // 32-row round at a time, and the later phases (B, T^T, the second reads
     // of V and C) find them in L2.
@@ -473,6 +473,7 @@ __device__ __noinline__ bool task_update_mixed_tf(unsigned char *sm, double *Bt,
         tc::prefetch_l2(Ct, NB * NB * 8);
         if (Bt)
             tc::prefetch_l2(Bt, NB * NB * 8);
+        tc::prefetch_l2(TFg + TF_OFF_VT, TF_BYTES);
         tc::prefetch_l2(TW, TF_BYTES);
         tc::prefetch_l2(TFg + TF_OFF_V, TF_BYTES);
     }
