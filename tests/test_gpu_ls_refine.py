@@ -109,3 +109,18 @@ def test_full_tall_skinny_16_rhs(tq):
     err = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
     assert info.converged == 1 and err <= 1e-10, (info.as_dict(), err)
     assert _optimality(A, B - A @ X) <= 20 * n * EPS
+
+
+def test_refined_ls_many_rhs(tq):
+    """More right-hand sides than one 128-column chunk of the tensor-core
+    application (two chunks, the second partial), flat TF32 factors."""
+    m, n, nrhs = 2000, 300, 130
+    A, B = _tall_problem(m, n, nrhs, 1e2, 1.0, seed=97)
+    Ad, Bd = tq.to_device_colmajor(A), tq.to_device_colmajor(B)
+    f = tq.tileqr_factor(Ad, 128, 16, precision=tq.TILEQR_TF32).check()
+    X, info = f.solve_ls_refine(Ad, Bd, max_iter=10, tol=1e-14)
+    X = X.cpu().numpy()
+    Xo = oracle.solve_ls(oracle.tiled_qr(A, 128, 16), B.copy())
+    err = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
+    assert info.converged == 1 and err <= 1e-10, (info.as_dict(), err)
+    assert _optimality(A, B - A @ X) <= 20 * n * EPS
