@@ -426,25 +426,41 @@ __device__ __noinline__ void panel_factor(double *sm, double *Pt, double *Ph, in
     double *taus = sm + C_::OFF_TAU;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int RPL = (NB + 31) / 32;   // tail rows per lane
-    if (warp == 0)
+    // Warp 0 forms each column's scalars and scales the column's tail into
+    // the stored reflector v = x / (alpha - beta) before the column's
+    // barrier, so the other warps read v as it is instead of each of them
+    // multiplying it again (on GB300 every FP64 instruction takes the SM's
+    // shared FP64 pipe).
+    auto scale_tail = [&](double *y, int r0, double sc) {
+#pragma unroll
+        for (int k = 0; k < RPL; k++) {
+            const int r = r0 + lane + 32 * k;
+            if (r < rows)
+                y[r] *= sc;
+        }
+        __syncwarp();
+    };
+    if (warp == 0) {
         column_scalars(Pt, TS ? 0 : 1, rows, Ph[0], red, lane);
+        scale_tail(Pt, TS ? 0 : 1, red[2]);
+    }
     __syncthreads();
 #pragma unroll 1
     for (int jj = 0; jj < S; jj++) {
         const int t0 = TS ? 0 : jj + 1;
         double *x = Pt + jj * LDC;
         const double *sc = red + 4 * (jj & 1);
-        const double beta = sc[0], tau = sc[1], scale = sc[2];
+        const double beta = sc[0], tau = sc[1];
         // apply H_jj to columns jj+1..S-1 (warp 0: column jj+1; warps 1..:
-        // the rest, strided).  Each lane scales its slice of the tail once
-        // (v = x / (alpha - beta)), so the dot products see O(1) reflector
+        // the rest, strided).  The tail already holds the scaled reflector
+        // v = x / (alpha - beta), so the dot products see O(1) reflector
         // entries and neither under- nor overflow for extreme magnitudes.
         if (tau != 0.0 && jj + 1 < S) {
             double vs[RPL];
 #pragma unroll
             for (int k = 0; k < RPL; k++) {
                 const int r = t0 + lane + 32 * k;
-                vs[k] = (r < rows) ? x[r] * scale : 0.0;
+                vs[k] = (r < rows) ? x[r] : 0.0;
             }
             // helpers: the warps on the other three sub-partitions (warp & 3
             // != 0), so that no FP64 work queues on warp 0's FP64 pipe (one
@@ -476,14 +492,14 @@ __device__ __noinline__ void panel_factor(double *sm, double *Pt, double *Ph, in
                 __syncwarp();
             }
         }
-        // scalars of the next column (its update by H_jj, if any, was warp 0's)
+        // scalars of the next column (its update by H_jj, if any, was warp 0's),
+        // and its tail scaled into the reflector
         if (warp == 0 && jj + 1 < S) {
             const int c = jj + 1;
             column_scalars(Pt + c * LDC, TS ? 0 : c + 1, rows, Ph[c * ldh + c], red + 4 * (c & 1), lane);
+            scale_tail(Pt + c * LDC, TS ? 0 : c + 1, red[4 * (c & 1) + 2]);
         }
         __syncthreads();
-        for (int r = t0 + tid; r < rows; r += NT)
-            x[r] *= scale;
         if (tid == 0) {
             Ph[jj * ldh + jj] = beta;
             taus[jj] = tau;
