@@ -456,20 +456,21 @@ __device__ __noinline__ void panel_factor(double *sm, double *Pt, double *Ph, in
         // v = x / (alpha - beta), so the dot products see O(1) reflector
         // entries and neither under- nor overflow for extreme magnitudes.
         if (tau != 0.0 && jj + 1 < S) {
-            double vs[RPL];
-#pragma unroll
-            for (int k = 0; k < RPL; k++) {
-                const int r = t0 + lane + 32 * k;
-                vs[k] = (r < rows) ? x[r] : 0.0;
-            }
             // helpers: the warps on the other three sub-partitions (warp & 3
-            // != 0), so that no FP64 work queues on warp 0's FP64 pipe (one
-            // warp instruction per ~64 cycles per sub-partition on GB300)
+            // != 0), so that no FP64 work queues on warp 0's FP64 pipe; each
+            // takes two columns at a time, one per half-warp, which needs
+            // fewer FP64 instructions per column (a 4-level reduction shared
+            // by the two) on GB300's thin FP64 pipe
             constexpr int NHELP = NWARP - NWARP / 4;
             const int h = warp - 1 - (warp >> 2);   // helper index of warp (warp & 3 != 0)
-            const int cfirst = (warp == 0) ? jj + 1 : ((warp & 3) ? jj + 2 + h : S);
-            const int cstep = (warp == 0) ? S : NHELP;
-            for (int c = cfirst; c < S; c += cstep) {
+            if (warp == 0) {
+                const int c = jj + 1;
+                double vs[RPL];
+#pragma unroll
+                for (int k = 0; k < RPL; k++) {
+                    const int r = t0 + lane + 32 * k;
+                    vs[k] = (r < rows) ? x[r] : 0.0;
+                }
                 double *y = Pt + c * LDC;
                 double d = 0.0;
 #pragma unroll
@@ -490,6 +491,41 @@ __device__ __noinline__ void panel_factor(double *sm, double *Pt, double *Ph, in
                         y[r] = fma(-tw, vs[k], y[r]);
                 }
                 __syncwarp();
+            } else if (warp & 3) {
+                constexpr int RPH = (NB + 15) / 16;   // tail rows per lane of a half-warp
+                const int hl = lane & 15, half = lane >> 4;
+                double vh[RPH];
+#pragma unroll
+                for (int k = 0; k < RPH; k++) {
+                    const int r = t0 + hl + 16 * k;
+                    vh[k] = (r < rows) ? x[r] : 0.0;
+                }
+                for (int cp = jj + 2 + 2 * h; cp < S; cp += 2 * NHELP) {
+                    const int c = cp + half;
+                    const bool live = c < S;
+                    double *y = Pt + (live ? c : cp) * LDC;
+                    double d = 0.0;
+#pragma unroll
+                    for (int k = 0; k < RPH; k++) {
+                        const int r = t0 + hl + 16 * k;
+                        if (live && r < rows)
+                            d = fma(vh[k], y[r], d);
+                    }
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1)
+                        d += __shfl_xor_sync(0xffffffffu, d, o);
+                    const double tw = live ? tau * (Ph[c * ldh + jj] + d) : 0.0;
+                    __syncwarp();
+                    if (live && hl == 0)
+                        Ph[c * ldh + jj] -= tw;
+#pragma unroll
+                    for (int k = 0; k < RPH; k++) {
+                        const int r = t0 + hl + 16 * k;
+                        if (live && r < rows)
+                            y[r] = fma(-tw, vh[k], y[r]);
+                    }
+                    __syncwarp();
+                }
             }
         }
         // scalars of the next column (its update by H_jj, if any, was warp 0's),
