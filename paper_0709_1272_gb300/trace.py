@@ -128,6 +128,63 @@ def span_bounds(graph, dur_by_kind: dict, slots: int) -> dict:
             "work_per_slot_s": float(dur.sum() / slots)}
 
 
+def ready_level(kind: int, k: int, j: int) -> int:
+    """Ready-queue level of a task (0 = served first), as the persistent
+    kernel assigns it: DGEQRT 0, DTSQRT and DTTQRT 1, DLARFB and DTTMQR 2,
+    DSSRFB 3, and an update of column k + 1 one level up (it feeds the next
+    step's panel)."""
+    base = kind if kind < 4 else (1 if kind == 4 else 2)
+    return base - 1 if (kind in (2, 3, 5) and j == k + 1) else base
+
+
+def priority_schedule(graph, dur_by_kind: dict, slots: int, claim_s: float = 0.0) -> dict:
+    """Simulated span of the persistent kernel's policy on `graph`
+    (tileqr_task_graph output, QR kinds): `slots` workers; a released task
+    joins the FIFO of its ready level; a free worker takes the oldest task of
+    the lowest non-empty level and holds it for claim_s + its kind's duration
+    (seconds, keyed by the kind codes 0..5).  With the per-kind mean times of
+    a trace it predicts the trace's span, and with other times it answers
+    what-if questions (a faster update, a faster panel, more workers).
+    Returns the span and the busy fraction of the workers."""
+    import heapq
+    from collections import deque
+    tasks, ndeps, ptr, succ = graph
+    nt = len(tasks)
+    dur = np.array([dur_by_kind[int(k)] for k in tasks[:, 0]], dtype=np.float64)
+    lvl = [ready_level(int(kd), int(k), int(j)) for kd, _, j, k in tasks]
+    left = ndeps.astype(np.int64).copy()
+    queues = [deque() for _ in range(4)]
+    for g in range(nt):
+        if left[g] == 0:
+            queues[lvl[g]].append(g)
+    events = []
+    now, free, done, seq, busy = 0.0, slots, 0, 0, 0.0
+    while done < nt:
+        while free > 0:
+            q = next((q for q in queues if q), None)
+            if q is None:
+                break
+            g = q.popleft()
+            free -= 1
+            busy += claim_s + dur[g]
+            heapq.heappush(events, (now + claim_s + dur[g], seq, g))
+            seq += 1
+        if not events:
+            raise ValueError("the graph has a cycle or a task that is never released")
+        # every task ending now completes (in start order) before the
+        # freed workers claim
+        now = events[0][0]
+        while events and events[0][0] == now:
+            _, _, g = heapq.heappop(events)
+            free += 1
+            done += 1
+            for v in succ[ptr[g]:ptr[g + 1]]:
+                left[v] -= 1
+                if left[v] == 0:
+                    queues[lvl[v]].append(int(v))
+    return {"span_s": float(now), "busy_fraction": float(busy / (slots * now)) if now > 0 else 1.0}
+
+
 def to_chrome(records: np.ndarray, path: str, domain: int = 0) -> None:
     d = decode(records, domain)
     base = int(d["t0"].min())

@@ -138,3 +138,70 @@ def test_span_bounds_closed_forms(tq):
     span = (rec[:, 2].max() - rec[:, 1].min()) * 1e-9
     assert span >= b["critical_path_s"] - 1e-12
     assert span >= b["work_per_slot_s"] - 1e-12
+
+
+def _ticks_schedule(graph, dur, slots):
+    """The kernel's policy stepped one integer tick at a time (a second,
+    independent form of trace.priority_schedule for integer durations)."""
+    tasks, ndeps, ptr, succ = graph
+    nt = len(tasks)
+    lvl = [trace.ready_level(int(kd), int(k), int(j)) for kd, _, j, k in tasks]
+    left = [int(x) for x in ndeps]
+    fifo = [[] for _ in range(4)]
+    for g in range(nt):
+        if left[g] == 0:
+            fifo[lvl[g]].append(g)
+    running = {}          # task -> end tick
+    started = []          # start order
+    t, done = 0, 0
+    while done < nt:
+        for g in [g for g in started if running.get(g) == t]:
+            del running[g]
+            done += 1
+            for v in succ[ptr[g]:ptr[g + 1]]:
+                left[int(v)] -= 1
+                if left[int(v)] == 0:
+                    fifo[lvl[int(v)]].append(int(v))
+        while len(running) < slots and any(fifo):
+            g = next(f for f in fifo if f).pop(0)
+            running[g] = t + dur[int(tasks[g, 0])]
+            started.append(g)
+        if done < nt:
+            t += 1
+    return t
+
+
+def test_priority_schedule(tq):
+    nb = 64
+    # one tile column: the DGEQRT then p - 1 DTSQRTs in a chain, whatever the slots
+    p = 9
+    graph = tq.tileqr_task_graph(p * nb, nb, nb)
+    dur = {0: 5.0, 1: 3.0, 2: 1.0, 3: 2.0, 4: 1.0, 5: 1.0}
+    for slots in (1, 4):
+        assert trace.priority_schedule(graph, dur, slots)["span_s"] == pytest.approx(5.0 + (p - 1) * 3.0)
+    # one worker runs the whole work back to back, claims included
+    graph = tq.tileqr_task_graph(5 * nb, 4 * nb, nb)
+    b = trace.span_bounds(graph, dur, slots=1)
+    r = trace.priority_schedule(graph, dur, 1, claim_s=0.5)
+    assert r["span_s"] == pytest.approx(b["work_s"] + 0.5 * len(graph[0]))
+    assert r["busy_fraction"] == pytest.approx(1.0)
+    # as many workers as tasks: the critical path
+    r = trace.priority_schedule(graph, dur, len(graph[0]))
+    assert r["span_s"] == pytest.approx(trace.span_bounds(graph, dur, 1)["critical_path_s"])
+    # in between: never below either bound, and equal to the tick-by-tick
+    # form of the same policy (flat and tree graphs, integer durations)
+    idur = {0: 7, 1: 5, 2: 2, 3: 3, 4: 4, 5: 2}
+    for (m, n, h) in ((6 * nb, 6 * nb, 0), (10 * nb, 3 * nb, 3), (4 * nb, 7 * nb, 0)):
+        graph = tq.tileqr_task_graph(m, n, nb, h)
+        for slots in (2, 3, 5):
+            r = trace.priority_schedule(graph, idur, slots)
+            b = trace.span_bounds(graph, idur, slots)
+            assert r["span_s"] >= max(b["critical_path_s"], b["work_per_slot_s"]) - 1e-9
+            assert r["span_s"] == _ticks_schedule(graph, idur, slots)
+
+
+def test_ready_levels():
+    # DGEQRT > DTSQRT > DLARFB > DSSRFB; the tree's merge joins the panel
+    # level, its update the row-update level; column k + 1 one level up
+    assert [trace.ready_level(kd, 0, 5) for kd in range(6)] == [0, 1, 2, 3, 1, 2]
+    assert [trace.ready_level(kd, 0, 1) for kd in (2, 3, 5)] == [1, 2, 1]
